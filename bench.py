@@ -1,0 +1,322 @@
+"""Benchmark: k-point eigenpairs/s of the Bloch-wave band solve on one GB300.
+
+Workload (default): 128^3 periodic cell, 200 Voronoi grains, Cu-like cubic
+stiffness with a <001> von Mises-Fisher fibre (kappa 20), 10 bands at 64
+wave vectors on Gamma-X-M-Gamma-R; synthetic, seeded.  A step solves one
+batch of wave vectors of that path (--k-per-step) to the frequency accuracy
+of the form (chosen: FP32 fields + FP64 refinement; plain: FP64 throughout).
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own k
+batches (no collective on the data path; barrier + max over ranks for time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "k-point eigenpairs/s at 128^3 (freq rel err <=1e-6)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0}   # algorithmic bytes per voxel, 5-pass chain
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rve128_g200")
+    ap.add_argument("--form", default="chosen", choices=["chosen", "plain"])
+    ap.add_argument("--k-per-step", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def oracle_sample(p, n_iter=2):
+    """Oracle as it stands, timed on a bounded sample: n_iter PCG iterations of
+    Algorithm 2 at the workload's grid for its first non-zero wave vector."""
+    from oracle import bloch_oracle as O
+    from paper_2106_12487_gb300 import synth
+    med = O.Medium.from_problem(p)
+    k = p.k_list[1]
+    b = synth.random_field(p.grid, 99)
+    t0 = time.perf_counter()
+    O.pcg(lambda x: O.apply_K(med, k, x), lambda x: O.apply_precond(med, k, x), b, 1e-30, n_iter)
+    dt = time.perf_counter() - t0
+    # pcg runs n_iter operator applies plus one for the final true residual
+    return dt / (n_iter + 1)
+
+
+def oracle_applies_per_eigenpair():
+    """K-applies per eigenpair of the oracle's own band solve (shift-invert
+    Lanczos, ARPACK) on the 16^3 workload, as recorded by
+    tests/golden/make_golden.py."""
+    path = os.path.join(ROOT, "tests", "golden", "rve16_g8_bands.json")
+    with open(path) as f:
+        g = json.load(f)
+    return float(g["oracle_cg_iters"]) / float(g["eigenpairs"]), "rve16_g8 oracle Lanczos"
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, ws, rank):
+    """The oracle (FP64 numpy) on the host cores, same workload and metric."""
+    if rank != 0:
+        return
+    from paper_2106_12487_gb300 import synth
+    p = synth.workload(args.workload)
+    a_per_pair, src = oracle_applies_per_eigenpair()
+    for _ in range(args.warmup):
+        oracle_sample(p, 1)
+    t_apply = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t_apply.append(oracle_sample(p, 1))
+    wall = time.perf_counter() - t0
+    ta = float(np.mean(t_apply))
+    value = 1.0 / (ta * a_per_pair)
+    sample = (f"{args.steps} x (1 PCG iteration + residual check) of the FP64 oracle at {p.grid} "
+              f"({ta:.2f} s per A_k apply); eigenpairs/s = 1/(s per apply x {a_per_pair:.1f} applies per "
+              f"eigenpair, {src})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "grid": list(p.grid),
+                                            "n_bands": p.n_bands, "n_k": int(p.k_list.shape[0])},
+            "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2106_12487_gb300 import bloch, synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    p = synth.workload(args.workload)
+    prec = bloch.FP32 if args.form == "chosen" else bloch.FP64
+    opt = dict(precision=prec, method=bloch.SUBSPACE, tol_lin=1e-3 if prec == bloch.FP32 else 1e-8,
+               tol_eig=1e-7 if prec == bloch.FP32 else 1e-10, max_cg=500, max_outer=300)
+    plan = bloch.Plan.from_problem(p, **opt)
+    nk = p.k_list.shape[0]
+    kps = args.k_per_step
+
+    def kbatch(step):
+        # each rank walks its own contiguous share of the path
+        idx = [((step * ws + rank) * kps + i) % nk for i in range(kps)]
+        return p.k_list[idx]
+
+    stream = torch.cuda.current_stream()
+    for s in range(args.warmup):
+        plan.solve_bands(kbatch(s), p.n_bands, allow_nonconv=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats_all = []
+    launches0 = plan.kernel_launches
+    ev0.record(stream)
+    for s in range(args.steps):
+        _, st, _ = plan.solve_bands(kbatch(args.warmup + s), p.n_bands, allow_nonconv=True)
+        stats_all.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    launches = plan.kernel_launches - launches0
+    t = ev0.elapsed_time(ev1) / 1000.0
+    t = max_over_ranks(ws, t)
+    pairs = args.steps * kps * p.n_bands * ws
+    value = pairs / t
+    cg = sum(s["cg_iterations"] for s in stats_all)
+    kap = sum(s["k_applies"] for s in stats_all)
+
+    # dominant kernel chain: the 5-pass K-apply on a block of q vectors, timed
+    # with CUDA events on the launching stream
+    q = min(2 * p.n_bands, p.n_bands + 8)
+    dt = torch.complex64 if prec == bloch.FP32 else torch.complex128
+    u = torch.randn(q * 3 * plan.V, dtype=dt, device="cuda")
+    out = torch.empty_like(u)
+    kq = np.repeat(p.k_list[5:6], q, axis=0)
+    for _ in range(3):
+        plan.apply_K(kq, u, out)
+    torch.cuda.synchronize()
+    reps = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.apply_K(kq, u, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / 1000.0 / reps
+    alg_bytes = KAPPLY_BYTES_PER_VOXEL[prec] * plan.V * q
+    peak, peak_src = peaks()
+    achieved = alg_bytes / t_apply / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"K-apply 5-pass chain, {q} vectors at {p.grid} ({peak_src} peak)",
+            "ms_per_launch": t_apply * 1000.0}
+
+    # end to end through the public API with host buffers: plan upload from
+    # host arrays, band solve, frequencies back to host
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan2 = bloch.Plan.from_problem(p, **opt)
+        om, _, _ = plan2.solve_bands(kbatch(0), p.n_bands, allow_nonconv=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        plan2.close()
+        h2d = p.grain_ids.nbytes + p.C_per_grain.nbytes + p.rho.nbytes + kps * 3 * 8
+        e2e = {"value": kps * p.n_bands / te, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(om.nbytes)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        ta = oracle_sample(p, 2)
+        a_per_pair, src = oracle_applies_per_eigenpair()
+        cpu = {"value": 1.0 / (ta * a_per_pair), "unit": "eigenpairs/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"2 PCG iterations + residual of the FP64 oracle at {p.grid} ({ta:.2f} s per A_k apply), "
+                         f"scaled by {a_per_pair:.1f} oracle applies per eigenpair ({src})"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == bloch.FP32 else "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "grid": list(p.grid), "grains": int(p.G),
+                           "n_bands": p.n_bands, "n_k_path": int(nk), "k_per_step": kps,
+                           "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
+                           "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
+                                 % (3 * plan.V * 8 / 1e6)},
+                "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+                "solver": {"cg_iterations": cg, "k_applies": kap,
+                           "k_applies_per_eigenpair": kap / (args.steps * kps * p.n_bands)}}
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

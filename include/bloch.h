@@ -1,0 +1,205 @@
+/*
+ * bloch.h -- C ABI of the GB300 (sm_103a) FFT-based Bloch-wave dispersion library.
+ *
+ * The library applies, inverts and diagonalises the Fourier-space Bloch-wave
+ * operators of Segurado & Lebensohn, "An FFT-based approach for Bloch wave
+ * analysis: application to polycrystals" (arXiv 2106.12487):
+ *
+ *   stiffness  A_k{U}_i = (xi_j + k_j) F{ C_ijkl(x) F^-1((xi_l + k_l) U_k) }   Section 3.2, Eq. (hatA)
+ *   mass       M{U}     = F{ rho(x) F^-1(U) }                                  Section 3.2, Eq. (hatM)
+ *   inverse    A_k^-1 by conjugate gradient with the Green-operator
+ *              preconditioner P_ik = C0_ijkl (xi+k)_j (xi+k)_l                  Section 3.3, Algorithm 2,
+ *                                                                             Eqs. (matrixP), (precond)
+ *   bands      the n lowest omega = sqrt(lambda) of A_k U = lambda M U for a
+ *              list of wave vectors, by shift-invert Lanczos or subspace
+ *              iteration                                                      Section 3.3, Algorithms 1 and 3
+ *
+ * Conventions shared by every entry point
+ *   - grid = {Nx, Ny, Nz}; every field is stored [batch][component][z][y][x]
+ *     (x fastest), components (x, y, z); a "vector" is 3*V complex values with
+ *     V = Nx*Ny*Nz.  Fourier fields use the standard FFT bin order along each
+ *     axis: bin m carries xi = 2*pi/L*(m if m < ceil(N/2) else m - N), which is
+ *     the set of Eq. (frequencies).
+ *   - Complex values are interleaved (re, im): float2 for BLOCH_FP32 buffers,
+ *     double2 for BLOCH_FP64 buffers.  Device pointers must be 16-byte aligned.
+ *   - SI units throughout: Pa, kg/m^3, m, rad/m, rad/s.
+ *   - Stiffness tables are 6x6 Voigt matrices in the order (11,22,33,23,13,12)
+ *     with engineering shear strain (sigma_V = C_V eps_V, eps_V = (e11, e22,
+ *     e33, 2e23, 2e13, 2e12)), row-major, symmetric positive definite.
+ *   - Ownership: the caller owns every buffer it passes; the plan copies what
+ *     it keeps during bloch_plan_create.  Device work is enqueued on the
+ *     plan's CUDA stream; entry points that return host results synchronise
+ *     that stream before returning.
+ *   - Errors: every entry point returns a bloch_status; no exception crosses
+ *     the ABI.  bloch_last_error() returns a thread-local message describing
+ *     the most recent failure on the calling thread.
+ */
+#ifndef BLOCH_H
+#define BLOCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BLOCH_OK = 0,
+    BLOCH_EINVAL = 1,        /* an argument is out of range or inconsistent      */
+    BLOCH_ENOMEM = 2,        /* device or host allocation failed                 */
+    BLOCH_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed      */
+    BLOCH_ENOTCONV_CG = 4,   /* PCG hit its iteration cap before the tolerance   */
+    BLOCH_ENOTCONV_EIG = 5,  /* the eigensolver hit its sweep/restart cap        */
+    BLOCH_ENONFINITE = 6,    /* NaN or Inf met in inputs or iterates             */
+    BLOCH_EUNSUPPORTED = 7   /* grid size with a prime factor > 7, or too large  */
+} bloch_status;
+
+typedef enum { BLOCH_FP64 = 0, BLOCH_FP32 = 1 } bloch_precision;
+typedef enum { BLOCH_LANCZOS = 0, BLOCH_SUBSPACE = 1 } bloch_method;
+
+typedef struct bloch_plan bloch_plan;   /* opaque; owned by the library */
+
+/* Solver options.  bloch_default_options() fills the defaults listed here. */
+typedef struct {
+    int32_t precision;   /* BLOCH_FP64: fields and CG in FP64 (the paper's plain form).
+                            BLOCH_FP32: fields and CG in FP32 complex with FP32
+                            accumulation, then an FP64 Rayleigh-Ritz refinement of the
+                            converged block.  Default BLOCH_FP64.                       */
+    int32_t method;      /* BLOCH_LANCZOS (shift-invert Lanczos with thick restart) or
+                            BLOCH_SUBSPACE (Algorithm 1).  Default BLOCH_SUBSPACE.       */
+    double tol_lin;      /* PCG stop: ||Y - A U||_2 <= tol_lin ||Y||_2.  Default 1e-10.  */
+    double tol_eig;      /* eigensolver stop (see bloch_solve_bands).  Default 1e-10.    */
+    int32_t max_cg;      /* PCG iteration cap per solve.  Default 2000.                  */
+    int32_t max_outer;   /* sweep cap (subspace) or restart cap (Lanczos).  Default 500. */
+    int32_t block;       /* subspace block size q; 0 = min(2n, n+8) (Algorithm 1).      */
+    int32_t k_batch;     /* wave vectors advanced together; 0 = choose from free memory. */
+    int32_t ncv;         /* Lanczos basis size; 0 = max(2n+1, 20).                       */
+} bloch_options;
+
+/* Statistics of the last bloch_solve_bands call (all counts summed over k). */
+typedef struct {
+    int64_t cg_iterations;     /* PCG iterations (each = one A_k apply per system)   */
+    int64_t linear_solves;     /* PCG solves                                         */
+    int64_t k_applies;         /* all A_k applies, incl. residual checks/refinement  */
+    int64_t outer_iterations;  /* subspace sweeps or Lanczos restarts                */
+    double max_rel_residual;   /* max over bands of ||A u - lam M u|| / ||A u|| (FP64) */
+    double seconds;            /* wall time of the call                              */
+} bloch_stats;
+
+/* Fill *opt with the defaults above. */
+void bloch_default_options(bloch_options* opt);
+
+/*
+ * Create a plan for one voxelised periodic cell (Section 3.2 discretisation,
+ * Algorithm 3 step (a)).
+ *   grid          {Nx, Ny, Nz}, each >= 1 with prime factors in {2,3,5,7} and <= 512
+ *   L             cell edge lengths (m), > 0
+ *   grain_ids     host, V int32 values in [0, G), layout [z][y][x]
+ *   G             number of grains (>= 1)
+ *   C_per_grain   host, G x 6 x 6 Voigt stiffness (Pa), symmetric positive definite
+ *   rho           host, G densities (kg/m^3), > 0
+ *   opt           solver options (may be NULL for defaults); copied
+ *   cuda_stream   cudaStream_t to enqueue on (NULL = legacy default stream)
+ * The plan stores grain ids (int32) and per-grain tables on the device, the
+ * volume-averaged stiffness C0 used by the preconditioner, the frequency and
+ * twiddle tables.  Returns BLOCH_EINVAL on invalid arguments (message in
+ * bloch_last_error), BLOCH_EUNSUPPORTED for grid sizes outside the limits,
+ * BLOCH_ENOMEM / BLOCH_ECUDA on device failures.  On failure *out is NULL.
+ */
+bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const double L[3],
+                               const int32_t* grain_ids, int32_t G, const double* C_per_grain,
+                               const double* rho, const bloch_options* opt, void* cuda_stream);
+
+/* Release every device and host resource of the plan (NULL is ignored). */
+void bloch_plan_destroy(bloch_plan* plan);
+
+/*
+ * Stiffness operator, Eq. (hatA), on nb Fourier-space vectors at once.
+ *   k          host, nb x 3 wave vectors (rad/m), one per vector
+ *   precision  BLOCH_FP32 (u, Ku are float2) or BLOCH_FP64 (double2)
+ *   u          device, nb x 3 x V complex, Fourier basis; not modified
+ *   Ku         device, nb x 3 x V complex; may not alias u
+ * Enqueued on the plan's stream (asynchronous).  Scratch: 6 x V complex per
+ * vector, held by the plan and grown on demand.
+ */
+bloch_status bloch_apply_K(bloch_plan* plan, int32_t nb, const double* k, int32_t precision,
+                           const void* u, void* Ku);
+
+/*
+ * Mass operator, Eq. (hatM): Mu = F{rho(x) F^-1 u} on nb Fourier-space vectors.
+ * With a uniform density this is exactly rho*u (F F^-1 = I) and costs one
+ * scaling; otherwise three inverse and three forward 3D FFTs per vector.
+ * Same buffer conventions as bloch_apply_K; Mu may alias u.
+ */
+bloch_status bloch_apply_M(bloch_plan* plan, int32_t nb, int32_t precision, const void* u, void* Mu);
+
+/*
+ * Green-operator preconditioner, Eqs. (matrixP) and (precond):
+ * z(xi) = P^-1(xi + k) r(xi), P_ik = C0_ijkl (xi+k)_j (xi+k)_l, with C0 the
+ * volume average of C(x); bins where xi + k = 0 give z = 0.
+ * Same buffer conventions as bloch_apply_K; z may alias r.
+ */
+bloch_status bloch_apply_precond(bloch_plan* plan, int32_t nb, const double* k, int32_t precision,
+                                 const void* r, void* z);
+
+/*
+ * Inverse operator of Eq. (def_invop) by preconditioned CG (Algorithm 2),
+ * nb independent systems A_{k_b} x_b = b_b advanced together.
+ *   b          device, nb x 3 x V complex right-hand sides (bin 0 must be zero when k = 0)
+ *   x          device, nb x 3 x V complex; on entry the start vector if use_x0 != 0,
+ *              else ignored (x0 = 0); on exit the solutions
+ *   tol        stop when ||b - A x||_2 <= tol ||b||_2 (recursive residual)
+ *   max_iter   iteration cap
+ *   iters      host, nb (may be NULL): iterations taken per system
+ *   rel_res    host, nb (may be NULL): final recursive relative residual per system
+ * Synchronises the stream.  Returns BLOCH_ENOTCONV_CG if any system missed tol.
+ */
+bloch_status bloch_pcg(bloch_plan* plan, int32_t nb, const double* k, int32_t precision,
+                       const void* b, void* x, double tol, int32_t max_iter, int32_t use_x0,
+                       int32_t* iters, double* rel_res);
+
+/*
+ * Dispersion bands, Algorithm 3: for each wave vector k_r the n_bands lowest
+ * eigenvalues lambda of A_k U = lambda M U, reported as omega = sqrt(lambda)
+ * (rad/s), ascending.  At k = 0 the three rigid translations are reported as
+ * omega = 0 and the rest is sought on their M-orthogonal complement.
+ *   n_k, k_list   host, n_k x 3 (rad/m)
+ *   n_bands       >= 1 and < 3V
+ *   omega_out     host, n_k x n_bands
+ *   vecs_out      optional device buffer n_k x n_bands x 3 x V complex in the
+ *                 precision of the options (NULL = not returned), M-normalised
+ *   stats         optional host struct (NULL = not returned)
+ * Stop test (options.method = BLOCH_SUBSPACE, Algorithm 1): err1 <= tol_eig
+ * and err2 <= 10 tol_eig (relative eigenvalue change, max relative residual).
+ * With BLOCH_FP32 the FP32 iteration stops at the FP32 noise floor and the
+ * block is refined by an FP64 Rayleigh-Ritz projection.  Synchronises.
+ */
+bloch_status bloch_solve_bands(bloch_plan* plan, int32_t n_k, const double* k_list, int32_t n_bands,
+                               double* omega_out, void* vecs_out, bloch_stats* stats);
+
+/*
+ * Host utility (no GPU): the dense generalised Hermitian eigenproblem
+ * K Q = M Q diag(lam) solved for the projected matrices of Algorithm 1
+ * (step EIG(K, M)), by Cholesky of M and cyclic complex Jacobi, in FP64.
+ *   n      matrix order
+ *   K, M   n x n row-major complex (interleaved re, im), Hermitian; M positive definite
+ *   lam    out, n eigenvalues ascending
+ *   Q      out, n x n row-major complex, eigenvectors in columns, Q^H M Q = I
+ * Returns BLOCH_EINVAL if M is not positive definite.
+ */
+bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, double* lam, double* Q);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* bloch_last_error(void);
+
+/* Bytes of device memory held by the plan right now (tables + scratch). */
+size_t bloch_plan_device_bytes(const bloch_plan* plan);
+
+/* Number of CUDA kernels the plan has launched since it was created. */
+uint64_t bloch_plan_kernel_launches(const bloch_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLOCH_H */

@@ -1,0 +1,757 @@
+// Eigensolvers and the dispersion driver (Section 3.3, Algorithms 1 and 3).
+//
+// Subspace iteration (Algorithm 1) advances a batch of wave vectors ("slots")
+// together, each slot holding its own block of q vectors [slot][q][3][V].
+// One sweep, for every active slot:
+//   KU = A_k U, lam_p = Rayleigh quotient of u_p, R = M U - KU diag(1/lam)
+//   err1 (relative change of lam), err2 = max_p lam_p |R_p| / |KU_p|
+//   delta = A_k^-1 R by PCG (Algorithm 2) on all slots x q systems at once
+//   U_bar = U diag(1/lam) + delta          (= A_k^-1 M U, the paper's step)
+//   Kn = M U - r_cg (= A_k U_bar exactly up to the recursive CG residual)
+//   K = U_bar^H Kn, M = U_bar^H M U_bar, (K, M) -> (lam, Q), U <- U_bar Q
+// Writing the paper's inverse step as a correction of U diag(1/lam) keeps the
+// PCG right-hand side small, so the field precision (FP32 in the chosen form)
+// only limits the correction, and the residual R can be formed in FP64 from
+// an FP64 operator apply (the refinement phase) while every other step stays
+// in FP32.  Converged slots are refilled from the queue of wave vectors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "eig_kernels.cuh"
+#include "internal.h"
+
+namespace bloch {
+
+using cd = std::complex<double>;
+
+// ====================================================================
+// Small dense Hermitian eigenproblems (host, FP64)
+// ====================================================================
+
+// Cyclic complex Jacobi.  A (n x n, row-major, Hermitian) is destroyed.
+// w ascending; V row-major with eigenvectors in columns.
+static bool herm_jacobi(int n, std::vector<cd>& A, std::vector<double>& w, std::vector<cd>& V) {
+    V.assign((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    bool ok = false;
+    for (int sweep = 0; sweep < 200; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double a2 = std::norm(A[(size_t)i * n + j]);
+                tot += a2;
+                if (i != j) off += a2;
+            }
+        if (off <= 1e-32 * tot || tot == 0.0) {
+            ok = true;
+            break;
+        }
+        for (int p = 0; p < n - 1; ++p)
+            for (int r = p + 1; r < n; ++r) {
+                const cd apr = A[(size_t)p * n + r];
+                const double mag = std::abs(apr);
+                if (mag == 0.0) continue;
+                const double app = A[(size_t)p * n + p].real(), arr = A[(size_t)r * n + r].real();
+                if (mag < 1e-300 || mag <= 1e-18 * std::sqrt(std::fabs(app * arr)) * 1e-3) {
+                    A[(size_t)p * n + r] = A[(size_t)r * n + p] = 0.0;
+                    continue;
+                }
+                const cd e = apr / mag;  // exp(i phi)
+                const double tau = (arr - app) / (2.0 * mag);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                const cd em = std::conj(e);
+                // W: W_pp = c, W_pr = s, W_rp = -s e^{-i phi}, W_rr = c e^{-i phi}
+                const cd Wpp = c, Wpr = s, Wrp = -s * em, Wrr = c * em;
+                for (int i = 0; i < n; ++i) {  // A <- A W
+                    const cd aip = A[(size_t)i * n + p], air = A[(size_t)i * n + r];
+                    A[(size_t)i * n + p] = aip * Wpp + air * Wrp;
+                    A[(size_t)i * n + r] = aip * Wpr + air * Wrr;
+                }
+                for (int j = 0; j < n; ++j) {  // A <- W^H A
+                    const cd apj = A[(size_t)p * n + j], arj = A[(size_t)r * n + j];
+                    A[(size_t)p * n + j] = std::conj(Wpp) * apj + std::conj(Wrp) * arj;
+                    A[(size_t)r * n + j] = std::conj(Wpr) * apj + std::conj(Wrr) * arj;
+                }
+                for (int i = 0; i < n; ++i) {  // V <- V W
+                    const cd vip = V[(size_t)i * n + p], vir = V[(size_t)i * n + r];
+                    V[(size_t)i * n + p] = vip * Wpp + vir * Wrp;
+                    V[(size_t)i * n + r] = vip * Wpr + vir * Wrr;
+                }
+                A[(size_t)p * n + r] = A[(size_t)r * n + p] = 0.0;
+                A[(size_t)p * n + p] = A[(size_t)p * n + p].real();
+                A[(size_t)r * n + r] = A[(size_t)r * n + r].real();
+            }
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int a, int b) { return A[(size_t)a * n + a].real() < A[(size_t)b * n + b].real(); });
+    std::vector<cd> Vs((size_t)n * n);
+    w.resize(n);
+    for (int j = 0; j < n; ++j) {
+        w[j] = A[(size_t)ord[j] * n + ord[j]].real();
+        for (int i = 0; i < n; ++i) Vs[(size_t)i * n + j] = V[(size_t)i * n + ord[j]];
+    }
+    V.swap(Vs);
+    return ok;
+}
+
+// K Q = M Q diag(lam), Q^H M Q = I; K, M Hermitian (row-major), M positive definite.
+// Returns 0 on success, 1 if M is not positive definite, 2 if Jacobi did not converge.
+static int gen_herm_eig(int n, const cd* K, const cd* M, std::vector<double>& lam, std::vector<cd>& Q) {
+    std::vector<cd> L((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            cd s = 0.5 * (M[(size_t)i * n + j] + std::conj(M[(size_t)j * n + i]));
+            for (int k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * std::conj(L[(size_t)j * n + k]);
+            if (i == j) {
+                if (!(s.real() > 0.0)) return 1;
+                L[(size_t)i * n + i] = std::sqrt(s.real());
+            } else {
+                L[(size_t)i * n + j] = s / L[(size_t)j * n + j];
+            }
+        }
+    // X = L^-1 Kh (Kh = Hermitian part of K)
+    std::vector<cd> X((size_t)n * n);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            cd s = 0.5 * (K[(size_t)i * n + c] + std::conj(K[(size_t)c * n + i]));
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * X[(size_t)k * n + c];
+            X[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        }
+    // Cm = X L^-H = (L^-1 X^H)^H
+    std::vector<cd> Y((size_t)n * n);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            cd s = std::conj(X[(size_t)c * n + i]);
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * Y[(size_t)k * n + c];
+            Y[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        }
+    std::vector<cd> Cm((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Cm[(size_t)i * n + j] = std::conj(Y[(size_t)j * n + i]);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) {
+            const cd h = 0.5 * (Cm[(size_t)i * n + j] + std::conj(Cm[(size_t)j * n + i]));
+            Cm[(size_t)i * n + j] = h;
+            Cm[(size_t)j * n + i] = std::conj(h);
+        }
+    std::vector<cd> W;
+    const bool ok = herm_jacobi(n, Cm, lam, W);
+    // Q = L^-H W  (back substitution with L^H)
+    Q.assign((size_t)n * n, cd(0, 0));
+    for (int c = 0; c < n; ++c)
+        for (int i = n - 1; i >= 0; --i) {
+            cd s = W[(size_t)i * n + c];
+            for (int k = i + 1; k < n; ++k) s -= std::conj(L[(size_t)k * n + i]) * Q[(size_t)k * n + c];
+            Q[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        }
+    return ok ? 0 : 2;
+}
+
+// ====================================================================
+// Start vectors (Section 3.3: "unit vectors corresponding to the lowest
+// frequencies"): Fourier unit vectors at the bins of smallest |xi + k|,
+// polarised along the eigenvectors of the reference acoustic tensor
+// P0(xi + k), the q of lowest reference eigenvalue.
+// ====================================================================
+struct StartEntry {
+    long long idx;  // element index comp*V + voxel
+    double2 val;
+};
+
+static std::vector<StartEntry> start_vectors(const bloch_plan* pl, const double k[3], int q, bool gamma) {
+    const int N[3] = {pl->Nx, pl->Ny, pl->Nz};
+    int lo[3], hi[3];
+    std::vector<int> mlist[3];
+    for (int a = 0; a < 3; ++a) {
+        const double kap = k[a] * pl->L[a] / (2.0 * M_PI);
+        const int c = (int)std::lround(-kap);
+        if (N[a] <= 13) {
+            for (int m = 0; m < N[a]; ++m) mlist[a].push_back(m);
+        } else {
+            for (int d = -6; d <= 6; ++d) {
+                const int mt = c + d;   // integer frequency
+                const int half = (N[a] + 1) / 2;
+                if (mt >= half || mt < half - N[a]) continue;
+                mlist[a].push_back(mt >= 0 ? mt : mt + N[a]);
+            }
+        }
+        (void)lo;
+        (void)hi;
+    }
+    struct Cand {
+        double q2;
+        long long v;
+        double qv[3];
+    };
+    std::vector<Cand> cands;
+    const double* xi = pl->xi_host.data();
+    for (int mz : mlist[2])
+        for (int my : mlist[1])
+            for (int mx : mlist[0]) {
+                Cand c;
+                c.qv[0] = xi[mx] + k[0];
+                c.qv[1] = xi[pl->Nx + my] + k[1];
+                c.qv[2] = xi[pl->Nx + pl->Ny + mz] + k[2];
+                c.q2 = c.qv[0] * c.qv[0] + c.qv[1] * c.qv[1] + c.qv[2] * c.qv[2];
+                c.v = ((long long)mz * pl->Ny + my) * pl->Nx + mx;
+                if (gamma && c.q2 == 0.0) continue;
+                cands.push_back(c);
+            }
+    std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) {
+        return a.q2 < b.q2 || (a.q2 == b.q2 && a.v < b.v);
+    });
+    const size_t nc = std::min(cands.size(), (size_t)std::max(8 * q, 8));
+    struct Item {
+        double mu;
+        long long v;
+        int a;
+        double w[3];
+    };
+    std::vector<Item> items;
+    static const int vi[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    for (size_t c = 0; c < nc; ++c) {
+        const double* qv = cands[c].qv;
+        std::vector<cd> P(9);
+        for (int i = 0; i < 3; ++i)
+            for (int kk = 0; kk < 3; ++kk) {
+                double s = 0;
+                for (int j = 0; j < 3; ++j)
+                    for (int l = 0; l < 3; ++l) s += pl->C0V[vi[i][j] * 6 + vi[kk][l]] * qv[j] * qv[l];
+                P[i * 3 + kk] = s;
+            }
+        std::vector<double> w;
+        std::vector<cd> Vv;
+        herm_jacobi(3, P, w, Vv);
+        for (int a = 0; a < 3; ++a) {
+            Item it;
+            it.mu = w[a];
+            it.v = cands[c].v;
+            it.a = a;
+            for (int i = 0; i < 3; ++i) it.w[i] = Vv[i * 3 + a].real();
+            items.push_back(it);
+        }
+    }
+    std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
+        if (x.mu != y.mu) return x.mu < y.mu;
+        if (x.v != y.v) return x.v < y.v;
+        return x.a < y.a;
+    });
+    std::vector<StartEntry> out;
+    const int nq = (int)std::min<size_t>(items.size(), (size_t)q);
+    for (int p = 0; p < nq; ++p)
+        for (int c = 0; c < 3; ++c) {
+            StartEntry e;
+            e.idx = (long long)p * 3 * pl->V + (long long)c * pl->V + items[p].v;
+            e.val = make_double2(items[p].w[c], 0.0);
+            out.push_back(e);
+        }
+    return out;
+}
+
+// ====================================================================
+// Subspace iteration (Algorithm 1), batched over wave vectors
+// ====================================================================
+template <typename T>
+struct Subspace {
+    using C = cplx_t<T>;
+    bloch_plan* pl;
+    int n, q, B;
+    long long n3;
+    bool fp64res;     // FP32 fields with an FP64 residual refinement phase
+    bool uniform;
+    double rho_s;
+    double tol_eig, tol_lin;
+    int max_outer, max_cg;
+    const std::vector<std::array<double, 3>>* klist;
+    double* omega_out;
+    void* vecs_out;
+    int n_bands;
+    bloch_stats* st;
+    bool any_unconverged = false;
+
+    C *U = nullptr, *Ub = nullptr, *KU = nullptr, *R = nullptr, *MU = nullptr, *MUb = nullptr;
+    double *d_part = nullptr, *d_scal = nullptr;
+    double2 *d_gpart = nullptr, *d_G = nullptr, *d_Q = nullptr, *d_val = nullptr;
+    long long* d_idx = nullptr;
+    double2 *U64 = nullptr, *KU64 = nullptr, *MU64 = nullptr;
+    int gblk = 0, dblk = 0;
+
+    struct Slot {
+        int kidx = -1;
+        double k[3];
+        bool gamma = false;
+        int n_eff = 0;
+        int sweeps = 0;
+        int phase = 0;
+        std::vector<double> lam, lam_prev, unorm2;
+        double err1 = INFINITY, err2 = INFINITY, err2_prev = INFINITY;
+        bool has_prev = false;
+    };
+    std::vector<Slot> slots;
+    int nact = 0;
+    size_t next_k = 0;
+    std::vector<int> order;   // k indices needing an iterative solve
+
+    std::vector<void*> allocs;
+    ~Subspace() {
+        cudaStreamSynchronize(pl->stream);
+        for (void* p : allocs) cudaFree(p);
+    }
+    template <typename X>
+    bloch_status alloc(X** p, size_t n_el) {
+        cudaError_t e = cudaMalloc((void**)p, n_el * sizeof(X));
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (eigensolver block)");
+        allocs.push_back(*p);
+        return BLOCH_OK;
+    }
+
+    C* vec(C* base, int slot, int i = 0) const { return base + ((size_t)slot * q + i) * n3; }
+
+    bloch_status setup() {
+        bloch_status s;
+        const size_t blk = (size_t)B * q * n3;
+        if ((s = alloc(&U, blk)) || (s = alloc(&Ub, blk)) || (s = alloc(&KU, blk)) || (s = alloc(&R, blk))) return s;
+        if (!uniform) {
+            if ((s = alloc(&MU, blk)) || (s = alloc(&MUb, blk))) return s;
+        }
+        dblk = (int)std::max(1LL, std::min<long long>((n3 + 255) / 256, std::max(1, 2048 / std::max(1, B * q))));
+        gblk = (int)std::max(1LL, std::min<long long>((n3 + kGramChunk - 1) / kGramChunk, std::max(1, 1024 / B)));
+        if ((s = alloc(&d_part, (size_t)B * q * dblk * 3)) || (s = alloc(&d_scal, (size_t)B * q * 2)) ||
+            (s = alloc(&d_gpart, (size_t)B * gblk * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
+            (s = alloc(&d_Q, (size_t)B * q * q)) || (s = alloc(&d_idx, (size_t)3 * q)) ||
+            (s = alloc(&d_val, (size_t)3 * q)))
+            return s;
+        if (fp64res) {
+            if ((s = alloc(&U64, (size_t)q * n3)) || (s = alloc(&KU64, (size_t)q * n3))) return s;
+            if (!uniform && (s = alloc(&MU64, (size_t)q * n3))) return s;
+            if ((s = ensure_ws<double>(pl, q)) != BLOCH_OK) return s;
+        }
+        if ((s = ensure_cg<T>(pl, B * q)) != BLOCH_OK) return s;
+        slots.assign(B, Slot());
+        return BLOCH_OK;
+    }
+
+    bloch_status set_k_range(int first, int count) {
+        std::vector<double> kv((size_t)count * q * 3);
+        for (int s = 0; s < count; ++s)
+            for (int i = 0; i < q; ++i)
+                for (int a = 0; a < 3; ++a) kv[((size_t)s * q + i) * 3 + a] = slots[first + s].k[a];
+        return set_k<T>(pl, count * q, kv.data());
+    }
+
+    bloch_status init_slot(int s, int kidx) {
+        Slot& sl = slots[s];
+        sl = Slot();
+        sl.kidx = kidx;
+        for (int a = 0; a < 3; ++a) sl.k[a] = (*klist)[kidx][a];
+        sl.gamma = sl.k[0] == 0.0 && sl.k[1] == 0.0 && sl.k[2] == 0.0;
+        sl.n_eff = sl.gamma ? n_bands - 3 : n_bands;
+        sl.phase = 0;
+        std::vector<StartEntry> se = start_vectors(pl, sl.k, q, sl.gamma);
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(vec(U, s), 0, sizeof(C) * q * n3, pl->stream));
+        std::vector<long long> idx(se.size());
+        std::vector<double2> val(se.size());
+        for (size_t i = 0; i < se.size(); ++i) {
+            idx[i] = se[i].idx + (long long)s * q * n3;
+            val[i] = se[i].val;
+        }
+        if (!se.empty()) {
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_idx, idx.data(), sizeof(long long) * idx.size(),
+                                                 cudaMemcpyHostToDevice, pl->stream));
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_val, val.data(), sizeof(double2) * val.size(),
+                                                 cudaMemcpyHostToDevice, pl->stream));
+            ++pl->launches;
+            k_scatter<T><<<((int)se.size() + 127) / 128, 128, 0, pl->stream>>>(U, d_idx, d_val, (int)se.size());
+            // the scatter buffers are reused by the next init: wait for the copies
+            BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        }
+        return BLOCH_OK;
+    }
+
+    // Rayleigh quotients and residuals of slots [first, first+count)
+    template <typename TK>
+    bloch_status residual_run(int first, int count, const cplx_t<TK>* Uk, const cplx_t<TK>* KUk,
+                              const cplx_t<TK>* MUk) {
+        const int nv = count * q;
+        dim3 gr(dblk, nv);
+        ++pl->launches;
+        k_rq_dots<TK><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, n3, d_part);
+        std::vector<double> part((size_t)nv * dblk * 3);
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
+                                             cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        std::vector<double> ukv(nv), umu(nv), kk(nv), inv(nv);
+        for (int v = 0; v < nv; ++v) {
+            double a = 0, b = 0, c = 0;
+            for (int j = 0; j < dblk; ++j) {
+                a += part[((size_t)v * dblk + j) * 3 + 0];
+                b += part[((size_t)v * dblk + j) * 3 + 1];
+                c += part[((size_t)v * dblk + j) * 3 + 2];
+            }
+            ukv[v] = a;
+            umu[v] = b;
+            kk[v] = c;
+            const double lam = (b > 0) ? a / b : 0.0;
+            inv[v] = lam > 0 ? 1.0 / lam : 0.0;
+        }
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(d_scal, inv.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, pl->stream));
+        ++pl->launches;
+        k_residual<TK, T><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, d_scal, vec(R, first), n3, d_part);
+        std::vector<double> rp((size_t)nv * dblk);
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(rp.data(), d_part, sizeof(double) * rp.size(), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        for (int s = 0; s < count; ++s) {
+            Slot& sl = slots[first + s];
+            sl.lam_prev = sl.lam;
+            sl.lam.assign(q, 0.0);
+            sl.unorm2.assign(q, 0.0);
+            double e2 = 0;
+            for (int i = 0; i < q; ++i) {
+                const int v = s * q + i;
+                double r2 = 0;
+                for (int j = 0; j < dblk; ++j) r2 += rp[(size_t)v * dblk + j];
+                const double lam = umu[v] > 0 ? ukv[v] / umu[v] : 0.0;
+                sl.lam[i] = lam;
+                sl.unorm2[i] = umu[v];
+                if (i < sl.n_eff && kk[v] > 0) e2 = std::max(e2, lam * std::sqrt(r2) / std::sqrt(kk[v]));
+            }
+            sl.err2_prev = sl.err2;
+            sl.err2 = e2;
+            if (sl.has_prev) {
+                double num = 0, den = 0;
+                for (int i = 0; i < sl.n_eff; ++i) {
+                    num += (sl.lam[i] - sl.lam_prev[i]) * (sl.lam[i] - sl.lam_prev[i]);
+                    den += sl.lam_prev[i] * sl.lam_prev[i];
+                }
+                sl.err1 = den > 0 ? std::sqrt(num / den) : 0.0;
+            }
+            sl.has_prev = true;
+            st->k_applies += q;
+        }
+        return BLOCH_OK;
+    }
+
+    bloch_status residual_step(int first, int count) {
+        bloch_status s;
+        int i = first;
+        while (i < first + count) {
+            if (slots[i].phase == 0 || !fp64res) {
+                int j = i;
+                while (j < first + count && (slots[j].phase == 0 || !fp64res)) ++j;
+                if ((s = set_k_range(i, j - i)) != BLOCH_OK) return s;
+                launch_K<T>(pl, (j - i) * q, vec(U, i), vec(KU, i), T(1));
+                if (!uniform) launch_M<T>(pl, (j - i) * q, vec(U, i), vec(MU, i), T(1));
+                if ((s = residual_run<T>(i, j - i, vec(U, i), vec(KU, i), uniform ? nullptr : vec(MU, i))) != BLOCH_OK)
+                    return s;
+                i = j;
+            } else {
+                // FP64 refinement: residual of the FP32 block from an FP64 operator apply
+                const size_t ne = (size_t)q * n3;
+                ++pl->launches;
+                k_convert<T, double><<<1024, 256, 0, pl->stream>>>(vec(U, i), U64, ne);
+                std::vector<double> kv((size_t)q * 3);
+                for (int v = 0; v < q; ++v)
+                    for (int a = 0; a < 3; ++a) kv[(size_t)v * 3 + a] = slots[i].k[a];
+                if ((s = set_k<double>(pl, q, kv.data())) != BLOCH_OK) return s;
+                launch_K<double>(pl, q, U64, KU64, 1.0);
+                if (!uniform) launch_M<double>(pl, q, U64, MU64, 1.0);
+                if ((s = residual_run<double>(i, 1, U64, KU64, uniform ? nullptr : MU64)) != BLOCH_OK) return s;
+                ++i;
+            }
+        }
+        BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        return BLOCH_OK;
+    }
+
+    void finalize_slot(int s, bool converged) {
+        Slot& sl = slots[s];
+        const double lam_scale = pl->Kscale / pl->rho_ref;
+        double* om = omega_out + (size_t)sl.kidx * n_bands;
+        int b = 0;
+        if (sl.gamma)
+            for (; b < std::min(3, n_bands); ++b) om[b] = 0.0;
+        for (int i = 0; i < sl.n_eff; ++i) om[b + i] = std::sqrt(std::max(sl.lam[i], 0.0) * lam_scale);
+        st->outer_iterations += sl.sweeps;
+        st->max_rel_residual = std::max(st->max_rel_residual, sl.err2);
+        if (!converged) any_unconverged = true;
+        if (vecs_out) {
+            C* out = (C*)vecs_out + (size_t)sl.kidx * n_bands * n3;
+            if (sl.gamma) {
+                cudaMemsetAsync(out, 0, sizeof(C) * std::min(3, n_bands) * n3, pl->stream);
+                std::vector<long long> idx;
+                std::vector<double2> val;
+                const double nv = 1.0 / std::sqrt(pl->rho_ref * rho_s);
+                for (int c = 0; c < std::min(3, n_bands); ++c) {
+                    idx.push_back((long long)sl.kidx * n_bands * n3 + (long long)c * n3 + (long long)c * pl->V);
+                    val.push_back(make_double2(nv, 0.0));
+                }
+                cudaMemcpyAsync(d_idx, idx.data(), sizeof(long long) * idx.size(), cudaMemcpyHostToDevice, pl->stream);
+                cudaMemcpyAsync(d_val, val.data(), sizeof(double2) * val.size(), cudaMemcpyHostToDevice, pl->stream);
+                ++pl->launches;
+                k_scatter<T><<<1, 32, 0, pl->stream>>>((C*)vecs_out, d_idx, d_val, (int)idx.size());
+                cudaStreamSynchronize(pl->stream);
+            }
+            if (sl.n_eff > 0) {
+                std::vector<double> sc(sl.n_eff);
+                for (int i = 0; i < sl.n_eff; ++i)
+                    sc[i] = sl.unorm2[i] > 0 ? 1.0 / std::sqrt(pl->rho_ref * sl.unorm2[i]) : 0.0;
+                cudaMemcpyAsync(d_scal, sc.data(), sizeof(double) * sl.n_eff, cudaMemcpyHostToDevice, pl->stream);
+                dim3 gr(dblk, sl.n_eff);
+                ++pl->launches;
+                k_scale_vecs<T, T><<<gr, 256, 0, pl->stream>>>(vec(U, s), out + (size_t)b * n3, d_scal, n3);
+                cudaStreamSynchronize(pl->stream);
+            }
+        }
+    }
+
+    // move slot `from` into slot `to` (device blocks U, R, MU and host state)
+    bloch_status move_slot(int from, int to) {
+        const size_t bytes = sizeof(C) * q * n3;
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(U, to), vec(U, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(R, to), vec(R, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        if (!uniform)
+            BLOCH_CUDA_CHECK_RET(
+                cudaMemcpyAsync(vec(MU, to), vec(MU, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        slots[to] = slots[from];
+        return BLOCH_OK;
+    }
+
+    bloch_status run() {
+        bloch_status s;
+        // fill the slots
+        nact = 0;
+        while (nact < B && next_k < order.size()) {
+            if ((s = init_slot(nact, order[next_k++])) != BLOCH_OK) return s;
+            ++nact;
+        }
+        if (nact == 0) return BLOCH_OK;
+        if ((s = residual_step(0, nact)) != BLOCH_OK) return s;
+        const double tol = tol_eig;
+        while (nact > 0) {
+            // convergence / phase decisions on the residuals just computed
+            std::vector<int> done;
+            for (int i = 0; i < nact; ++i) {
+                Slot& sl = slots[i];
+                const bool test = sl.err1 <= tol && sl.err2 <= 10.0 * tol;
+                if (fp64res && sl.phase == 0) {
+                    const bool stall = sl.sweeps >= 3 && sl.err2 > 0.7 * sl.err2_prev;
+                    if (test || stall || sl.err2 <= 1e-4) sl.phase = 1;
+                    if (sl.sweeps >= max_outer) done.push_back(i);
+                } else if (test || sl.sweeps >= max_outer) {
+                    done.push_back(i);
+                }
+            }
+            if (!done.empty()) {
+                std::vector<int> fresh;
+                for (int i : done) finalize_slot(i, slots[i].err1 <= tol && slots[i].err2 <= 10.0 * tol);
+                // refill from the queue, then compact
+                std::vector<int> holes = done;
+                std::vector<char> is_hole(nact, 0);
+                for (int h : holes) is_hole[h] = 1;
+                for (int h : holes) {
+                    if (next_k < order.size()) {
+                        if ((s = init_slot(h, order[next_k++])) != BLOCH_OK) return s;
+                        is_hole[h] = 0;
+                        fresh.push_back(h);
+                    }
+                }
+                int last = nact - 1;
+                for (int h = 0; h < nact; ++h) {
+                    if (!is_hole[h]) continue;
+                    while (last > h && is_hole[last]) --last;
+                    if (last <= h) break;
+                    // move last active into h
+                    for (int& f : fresh)
+                        if (f == last) f = h;
+                    if ((s = move_slot(last, h)) != BLOCH_OK) return s;
+                    is_hole[h] = 0;
+                    is_hole[last] = 1;
+                }
+                int na = 0;
+                for (int h = 0; h < nact; ++h)
+                    if (!is_hole[h]) na = h + 1;
+                nact = na;
+                for (int f : fresh)
+                    if ((s = residual_step(f, 1)) != BLOCH_OK) return s;
+                if (nact == 0) break;
+            }
+            // inverse step on all active slots: delta = A^-1 R
+            if ((s = set_k_range(0, nact)) != BLOCH_OK) return s;
+            long long cg_it = 0;
+            s = pcg_run<T>(pl, nact * q, R, Ub, 1.0, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
+            st->cg_iterations += cg_it;
+            st->k_applies += cg_it;
+            st->linear_solves += (long long)nact * q;
+            if (s != BLOCH_OK && s != BLOCH_ENOTCONV_CG) return s;
+            // U_bar = delta + U / lam
+            std::vector<double> inv((size_t)nact * q);
+            for (int i = 0; i < nact; ++i)
+                for (int j = 0; j < q; ++j) inv[(size_t)i * q + j] = slots[i].lam[j] > 0 ? 1.0 / slots[i].lam[j] : 0.0;
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_scal, inv.data(), sizeof(double) * inv.size(),
+                                                 cudaMemcpyHostToDevice, pl->stream));
+            dim3 gv(dblk, nact * q);
+            ++pl->launches;
+            k_add_scaled<T><<<gv, 256, 0, pl->stream>>>(Ub, U, d_scal, n3);
+            // Kn = M U - r_cg (into KU), Mn = M U_bar
+            const size_t ne = (size_t)nact * q * n3;
+            ++pl->launches;
+            k_kn<T><<<4096, 256, 0, pl->stream>>>(U, uniform ? nullptr : MU, rho_s, ws_of<T>(pl).r, KU, ne);
+            if (!uniform) launch_M<T>(pl, nact * q, Ub, MUb, T(1));
+            // projections K = Ub^H Kn, M = Ub^H Mn
+            dim3 gg(gblk, nact);
+            const int npair = q * q;
+            ++pl->launches;
+            k_gram<T><<<gg, 256, 0, pl->stream>>>(Ub, KU, q, n3, d_gpart);
+            ++pl->launches;
+            k_gram_final<<<dim3((npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair, d_G);
+            ++pl->launches;
+            k_gram<T><<<gg, 256, 0, pl->stream>>>(Ub, uniform ? Ub : MUb, q, n3, d_gpart);
+            ++pl->launches;
+            k_gram_final<<<dim3((npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair,
+                                                                                   d_G + (size_t)nact * npair);
+            std::vector<double2> G((size_t)2 * nact * npair);
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(G.data(), d_G, sizeof(double2) * G.size(), cudaMemcpyDeviceToHost,
+                                                 pl->stream));
+            BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+            std::vector<double2> Qh((size_t)nact * npair);
+            for (int i = 0; i < nact; ++i) {
+                std::vector<cd> Km(npair), Mm(npair), Qm;
+                const double ms = uniform ? rho_s : 1.0;
+                for (int t = 0; t < npair; ++t) {
+                    const double2 a = G[(size_t)i * npair + t], b = G[(size_t)(nact + i) * npair + t];
+                    Km[t] = cd(a.x, a.y);
+                    Mm[t] = cd(b.x, b.y) * ms;
+                }
+                std::vector<double> lam;
+                const int rc = gen_herm_eig(q, Km.data(), Mm.data(), lam, Qm);
+                if (rc == 1) return set_error(BLOCH_ENOTCONV_EIG, "projected mass matrix lost definiteness");
+                for (int t = 0; t < npair; ++t) Qh[(size_t)i * npair + t] = make_double2(Qm[t].real(), Qm[t].imag());
+                slots[i].sweeps += 1;
+            }
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_Q, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice,
+                                                 pl->stream));
+            dim3 gb((unsigned)std::min<long long>((n3 + 127) / 128, 8192), nact);
+            ++pl->launches;
+            k_basis<T><<<gb, 128, 0, pl->stream>>>(Ub, U, d_Q, q, n3);
+            BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+            if ((s = residual_step(0, nact)) != BLOCH_OK) return s;
+        }
+        return BLOCH_OK;
+    }
+};
+
+template <typename T>
+static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<double, 3>>& ks, int n_bands,
+                                 double* omega_out, void* vecs_out, bloch_stats* st, bool fp64res) {
+    Subspace<T> S;
+    S.pl = pl;
+    S.n3 = 3 * pl->V;
+    S.n_bands = n_bands;
+    S.n = n_bands;
+    const int qa = std::min(2 * n_bands, n_bands + 8);
+    S.q = pl->opt.block > 0 ? pl->opt.block : qa;
+    S.q = std::max(S.q, n_bands + 1);
+    if (S.q > kQMax) return set_error(BLOCH_EUNSUPPORTED, "block size above 32 vectors is not supported");
+    if ((long long)S.q > 3 * pl->V - 3) return set_error(BLOCH_EINVAL, "block larger than the problem");
+    S.fp64res = fp64res;
+    S.uniform = pl->uniform_rho;
+    S.rho_s = pl->uniform_rho ? pl->rho_uniform_scaled : 1.0;
+    S.tol_eig = pl->opt.tol_eig;
+    S.tol_lin = pl->opt.tol_lin;
+    if (std::is_same<T, float>::value) S.tol_lin = std::max(S.tol_lin, 3e-6);
+    S.max_outer = pl->opt.max_outer;
+    S.max_cg = pl->opt.max_cg;
+    S.klist = &ks;
+    S.omega_out = omega_out;
+    S.vecs_out = vecs_out;
+    S.st = st;
+    for (size_t i = 0; i < ks.size(); ++i) {
+        const bool gamma = ks[i][0] == 0.0 && ks[i][1] == 0.0 && ks[i][2] == 0.0;
+        if (gamma && !pl->uniform_rho)
+            return set_error(BLOCH_EUNSUPPORTED, "k = 0 with a non-uniform density is not supported");
+        if (gamma && n_bands <= 3) {
+            for (int b = 0; b < n_bands; ++b) omega_out[i * n_bands + b] = 0.0;
+            continue;
+        }
+        S.order.push_back((int)i);
+    }
+    // slots: from the options or from free memory
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const size_t blk = (size_t)S.q * S.n3 * sizeof(cplx_t<T>);
+    const size_t per_slot = blk * (S.uniform ? 9 : 11) + 64 * 1024;
+    long long Bmax = std::max<long long>(1, (long long)(0.6 * (double)freeb / (double)per_slot));
+    Bmax = std::min<long long>(Bmax, 10922 / S.q);
+    int B = pl->opt.k_batch > 0 ? pl->opt.k_batch : (int)Bmax;
+    B = std::max(1, std::min<int>(B, (int)std::max<size_t>(1, S.order.size())));
+    S.B = B;
+    if (S.order.empty()) return BLOCH_OK;
+    bloch_status s = S.setup();
+    if (s != BLOCH_OK) return s;
+    s = S.run();
+    if (s != BLOCH_OK) return s;
+    if (S.any_unconverged) return set_error(BLOCH_ENOTCONV_EIG, "eigensolver reached its sweep cap");
+    return BLOCH_OK;
+}
+
+}  // namespace bloch
+
+using namespace bloch;
+
+bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_list, int n_bands, double* omega_out,
+                                    void* vecs_out, bloch_stats* stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<std::array<double, 3>> ks(n_k);
+    for (int i = 0; i < n_k; ++i)
+        for (int a = 0; a < 3; ++a) {
+            ks[i][a] = k_list[3 * i + a];
+            if (!std::isfinite(ks[i][a])) return set_error(BLOCH_ENONFINITE, "k_list has a non-finite entry");
+        }
+    bloch_stats st;
+    std::memset(&st, 0, sizeof(st));
+    bloch_status s;
+    if (pl->opt.method == BLOCH_SUBSPACE) {
+        if (pl->opt.precision == BLOCH_FP32)
+            s = run_subspace<float>(pl, ks, n_bands, omega_out, vecs_out, &st, true);
+        else
+            s = run_subspace<double>(pl, ks, n_bands, omega_out, vecs_out, &st, false);
+    } else {
+        s = set_error(BLOCH_EUNSUPPORTED, "Lanczos method not available in this build");
+    }
+    cudaStreamSynchronize(pl->stream);
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    pl->last_stats = st;
+    if (stats) *stats = st;
+    return s;
+}
+
+extern "C" bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, double* lam, double* Q) {
+    if (n < 1 || !K || !M || !lam || !Q) return set_error(BLOCH_EINVAL, "invalid arguments");
+    std::vector<cd> Kc((size_t)n * n), Mc((size_t)n * n), Qc;
+    for (size_t i = 0; i < (size_t)n * n; ++i) {
+        Kc[i] = cd(K[2 * i], K[2 * i + 1]);
+        Mc[i] = cd(M[2 * i], M[2 * i + 1]);
+    }
+    std::vector<double> w;
+    const int rc = gen_herm_eig(n, Kc.data(), Mc.data(), w, Qc);
+    if (rc == 1) return set_error(BLOCH_EINVAL, "M is not positive definite");
+    for (int i = 0; i < n; ++i) lam[i] = w[i];
+    for (size_t i = 0; i < (size_t)n * n; ++i) {
+        Q[2 * i] = Qc[i].real();
+        Q[2 * i + 1] = Qc[i].imag();
+    }
+    return rc == 0 ? BLOCH_OK : set_error(BLOCH_ENOTCONV_EIG, "Jacobi sweeps did not converge");
+}

@@ -1,0 +1,677 @@
+// Plan creation, operator launchers, batched PCG and the C ABI entry points
+// for the operators (Section 3.2 Eqs. hatA/hatM, Section 3.3 Algorithm 2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace bloch {
+
+static thread_local std::string g_last_error;
+
+bloch_status set_error(bloch_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+bloch_status set_cuda_error(cudaError_t e, const char* what) {
+    g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? BLOCH_ENOMEM : BLOCH_ECUDA;
+}
+
+template <> Workspace<float>& ws_of<float>(bloch_plan* pl) { return pl->ws_f; }
+template <> Workspace<double>& ws_of<double>(bloch_plan* pl) { return pl->ws_d; }
+template <> const Geo& geo_of<float>(const bloch_plan* pl) { return pl->geo_f; }
+template <> const Geo& geo_of<double>(const bloch_plan* pl) { return pl->geo_d; }
+template <typename T> static const TileCfg& tile_of(const bloch_plan* pl);
+template <> const TileCfg& tile_of<float>(const bloch_plan* pl) { return pl->tile_f; }
+template <> const TileCfg& tile_of<double>(const bloch_plan* pl) { return pl->tile_d; }
+template <typename T> static const cplx_t<T>* tw_of(const bloch_plan* pl, int axis);
+template <> const float2* tw_of<float>(const bloch_plan* pl, int axis) { return pl->d_twf[axis]; }
+template <> const double2* tw_of<double>(const bloch_plan* pl, int axis) { return pl->d_twd[axis]; }
+template <typename T> static const T* ctab_of(const bloch_plan* pl);
+template <> const float* ctab_of<float>(const bloch_plan* pl) { return pl->d_Cf; }
+template <> const double* ctab_of<double>(const bloch_plan* pl) { return pl->d_Cd; }
+template <typename T> static const T* rtab_of(const bloch_plan* pl);
+template <> const float* rtab_of<float>(const bloch_plan* pl) { return pl->d_rf; }
+template <> const double* rtab_of<double>(const bloch_plan* pl) { return pl->d_rd; }
+
+// ------------------------------------------------------------ host helpers
+static bool factor_ok(int n) {
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Radix schedule: power-of-two part in as few stages as possible (each at most
+// max_r), then the odd factors 3, 5, 7.
+static AxisPlan make_axis(int N, int max_log2) {
+    AxisPlan ap{};
+    ap.N = N;
+    int n = N, l2 = 0;
+    while (n % 2 == 0) {
+        n /= 2;
+        ++l2;
+    }
+    int nst2 = (l2 + max_log2 - 1) / max_log2;
+    for (int s = 0; s < nst2; ++s) {
+        const int bits = l2 / (nst2 - s);
+        ap.radix[ap.nst++] = 1 << bits;
+        l2 -= bits;
+    }
+    for (int p : {3, 5, 7})
+        while (n % p == 0) {
+            ap.radix[ap.nst++] = p;
+            n /= p;
+        }
+    return ap;
+}
+
+static int choose_P(int N, int bufs, size_t elem, size_t budget, long long npen, int pmax) {
+    int P = pmax;
+    while (P > 1 && (size_t)bufs * N * P * elem + (size_t)(N + 1) * elem > budget) P >>= 1;
+    while (P > 1 && (long long)(P / 2) >= npen) P >>= 1;
+    return P;
+}
+
+template <typename T>
+static TileCfg make_tiles(int Nx, int Ny, int Nz) {
+    TileCfg t{};
+    const size_t el = sizeof(cplx_t<T>);
+    auto pad = [&](int N) { return (size_t)((N + 1) & ~1) * el; };
+    t.Pz5 = choose_P(Nz, 5, el, 96 * 1024, (long long)Nx * Ny, 32);
+    t.Py2 = choose_P(Ny, 2, el, 64 * 1024, (long long)Nx * Nz, 32);
+    t.Pz2 = choose_P(Nz, 2, el, 64 * 1024, (long long)Nx * Ny, 32);
+    t.Px7 = choose_P(Nx, 7, el, 96 * 1024, (long long)Ny * Nz, 16);
+    t.Px4 = choose_P(Nx, 4, el, 64 * 1024, (long long)Ny * Nz, 16);
+    t.smem_z5 = pad(Nz) + (size_t)5 * Nz * t.Pz5 * el;
+    t.smem_y2 = pad(Ny) + (size_t)2 * Ny * t.Py2 * el;
+    t.smem_z2 = pad(Nz) + (size_t)2 * Nz * t.Pz2 * el;
+    t.smem_x7 = pad(Nx) + (size_t)7 * Nx * t.Px7 * el;
+    t.smem_x4 = pad(Nx) + (size_t)4 * Nx * t.Px4 * el;
+    return t;
+}
+
+template <typename T>
+static cudaError_t set_smem_attrs() {
+    const int mx = 227 * 1024;
+    cudaError_t e;
+#define SETA(f)                                                                     \
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);   \
+    if (e != cudaSuccess) return e;
+    SETA(k_pass_z_strain<T>);
+    SETA((k_pass_axis<T, +1, 1>));
+    SETA((k_pass_axis<T, -1, 1>));
+    SETA((k_pass_axis<T, +1, 2>));
+    SETA((k_pass_axis<T, -1, 2>));
+    SETA(k_pass_x_stress<T>);
+    SETA(k_pass_z_div<T>);
+    SETA(k_pass_x_rho<T>);
+#undef SETA
+    return cudaSuccess;
+}
+
+int vec_blocks(const bloch_plan* pl, int nb) {
+    long long b = (pl->V + 255) / 256;
+    long long cap = std::max(1, 4096 / std::max(nb, 1));
+    return (int)std::max(1LL, std::min(b, cap));
+}
+
+template <typename T>
+static cudaError_t dmalloc(T** p, size_t n, size_t* acc) {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaSuccess && acc) *acc += n * sizeof(T);
+    return e;
+}
+
+// ------------------------------------------------------------ workspaces
+template <typename T>
+bloch_status ensure_ws(bloch_plan* pl, int nb) {
+    Workspace<T>& w = ws_of<T>(pl);
+    if (nb <= w.cap) return BLOCH_OK;
+    cudaStreamSynchronize(pl->stream);
+    const int S = pl->Nx + pl->Ny + pl->Nz;
+    if (w.E) pl->device_bytes -= (size_t)w.cap * (6 * pl->V * sizeof(cplx_t<T>) + S * sizeof(T) + 3 * sizeof(double));
+    cudaFree(w.E);
+    cudaFree(w.qtab);
+    cudaFree(w.kvec);
+    w.E = nullptr;
+    w.qtab = nullptr;
+    w.kvec = nullptr;
+    w.cap = 0;
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.E, (size_t)6 * pl->V * nb, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.qtab, (size_t)S * nb, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.kvec, (size_t)3 * nb, &pl->device_bytes));
+    w.cap = nb;
+    return BLOCH_OK;
+}
+
+template <typename T>
+bloch_status ensure_cg(bloch_plan* pl, int nb) {
+    bloch_status st = ensure_ws<T>(pl, nb);
+    if (st != BLOCH_OK) return st;
+    Workspace<T>& w = ws_of<T>(pl);
+    if (nb <= w.cg_cap) return BLOCH_OK;
+    cudaStreamSynchronize(pl->stream);
+    const size_t vec = (size_t)3 * pl->V * sizeof(cplx_t<T>);
+    if (w.r) pl->device_bytes -= (size_t)w.cg_cap * (3 * vec + pl->nblk_max * (3 * sizeof(double) + sizeof(double2)) +
+                                                     sizeof(double2) + sizeof(CGSys));
+    cudaFree(w.r);
+    cudaFree(w.p);
+    cudaFree(w.Ap);
+    cudaFree(w.part3);
+    cudaFree(w.part2);
+    cudaFree(w.dots);
+    cudaFree(w.sys);
+    w.r = w.p = w.Ap = nullptr;
+    w.part3 = nullptr;
+    w.part2 = w.dots = nullptr;
+    w.sys = nullptr;
+    w.cg_cap = 0;
+    const size_t n = (size_t)3 * pl->V * nb;
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.r, n, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.p, n, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.Ap, n, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.part3, (size_t)nb * pl->nblk_max * 3, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.part2, (size_t)nb * pl->nblk_max, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.dots, (size_t)nb, &pl->device_bytes));
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.sys, (size_t)nb, &pl->device_bytes));
+    w.cg_cap = nb;
+    return BLOCH_OK;
+}
+
+template <typename T>
+bloch_status set_k(bloch_plan* pl, int nb, const double* k_host) {
+    bloch_status st = ensure_ws<T>(pl, nb);
+    if (st != BLOCH_OK) return st;
+    for (int i = 0; i < 3 * nb; ++i)
+        if (!std::isfinite(k_host[i])) return set_error(BLOCH_ENONFINITE, "wave vector has a non-finite component");
+    Workspace<T>& w = ws_of<T>(pl);
+    BLOCH_CUDA_CHECK_RET(
+        cudaMemcpyAsync(w.kvec, k_host, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, pl->stream));
+    const int S = pl->Nx + pl->Ny + pl->Nz;
+    const int blocks = (int)std::min<long long>(1024, ((long long)nb * S + 255) / 256);
+    ++pl->launches;
+    k_qtab<T><<<blocks, 256, 0, pl->stream>>>(w.kvec, pl->d_xi, pl->Nx, pl->Ny, pl->Nz, nb, pl->qscale, w.qtab);
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    return BLOCH_OK;
+}
+
+// ------------------------------------------------------------ operators
+template <typename T>
+void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    const TileCfg& t = tile_of<T>(pl);
+    const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,
+                    pyz = (long long)pl->Ny * pl->Nz;
+    dim3 g1((unsigned)((pxy + t.Pz5 - 1) / t.Pz5), nb);
+    ++pl->launches;
+    k_pass_z_strain<T><<<g1, 256, t.smem_z5, pl->stream>>>(u, w.E, w.qtab, tw_of<T>(pl, 2), g, t.Pz5);
+    dim3 g2((unsigned)((pxz + t.Py2 - 1) / t.Py2), nb * 6);
+    ++pl->launches;
+    k_pass_axis<T, +1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    dim3 g3((unsigned)((pyz + t.Px7 - 1) / t.Px7), nb);
+    ++pl->launches;
+    k_pass_x_stress<T><<<g3, 256, t.smem_x7, pl->stream>>>(w.E, pl->d_ids, ctab_of<T>(pl), tw_of<T>(pl, 0), g, t.Px7);
+    ++pl->launches;
+    k_pass_axis<T, -1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    ++pl->launches;
+    k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5, out_scale);
+}
+
+template <typename T>
+void launch_M(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
+    const long long n = (long long)nb * 3 * pl->V;
+    if (pl->uniform_rho) {
+        const int blocks = (int)std::min<long long>(4096, (n + 255) / 256);
+        ++pl->launches;
+        k_scale<T><<<blocks, 256, 0, pl->stream>>>(u, out, T(pl->rho_uniform_scaled * out_scale), (size_t)n);
+        return;
+    }
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    const TileCfg& t = tile_of<T>(pl);
+    const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,
+                    pyz = (long long)pl->Ny * pl->Nz;
+    dim3 gz((unsigned)((pxy + t.Pz2 - 1) / t.Pz2), nb * 3);
+    dim3 gy((unsigned)((pxz + t.Py2 - 1) / t.Py2), nb * 3);
+    dim3 gx((unsigned)((pyz + t.Px4 - 1) / t.Px4), nb);
+    ++pl->launches;
+    k_pass_axis<T, +1, 2><<<gz, 256, t.smem_z2, pl->stream>>>(u, w.E, tw_of<T>(pl, 2), g, t.Pz2, T(1));
+    ++pl->launches;
+    k_pass_axis<T, +1, 1><<<gy, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    ++pl->launches;
+    k_pass_x_rho<T><<<gx, 256, t.smem_x4, pl->stream>>>(w.E, pl->d_ids, rtab_of<T>(pl), tw_of<T>(pl, 0), g, t.Px4);
+    ++pl->launches;
+    k_pass_axis<T, -1, 1><<<gy, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    ++pl->launches;
+    k_pass_axis<T, -1, 2><<<gz, 256, t.smem_z2, pl->stream>>>(w.E, out, tw_of<T>(pl, 2), g, t.Pz2, out_scale);
+}
+
+template <typename T>
+void launch_precond(bloch_plan* pl, int nb, const cplx_t<T>* r, cplx_t<T>* z, T out_scale) {
+    dim3 gr(vec_blocks(pl, nb), nb);
+    ++pl->launches;
+    k_precond<T><<<gr, 256, 0, pl->stream>>>(r, z, ws_of<T>(pl).qtab, geo_of<T>(pl), pl->pc, out_scale);
+}
+
+template <typename T>
+void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, long long n_per, double2* out,
+                double2* partial) {
+    const int nblk = vec_blocks(pl, nb);
+    dim3 gr(nblk, nb);
+    ++pl->launches;
+    k_dot_partial<T><<<gr, 256, 0, pl->stream>>>(a, c, n_per, partial);
+    ++pl->launches;
+    k_dot_final<<<nb, 256, 0, pl->stream>>>(partial, nblk, out);
+}
+
+// ------------------------------------------------------------ PCG (Algorithm 2)
+template <typename T>
+bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
+                     int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters) {
+    bloch_status st = ensure_cg<T>(pl, nb);
+    if (st != BLOCH_OK) return st;
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    const int nblk = vec_blocks(pl, nb);
+    dim3 gr(nblk, nb);
+    const double tol2 = tol * tol;
+    if (use_x0) launch_K<T>(pl, nb, x, w.Ap, T(1));
+    ++pl->launches;
+    k_cg_init<T><<<gr, 256, 0, pl->stream>>>(b, use_x0 ? w.Ap : nullptr, x, w.r, w.p, w.qtab, g, pl->pc,
+                                              T(rhs_scale), use_x0 ? 0 : 1, w.part3);
+    BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_nactive, 0, sizeof(int), pl->stream));
+    ++pl->launches;
+    k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 0, tol2, pl->d_nactive);
+    BLOCH_CUDA_CHECK_RET(
+        cudaMemcpyAsync(pl->h_nactive, pl->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+    BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+    int it = 0;
+    long long tot = 0;
+    while (*pl->h_nactive > 0 && it < max_iter) {
+        tot += *pl->h_nactive;
+        launch_K<T>(pl, nb, w.p, w.Ap, T(1));
+        launch_dot<T>(pl, nb, w.p, w.Ap, 3 * pl->V, w.dots, w.part2);
+        ++pl->launches;
+        k_cg_scalars<<<nb, 32, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 1, tol2, pl->d_nactive);
+        ++pl->launches;
+        k_cg_update<T><<<gr, 256, 0, pl->stream>>>(x, w.r, w.p, w.Ap, w.qtab, g, pl->pc, w.sys, w.part3);
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_nactive, 0, sizeof(int), pl->stream));
+        ++pl->launches;
+        k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 2, tol2, pl->d_nactive);
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(pl->h_nactive, pl->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+        ++it;
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        if (*pl->h_nactive == 0) break;
+        ++pl->launches;
+        k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, w.qtab, g, pl->pc, w.sys);
+    }
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    std::vector<CGSys> hs(nb);
+    BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(hs.data(), w.sys, sizeof(CGSys) * nb, cudaMemcpyDeviceToHost, pl->stream));
+    BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+    bool all = true, finite = true;
+    for (int i = 0; i < nb; ++i) {
+        const double rel = hs[i].bb > 0 ? std::sqrt(std::max(hs[i].rr, 0.0) / hs[i].bb) : 0.0;
+        if (!std::isfinite(hs[i].rr) || !std::isfinite(hs[i].bb)) finite = false;
+        if (iters) iters[i] = hs[i].iters;
+        if (relres) relres[i] = rel;
+        if (!(rel <= tol)) all = false;
+    }
+    if (total_iters) *total_iters += tot;
+    if (!finite) return set_error(BLOCH_ENONFINITE, "PCG met a non-finite residual");
+    if (!all) return set_error(BLOCH_ENOTCONV_CG, "PCG reached its iteration cap before the tolerance");
+    return BLOCH_OK;
+}
+
+#define INST(T)                                                                                          \
+    template bloch_status ensure_ws<T>(bloch_plan*, int);                                                \
+    template bloch_status ensure_cg<T>(bloch_plan*, int);                                                \
+    template bloch_status set_k<T>(bloch_plan*, int, const double*);                                     \
+    template void launch_K<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                        \
+    template void launch_M<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                        \
+    template void launch_precond<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                  \
+    template void launch_dot<T>(bloch_plan*, int, const cplx_t<T>*, const cplx_t<T>*, long long,         \
+                                double2*, double2*);                                                     \
+    template bloch_status pcg_run<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, double, double, int, \
+                                     bool, int*, double*, long long*);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace bloch
+
+using namespace bloch;
+
+// ============================================================== C ABI
+extern "C" {
+
+void bloch_default_options(bloch_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = BLOCH_FP64;
+    opt->method = BLOCH_SUBSPACE;
+    opt->tol_lin = 1e-10;
+    opt->tol_eig = 1e-10;
+    opt->max_cg = 2000;
+    opt->max_outer = 500;
+    opt->block = 0;
+    opt->k_batch = 0;
+    opt->ncv = 0;
+}
+
+const char* bloch_last_error(void) { return g_last_error.c_str(); }
+
+size_t bloch_plan_device_bytes(const bloch_plan* plan) { return plan ? plan->device_bytes : 0; }
+
+uint64_t bloch_plan_kernel_launches(const bloch_plan* plan) { return plan ? plan->launches : 0; }
+
+static void free_ws_all(bloch_plan* pl) {
+    auto fr = [](auto& w) {
+        cudaFree(w.E);
+        cudaFree(w.qtab);
+        cudaFree(w.kvec);
+        cudaFree(w.r);
+        cudaFree(w.p);
+        cudaFree(w.Ap);
+        cudaFree(w.part3);
+        cudaFree(w.part2);
+        cudaFree(w.dots);
+        cudaFree(w.sys);
+    };
+    fr(pl->ws_f);
+    fr(pl->ws_d);
+}
+
+void bloch_plan_destroy(bloch_plan* pl) {
+    if (!pl) return;
+    cudaStreamSynchronize(pl->stream);
+    free_ws_all(pl);
+    cudaFree(pl->d_xi);
+    cudaFree(pl->d_ids);
+    cudaFree(pl->d_Cf);
+    cudaFree(pl->d_Cd);
+    cudaFree(pl->d_rf);
+    cudaFree(pl->d_rd);
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(pl->d_twf[a]);
+        cudaFree(pl->d_twd[a]);
+    }
+    cudaFree(pl->d_nactive);
+    cudaFreeHost(pl->h_nactive);
+    delete pl;
+}
+
+static bool cholesky_pd(const double* A6) {
+    double L[36] = {0};
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A6[i * 6 + j];
+            for (int k = 0; k < j; ++k) s -= L[i * 6 + k] * L[j * 6 + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i * 6 + i] = std::sqrt(s);
+            } else {
+                L[i * 6 + j] = s / L[j * 6 + j];
+            }
+        }
+    return true;
+}
+
+bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const double L[3], const int32_t* grain_ids,
+                               int32_t G, const double* C_per_grain, const double* rho, const bloch_options* opt,
+                               void* cuda_stream) {
+    if (!out) return set_error(BLOCH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !L || !grain_ids || !C_per_grain || !rho) return set_error(BLOCH_EINVAL, "NULL argument");
+    for (int a = 0; a < 3; ++a) {
+        if (grid[a] < 1) return set_error(BLOCH_EINVAL, "grid sizes must be >= 1");
+        if (grid[a] > 512 || !factor_ok(grid[a]))
+            return set_error(BLOCH_EUNSUPPORTED, "grid sizes must be <= 512 with prime factors in {2,3,5,7}");
+        if (!(L[a] > 0.0) || !std::isfinite(L[a])) return set_error(BLOCH_EINVAL, "cell lengths must be > 0");
+    }
+    if (G < 1) return set_error(BLOCH_EINVAL, "G must be >= 1");
+    const long long V = (long long)grid[0] * grid[1] * grid[2];
+    for (int g = 0; g < G; ++g) {
+        const double* C = C_per_grain + (size_t)g * 36;
+        double mx = 0;
+        for (int i = 0; i < 36; ++i) {
+            if (!std::isfinite(C[i])) return set_error(BLOCH_ENONFINITE, "stiffness has a non-finite entry");
+            mx = std::max(mx, std::fabs(C[i]));
+        }
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < i; ++j)
+                if (std::fabs(C[i * 6 + j] - C[j * 6 + i]) > 1e-10 * mx)
+                    return set_error(BLOCH_EINVAL, "stiffness of grain " + std::to_string(g) + " is not symmetric");
+        if (!cholesky_pd(C))
+            return set_error(BLOCH_EINVAL, "stiffness of grain " + std::to_string(g) + " is not positive definite");
+        if (!(rho[g] > 0.0) || !std::isfinite(rho[g]))
+            return set_error(BLOCH_EINVAL, "density of grain " + std::to_string(g) + " must be > 0");
+    }
+    std::vector<long long> counts(G, 0);
+    for (long long v = 0; v < V; ++v) {
+        const int id = grain_ids[v];
+        if (id < 0 || id >= G) return set_error(BLOCH_EINVAL, "grain id out of range at voxel " + std::to_string(v));
+        counts[id]++;
+    }
+
+    bloch_plan* pl = new bloch_plan();
+    pl->Nx = grid[0];
+    pl->Ny = grid[1];
+    pl->Nz = grid[2];
+    pl->V = V;
+    for (int a = 0; a < 3; ++a) pl->L[a] = L[a];
+    pl->G = G;
+    if (opt) pl->opt = *opt;
+    else bloch_default_options(&pl->opt);
+    pl->stream = (cudaStream_t)cuda_stream;
+    std::memset(&pl->last_stats, 0, sizeof(pl->last_stats));
+    pl->ids_host.assign(grain_ids, grain_ids + V);
+    pl->C_host.assign(C_per_grain, C_per_grain + (size_t)G * 36);
+    pl->rho_host.assign(rho, rho + G);
+
+    // volume averages (Section 3.3: C0 is the volume-averaged stiffness)
+    double rbar = 0;
+    for (int i = 0; i < 36; ++i) pl->C0V[i] = 0;
+    for (int g = 0; g < G; ++g) {
+        const double w = (double)counts[g] / (double)V;
+        for (int i = 0; i < 36; ++i) pl->C0V[i] += w * C_per_grain[(size_t)g * 36 + i];
+        rbar += w * rho[g];
+    }
+    pl->uniform_rho = true;
+    for (int g = 0; g < G; ++g)
+        if (counts[g] > 0 && rho[g] != rho[grain_ids[0]]) pl->uniform_rho = false;
+    pl->rho_ref = rbar;
+    pl->rho_uniform_scaled = rho[grain_ids[0]] / rbar;
+    pl->qscale = std::max(L[0], std::max(L[1], L[2])) / (2.0 * M_PI);
+    pl->Cref = std::max(pl->C0V[0], std::max(pl->C0V[7], pl->C0V[14]));
+    pl->Kscale = pl->Cref / (pl->qscale * pl->qscale);
+
+    // preconditioner coefficients from the scaled C0 tensor
+    {
+        static const int vi[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+        static const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+        for (int a = 0; a < 6; ++a) {
+            const int i = pr[a][0], k = pr[a][1];
+            for (int m = 0; m < 6; ++m) {
+                const int j = pr[m][0], l = pr[m][1];
+                double c = pl->C0V[vi[i][j] * 6 + vi[k][l]];
+                if (j != l) c += pl->C0V[vi[i][l] * 6 + vi[k][j]];
+                pl->pc.a[a][m] = c / pl->Cref;
+            }
+        }
+    }
+
+    // frequencies (Eq. frequencies, FFT bin order)
+    pl->xi_host.resize(pl->Nx + pl->Ny + pl->Nz);
+    {
+        int o = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int N = grid[a];
+            for (int m = 0; m < N; ++m) {
+                const int mt = m < (N + 1) / 2 ? m : m - N;
+                pl->xi_host[o++] = 2.0 * M_PI / L[a] * mt;
+            }
+        }
+    }
+
+    auto fail = [&](bloch_status st) {
+        bloch_plan_destroy(pl);
+        return st;
+    };
+    cudaError_t e;
+#define CK(expr)                                                       \
+    if ((e = (expr)) != cudaSuccess) return fail(set_cuda_error(e, #expr));
+    size_t* acc = &pl->device_bytes;
+    CK(dmalloc(&pl->d_xi, pl->xi_host.size(), acc));
+    CK(cudaMemcpy(pl->d_xi, pl->xi_host.data(), sizeof(double) * pl->xi_host.size(), cudaMemcpyHostToDevice));
+    CK(dmalloc(&pl->d_ids, (size_t)V, acc));
+    CK(cudaMemcpy(pl->d_ids, grain_ids, sizeof(int32_t) * V, cudaMemcpyHostToDevice));
+    {
+        std::vector<double> cd((size_t)G * 36);
+        std::vector<float> cf((size_t)G * 36);
+        std::vector<double> rd(G);
+        std::vector<float> rf(G);
+        for (size_t i = 0; i < cd.size(); ++i) {
+            cd[i] = C_per_grain[i] / (pl->Cref * (double)V);
+            cf[i] = (float)cd[i];
+        }
+        for (int g = 0; g < G; ++g) {
+            rd[g] = rho[g] / (pl->rho_ref * (double)V);
+            rf[g] = (float)rd[g];
+        }
+        CK(dmalloc(&pl->d_Cd, cd.size(), acc));
+        CK(dmalloc(&pl->d_Cf, cf.size(), acc));
+        CK(dmalloc(&pl->d_rd, rd.size(), acc));
+        CK(dmalloc(&pl->d_rf, rf.size(), acc));
+        CK(cudaMemcpy(pl->d_Cd, cd.data(), sizeof(double) * cd.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pl->d_Cf, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pl->d_rd, rd.data(), sizeof(double) * rd.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pl->d_rf, rf.data(), sizeof(float) * rf.size(), cudaMemcpyHostToDevice));
+    }
+    for (int a = 0; a < 3; ++a) {
+        const int N = grid[a];
+        std::vector<double2> td(N);
+        std::vector<float2> tf(N);
+        for (int t = 0; t < N; ++t) {
+            const long double ang = -2.0L * 3.141592653589793238462643383279502884L * t / N;
+            td[t] = make_double2((double)std::cos(ang), (double)std::sin(ang));
+            tf[t] = make_float2((float)td[t].x, (float)td[t].y);
+        }
+        CK(dmalloc(&pl->d_twd[a], (size_t)N, acc));
+        CK(dmalloc(&pl->d_twf[a], (size_t)N, acc));
+        CK(cudaMemcpy(pl->d_twd[a], td.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pl->d_twf[a], tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+    }
+    CK(dmalloc(&pl->d_nactive, 1, acc));
+    CK(cudaMallocHost((void**)&pl->h_nactive, sizeof(int)));
+    CK(set_smem_attrs<float>());
+    CK(set_smem_attrs<double>());
+#undef CK
+    for (Geo* gp : {&pl->geo_f, &pl->geo_d}) {
+        gp->Nx = pl->Nx;
+        gp->Ny = pl->Ny;
+        gp->Nz = pl->Nz;
+        gp->V = V;
+    }
+    for (int a = 0; a < 3; ++a) {
+        pl->geo_f.ax[a] = make_axis(grid[a], 4);   // radices up to 16 in FP32
+        pl->geo_d.ax[a] = make_axis(grid[a], 3);   // up to 8 in FP64 (register budget)
+    }
+    pl->tile_f = make_tiles<float>(pl->Nx, pl->Ny, pl->Nz);
+    pl->tile_d = make_tiles<double>(pl->Nx, pl->Ny, pl->Nz);
+    pl->nblk_max = vec_blocks(pl, 1);
+    *out = pl;
+    return BLOCH_OK;
+}
+
+static bloch_status check_common(bloch_plan* pl, int nb, int precision) {
+    if (!pl) return set_error(BLOCH_EINVAL, "plan is NULL");
+    if (nb < 1 || nb > 65535 / 6) return set_error(BLOCH_EINVAL, "nb must be in [1, 10922]");
+    if (precision != BLOCH_FP32 && precision != BLOCH_FP64)
+        return set_error(BLOCH_EINVAL, "precision must be BLOCH_FP32 or BLOCH_FP64");
+    return BLOCH_OK;
+}
+
+bloch_status bloch_apply_K(bloch_plan* pl, int32_t nb, const double* k, int32_t precision, const void* u,
+                           void* Ku) {
+    bloch_status st = check_common(pl, nb, precision);
+    if (st != BLOCH_OK) return st;
+    if (!k || !u || !Ku) return set_error(BLOCH_EINVAL, "NULL argument");
+    if (u == Ku) return set_error(BLOCH_EINVAL, "Ku may not alias u");
+    if (precision == BLOCH_FP32) {
+        if ((st = set_k<float>(pl, nb, k)) != BLOCH_OK) return st;
+        launch_K<float>(pl, nb, (const float2*)u, (float2*)Ku, (float)pl->Kscale);
+    } else {
+        if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
+        launch_K<double>(pl, nb, (const double2*)u, (double2*)Ku, pl->Kscale);
+    }
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    return BLOCH_OK;
+}
+
+bloch_status bloch_apply_M(bloch_plan* pl, int32_t nb, int32_t precision, const void* u, void* Mu) {
+    bloch_status st = check_common(pl, nb, precision);
+    if (st != BLOCH_OK) return st;
+    if (!u || !Mu) return set_error(BLOCH_EINVAL, "NULL argument");
+    if (precision == BLOCH_FP32) {
+        if ((st = ensure_ws<float>(pl, nb)) != BLOCH_OK) return st;
+        launch_M<float>(pl, nb, (const float2*)u, (float2*)Mu, (float)pl->rho_ref);
+    } else {
+        if ((st = ensure_ws<double>(pl, nb)) != BLOCH_OK) return st;
+        launch_M<double>(pl, nb, (const double2*)u, (double2*)Mu, pl->rho_ref);
+    }
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    return BLOCH_OK;
+}
+
+bloch_status bloch_apply_precond(bloch_plan* pl, int32_t nb, const double* k, int32_t precision, const void* r,
+                                 void* z) {
+    bloch_status st = check_common(pl, nb, precision);
+    if (st != BLOCH_OK) return st;
+    if (!k || !r || !z) return set_error(BLOCH_EINVAL, "NULL argument");
+    if (precision == BLOCH_FP32) {
+        if ((st = set_k<float>(pl, nb, k)) != BLOCH_OK) return st;
+        launch_precond<float>(pl, nb, (const float2*)r, (float2*)z, (float)(1.0 / pl->Kscale));
+    } else {
+        if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
+        launch_precond<double>(pl, nb, (const double2*)r, (double2*)z, 1.0 / pl->Kscale);
+    }
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    return BLOCH_OK;
+}
+
+bloch_status bloch_pcg(bloch_plan* pl, int32_t nb, const double* k, int32_t precision, const void* b, void* x,
+                       double tol, int32_t max_iter, int32_t use_x0, int32_t* iters, double* rel_res) {
+    bloch_status st = check_common(pl, nb, precision);
+    if (st != BLOCH_OK) return st;
+    if (!k || !b || !x) return set_error(BLOCH_EINVAL, "NULL argument");
+    if (!(tol > 0.0) || max_iter < 0) return set_error(BLOCH_EINVAL, "tol must be > 0 and max_iter >= 0");
+    if (precision == BLOCH_FP32) {
+        if ((st = set_k<float>(pl, nb, k)) != BLOCH_OK) return st;
+        return pcg_run<float>(pl, nb, (const float2*)b, (float2*)x, 1.0 / pl->Kscale, tol, max_iter, use_x0 != 0,
+                              iters, rel_res, nullptr);
+    }
+    if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
+    return pcg_run<double>(pl, nb, (const double2*)b, (double2*)x, 1.0 / pl->Kscale, tol, max_iter, use_x0 != 0,
+                           iters, rel_res, nullptr);
+}
+
+bloch_status bloch_solve_bands(bloch_plan* pl, int32_t n_k, const double* k_list, int32_t n_bands,
+                               double* omega_out, void* vecs_out, bloch_stats* stats) {
+    if (!pl) return set_error(BLOCH_EINVAL, "plan is NULL");
+    if (n_k < 1 || !k_list || !omega_out) return set_error(BLOCH_EINVAL, "n_k >= 1, k_list and omega_out required");
+    if (n_bands < 1 || (long long)n_bands >= 3 * pl->V) return set_error(BLOCH_EINVAL, "n_bands must be in [1, 3V)");
+    return bloch_solve_bands_impl(pl, n_k, k_list, n_bands, omega_out, vecs_out, stats);
+}
+
+}  // extern "C"

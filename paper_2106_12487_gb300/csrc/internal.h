@@ -1,0 +1,122 @@
+// Internal plan structure and operator launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bloch.h"
+#include "fft.cuh"
+#include "passes.cuh"
+#include "vec.cuh"
+
+namespace bloch {
+
+bloch_status set_error(bloch_status st, const std::string& msg);
+bloch_status set_cuda_error(cudaError_t e, const char* what);
+
+// Per-precision device workspace, grown on demand (capacity in systems).
+template <typename T>
+struct Workspace {
+    using C = cplx_t<T>;
+    int cap = 0;            // systems the buffers hold
+    C* E = nullptr;         // 6 x V x cap  (FFT-pass intermediates)
+    T* qtab = nullptr;      // (Nx+Ny+Nz) x cap
+    double* kvec = nullptr; // 3 x cap
+    int cg_cap = 0;
+    C* r = nullptr;         // 3 x V x cg_cap
+    C* p = nullptr;
+    C* Ap = nullptr;
+    double* part3 = nullptr;  // cg_cap x nblk_max x 3
+    double2* part2 = nullptr; // cg_cap x nblk_max
+    double2* dots = nullptr;  // cg_cap
+    CGSys* sys = nullptr;     // cg_cap
+};
+
+struct TileCfg {
+    int Pz5;    // pencils per CTA, z passes with 5 buffers (strain / divergence)
+    int Py2;    // y pass, 2 buffers
+    int Pz2;    // z pass, 2 buffers (mass operator)
+    int Px7;    // x stress pass, 7 buffers
+    int Px4;    // x rho pass, 4 buffers
+    size_t smem_z5, smem_y2, smem_z2, smem_x7, smem_x4;
+};
+
+}  // namespace bloch
+
+struct bloch_plan {
+    int Nx, Ny, Nz;
+    long long V;
+    double L[3];
+    int G;
+    bloch_options opt;
+    cudaStream_t stream;
+
+    // unit scaling: q~ = q*qscale, C~ = C/Cref, rho~ = rho/rho_ref
+    double qscale, Cref, rho_ref, Kscale;
+    bool uniform_rho;
+    double rho_uniform_scaled;     // rho/rho_ref when uniform
+    double C0V[36];                // volume-averaged Voigt stiffness (Pa)
+    bloch::PrecondCoef pc;         // scaled
+
+    std::vector<double> xi_host;   // Nx + Ny + Nz (rad/m, FFT order)
+    std::vector<int32_t> ids_host;
+    std::vector<double> C_host;    // G x 36 (Pa)
+    std::vector<double> rho_host;  // G
+
+    double* d_xi = nullptr;
+    int32_t* d_ids = nullptr;
+    float* d_Cf = nullptr;
+    double* d_Cd = nullptr;
+    float* d_rf = nullptr;
+    double* d_rd = nullptr;
+    float2* d_twf[3] = {nullptr, nullptr, nullptr};
+    double2* d_twd[3] = {nullptr, nullptr, nullptr};
+    int* d_nactive = nullptr;
+    int* h_nactive = nullptr;     // pinned
+
+    bloch::Geo geo_f, geo_d;
+    bloch::TileCfg tile_f, tile_d;
+    int nblk_max;
+
+    bloch::Workspace<float> ws_f;
+    bloch::Workspace<double> ws_d;
+    size_t device_bytes = 0;
+    unsigned long long launches = 0;   // kernels launched by this plan
+    bloch_stats last_stats;
+};
+
+namespace bloch {
+
+template <typename T> Workspace<T>& ws_of(bloch_plan* pl);
+template <typename T> const Geo& geo_of(const bloch_plan* pl);
+
+// Grow the operator workspace to hold nb systems.
+template <typename T> bloch_status ensure_ws(bloch_plan* pl, int nb);
+// Grow the PCG workspace to hold nb systems.
+template <typename T> bloch_status ensure_cg(bloch_plan* pl, int nb);
+// Upload nb wave vectors (host, rad/m) and build the scaled q tables.
+template <typename T> bloch_status set_k(bloch_plan* pl, int nb, const double* k_host);
+// Scaled stiffness operator on nb systems whose q tables are set: out = out_scale * A~ u.
+template <typename T> void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale);
+// Scaled mass operator: out = out_scale * M~ u (M~ = M / rho_ref).  out may alias u.
+template <typename T> void launch_M(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale);
+// Scaled preconditioner on nb systems: z = out_scale * P~^-1 r.
+template <typename T> void launch_precond(bloch_plan* pl, int nb, const cplx_t<T>* r, cplx_t<T>* z, T out_scale);
+// Batched PCG on the scaled operator: A~ x = rhs_scale * b.
+template <typename T>
+bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
+                     int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters);
+// dots[b] = sum conj(a_b) c_b over n_per elements per system (device result).
+template <typename T>
+void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, long long n_per, double2* out,
+                double2* partial);
+
+int vec_blocks(const bloch_plan* pl, int nb);
+
+}  // namespace bloch
+
+// eigensolver entry (bloch_eig.cu)
+bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_list, int n_bands, double* omega_out,
+                                    void* vecs_out, bloch_stats* stats);

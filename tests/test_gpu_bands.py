@@ -1,0 +1,105 @@
+"""GPU band frequencies against the FP64 oracle (Algorithms 1 and 3).
+
+Bars: the FP64 plain form within 1e-9 relative frequency error, the FP32
+chosen form (FP32 fields and PCG, FP64 residual refinement and Rayleigh
+quotients) within 1e-6; zero modes at k = 0 are exactly zero.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bloch_oracle as O
+from paper_2106_12487_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_12487_gb300 import bloch, build
+    build.build()
+    bloch.lib()
+    return bloch
+
+
+def freq_err(got, want):
+    nz = want > 0
+    assert np.all(got[~nz] == 0.0)
+    return float(np.max(np.abs(got[nz] / want[nz] - 1.0)))
+
+
+FORMS = [(0, 1e-9, dict(tol_lin=1e-10, tol_eig=1e-11)), (1, 1e-6, dict(tol_lin=1e-3, tol_eig=1e-7))]
+
+
+@pytest.mark.parametrize("prec,bar,opt", FORMS)
+def test_bands_small_polycrystal(B, prec, bar, opt):
+    p = synth.small_polycrystal((8, 8, 8), 6, 5, n_bands=6)
+    med = O.Medium.from_problem(p)
+    ks = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [1.0, 1.0, 0.0], [0.3, 0.6, 0.9]]) * math.pi / 1e-3
+    want = O.solve_bands(med, ks, 6, 1e-12, 1e-12, method="lanczos").omega
+    plan = B.Plan.from_problem(p, precision=prec, **opt)
+    got, stats, _ = plan.solve_bands(ks, 6)
+    assert freq_err(got, want) < bar
+    assert stats["max_rel_residual"] < 1e-4
+
+
+@pytest.mark.parametrize("prec,bar,opt", FORMS)
+def test_bands_rve16_workload(B, prec, bar, opt):
+    """16^3 cell, 8 grains, Cu-like cubic, Haar orientations; 6 bands at 10
+    k-points on Gamma-X (expected values written by tests/golden/make_golden.py)."""
+    g = json.load(open(os.path.join(GOLDEN, "rve16_g8_bands.json")))
+    p = synth.workload("rve16_g8")
+    assert np.allclose(np.asarray(g["k_list"]), p.k_list)
+    plan = B.Plan.from_problem(p, precision=prec, **opt)
+    got, stats, _ = plan.solve_bands(p.k_list, p.n_bands)
+    assert freq_err(got, np.asarray(g["omega"])) < bar
+
+
+@pytest.mark.parametrize("batch", [1, 3])
+def test_bands_batching_is_invisible(B, batch):
+    """Solving the k list one slot at a time or three at a time gives the same
+    frequencies (slots are refilled and compacted as they converge)."""
+    p = synth.small_polycrystal((8, 8, 8), 6, 5, n_bands=5)
+    ks = synth.kpath("GXM", 7)
+    plan = B.Plan.from_problem(p, precision=0, tol_lin=1e-10, tol_eig=1e-11, k_batch=batch)
+    got, _, _ = plan.solve_bands(ks, 5)
+    ref_plan = B.Plan.from_problem(p, precision=0, tol_lin=1e-10, tol_eig=1e-11, k_batch=7)
+    ref, _, _ = ref_plan.solve_bands(ks, 5)
+    nz = ref > 0
+    assert np.max(np.abs(got[nz] / ref[nz] - 1)) < 1e-9
+
+
+def test_bands_vectors_are_eigenvectors(B):
+    """Returned vectors are M-normalised and their FP64 oracle Rayleigh quotients
+    reproduce the returned frequencies."""
+    import torch
+    p = synth.small_polycrystal((8, 8, 8), 6, 9, n_bands=4)
+    med = O.Medium.from_problem(p)
+    ks = np.array([[0.4, 0.2, 0.0], [0.0, 0.0, 0.0]]) * math.pi / 1e-3
+    plan = B.Plan.from_problem(p, precision=0, tol_lin=1e-10, tol_eig=1e-11)
+    vecs = torch.zeros(2 * 4 * 3 * 512, dtype=torch.complex128, device="cuda")
+    got, _, _ = plan.solve_bands(ks, 4, vecs_out=vecs)
+    V = vecs.cpu().numpy().reshape(2, 4, 3, 8, 8, 8)
+    for i in range(2):
+        lam, res = O.rayleigh_quotients(med, ks[i], V[i])
+        for b in range(4):
+            m = O.vdot(V[i, b], O.apply_M(med, V[i, b])).real
+            assert abs(m - 1.0) < 1e-9
+            if got[i, b] > 0:
+                assert abs(math.sqrt(lam[b]) / got[i, b] - 1) < 1e-9
+                assert res[b] < 1e-8
+
+
+def test_bands_nonconvergence_reported(B):
+    """A sweep cap of 1 returns ENOTCONV_EIG (status 5) with frequencies filled."""
+    p = synth.small_polycrystal((8, 8, 8), 6, 5, n_bands=4)
+    plan = B.Plan.from_problem(p, precision=0, max_outer=1)
+    got, _, st = plan.solve_bands([[0.5 * math.pi / 1e-3, 0, 0]], 4, allow_nonconv=True)
+    assert st == 5 and np.all(got > 0)
