@@ -38,9 +38,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rve128_g200")
     ap.add_argument("--form", default="chosen", choices=["chosen", "plain"])
-    ap.add_argument("--k-per-step", type=int, default=2)
+    ap.add_argument("--k-per-step", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--max-outer", type=int, default=300, help="sweep cap (profiling runs bound it)")
+    ap.add_argument("--kapply-only", action="store_true", help="time only the K-apply chain")
+    ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
+    ap.add_argument("--fft-variant", type=int, default=0, choices=[0, 1],
+                    help="0: two-stage register FFT passes, 1: shared-memory Stockham passes")
     return ap.parse_args()
 
 
@@ -57,6 +62,13 @@ def dist_init(args):
         else:
             dist.init_process_group("gloo")
     return ws, rank, local
+
+
+def k_indices(step, rank, ws, kps, nk):
+    """Wave-vector indices solved by `rank` at `step`: the ranks of one step
+    take disjoint consecutive batches of the path (weak scaling, no data-path
+    collective)."""
+    return [((step * ws + rank) * kps + i) % nk for i in range(kps)]
 
 
 def barrier(ws):
@@ -192,6 +204,39 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def kapply_roofline(plan, p, prec, nb=0):
+    """The dominant kernel chain: the 5-pass K-apply on a block of nb systems
+    (default: one subspace block), timed with CUDA events on the launching
+    stream after warm-up; inputs (nb x 3 x V complex) and the 6-component
+    intermediates are larger than L2 at 128^3."""
+    import torch
+    from paper_2106_12487_gb300 import bloch
+    q = nb if nb > 0 else min(2 * p.n_bands, p.n_bands + 8)
+    dt = torch.complex64 if prec == bloch.FP32 else torch.complex128
+    u = torch.randn(q * 3 * plan.V, dtype=dt, device="cuda")
+    out = torch.empty_like(u)
+    kq = np.repeat(p.k_list[5:6], q, axis=0)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        plan.apply_K(kq, u, out)
+    torch.cuda.synchronize()
+    reps = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.apply_K(kq, u, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / 1000.0 / reps
+    alg_bytes = KAPPLY_BYTES_PER_VOXEL[prec] * plan.V * q
+    peak, peak_src = peaks()
+    achieved = alg_bytes / t_apply / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"K-apply 5-pass chain, {q} systems at {tuple(p.grid)} ({peak_src} peak)",
+            "ms_per_launch": t_apply * 1000.0, "alg_bytes_per_launch": alg_bytes}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2106_12487_gb300 import bloch, synth
@@ -202,15 +247,20 @@ def run_ours(args, ws, rank, local):
     p = synth.workload(args.workload)
     prec = bloch.FP32 if args.form == "chosen" else bloch.FP64
     opt = dict(precision=prec, method=bloch.SUBSPACE, tol_lin=1e-3 if prec == bloch.FP32 else 1e-8,
-               tol_eig=1e-7 if prec == bloch.FP32 else 1e-10, max_cg=500, max_outer=300)
+               tol_eig=1e-6 if prec == bloch.FP32 else 1e-9, max_cg=500, max_outer=args.max_outer,
+               fft_variant=args.fft_variant)
     plan = bloch.Plan.from_problem(p, **opt)
+    if args.kapply_only:
+        roof = kapply_roofline(plan, p, prec, args.kapply_nb)
+        if rank == 0:
+            print(json.dumps({"kapply": roof}), flush=True)
+        plan.close()
+        return
     nk = p.k_list.shape[0]
     kps = args.k_per_step
 
     def kbatch(step):
-        # each rank walks its own contiguous share of the path
-        idx = [((step * ws + rank) * kps + i) % nk for i in range(kps)]
-        return p.k_list[idx]
+        return p.k_list[k_indices(step, rank, ws, kps, nk)]
 
     stream = torch.cuda.current_stream()
     for s in range(args.warmup):
@@ -240,31 +290,7 @@ def run_ours(args, ws, rank, local):
     cg = sum(s["cg_iterations"] for s in stats_all)
     kap = sum(s["k_applies"] for s in stats_all)
 
-    # dominant kernel chain: the 5-pass K-apply on a block of q vectors, timed
-    # with CUDA events on the launching stream
-    q = min(2 * p.n_bands, p.n_bands + 8)
-    dt = torch.complex64 if prec == bloch.FP32 else torch.complex128
-    u = torch.randn(q * 3 * plan.V, dtype=dt, device="cuda")
-    out = torch.empty_like(u)
-    kq = np.repeat(p.k_list[5:6], q, axis=0)
-    for _ in range(3):
-        plan.apply_K(kq, u, out)
-    torch.cuda.synchronize()
-    reps = 10
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        plan.apply_K(kq, u, out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_apply = e0.elapsed_time(e1) / 1000.0 / reps
-    alg_bytes = KAPPLY_BYTES_PER_VOXEL[prec] * plan.V * q
-    peak, peak_src = peaks()
-    achieved = alg_bytes / t_apply / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"K-apply 5-pass chain, {q} vectors at {p.grid} ({peak_src} peak)",
-            "ms_per_launch": t_apply * 1000.0}
+    roof = kapply_roofline(plan, p, prec, args.kapply_nb)
 
     # end to end through the public API with host buffers: plan upload from
     # host arrays, band solve, frequencies back to host
@@ -297,6 +323,7 @@ def run_ours(args, ws, rank, local):
                 "config": {"workload": args.workload, "grid": list(p.grid), "grains": int(p.G),
                            "n_bands": p.n_bands, "n_k_path": int(nk), "k_per_step": kps,
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
+                           "fft_variant": args.fft_variant,
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,

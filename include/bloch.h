@@ -75,6 +75,15 @@ typedef struct {
     int32_t block;       /* subspace block size q; 0 = min(2n, n+8) (Algorithm 1).      */
     int32_t k_batch;     /* wave vectors advanced together; 0 = choose from free memory. */
     int32_t ncv;         /* Lanczos basis size; 0 = max(2n+1, 20).                       */
+    int32_t warm_start;  /* subspace iteration: 1 = the k list is split into k_batch
+                            contiguous segments solved in parallel, and within a segment
+                            each k starts from the converged block of the previous k
+                            (Section 3.3); 0 = every k starts from the plane-wave start
+                            vectors.  Default 1.                                        */
+    int32_t fft_variant; /* 0 = two-stage register FFT passes where the axis length is a
+                            power of two in [16, 256], shared-memory Stockham passes
+                            elsewhere; 1 = shared-memory Stockham passes everywhere.
+                            Both compute the same operator.  Default 0.                  */
 } bloch_options;
 
 /* Statistics of the last bloch_solve_bands call (all counts summed over k). */

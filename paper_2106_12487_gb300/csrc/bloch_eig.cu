@@ -23,6 +23,7 @@
 #include <complex>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "eig_kernels.cuh"
@@ -296,12 +297,16 @@ struct Subspace {
         int phase = 0;
         std::vector<double> lam, lam_prev, unorm2;
         double err1 = INFINITY, err2 = INFINITY, err2_prev = INFINITY;
+        int stall = 0;
         bool has_prev = false;
     };
     std::vector<Slot> slots;
     int nact = 0;
     size_t next_k = 0;
     std::vector<int> order;   // k indices needing an iterative solve
+    bool warm = false;        // warm start along segments of the k list
+    // segments: slot s walks order[seg_next[s] .. seg_end[s]) when warm starting
+    std::vector<size_t> seg_next, seg_end;
 
     std::vector<void*> allocs;
     ~Subspace() {
@@ -326,7 +331,7 @@ struct Subspace {
             if ((s = alloc(&MU, blk)) || (s = alloc(&MUb, blk))) return s;
         }
         dblk = (int)std::max(1LL, std::min<long long>((n3 + 255) / 256, std::max(1, 2048 / std::max(1, B * q))));
-        gblk = (int)std::max(1LL, std::min<long long>((n3 + kGramChunk - 1) / kGramChunk, std::max(1, 1024 / B)));
+        gblk = (int)std::max(1LL, std::min<long long>((n3 + kG2Chunk - 1) / kG2Chunk, std::max(1, 608 / B)));
         if ((s = alloc(&d_part, (size_t)B * q * dblk * 3)) || (s = alloc(&d_scal, (size_t)B * q * 2)) ||
             (s = alloc(&d_gpart, (size_t)B * gblk * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
             (s = alloc(&d_Q, (size_t)B * q * q)) || (s = alloc(&d_idx, (size_t)3 * q)) ||
@@ -526,6 +531,28 @@ struct Subspace {
             BLOCH_CUDA_CHECK_RET(
                 cudaMemcpyAsync(vec(MU, to), vec(MU, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
         slots[to] = slots[from];
+        if (warm) {
+            seg_next[to] = seg_next[from];
+            seg_end[to] = seg_end[from];
+        }
+        return BLOCH_OK;
+    }
+
+    // Next wave vector of a slot's segment: start from the slot's converged
+    // block (the paper's warm start) unless k or its predecessor is Gamma,
+    // where the rigid-translation bin changes role (cold start instead).
+    bloch_status continue_slot(int s, int kidx) {
+        const Slot prev = slots[s];
+        const double* kn = (*klist)[kidx].data();
+        const bool gn = kn[0] == 0.0 && kn[1] == 0.0 && kn[2] == 0.0;
+        if (prev.gamma || gn) return init_slot(s, kidx);
+        Slot& sl = slots[s];
+        sl = Slot();
+        sl.kidx = kidx;
+        for (int a = 0; a < 3; ++a) sl.k[a] = kn[a];
+        sl.gamma = false;
+        sl.n_eff = n_bands;
+        sl.phase = 0;
         return BLOCH_OK;
     }
 
@@ -533,7 +560,20 @@ struct Subspace {
         bloch_status s;
         // fill the slots
         nact = 0;
-        while (nact < B && next_k < order.size()) {
+        if (warm) {
+            const int nseg = std::min<int>(B, (int)order.size());
+            seg_next.assign(B, 0);
+            seg_end.assign(B, 0);
+            for (int g = 0; g < nseg; ++g) {
+                seg_next[g] = order.size() * g / nseg;
+                seg_end[g] = order.size() * (g + 1) / nseg;
+            }
+            for (int g = 0; g < nseg; ++g) {
+                if ((s = init_slot(nact, order[seg_next[g]++])) != BLOCH_OK) return s;
+                ++nact;
+            }
+        }
+        while (!warm && nact < B && next_k < order.size()) {
             if ((s = init_slot(nact, order[next_k++])) != BLOCH_OK) return s;
             ++nact;
         }
@@ -547,8 +587,12 @@ struct Subspace {
                 Slot& sl = slots[i];
                 const bool test = sl.err1 <= tol && sl.err2 <= 10.0 * tol;
                 if (fp64res && sl.phase == 0) {
-                    const bool stall = sl.sweeps >= 3 && sl.err2 > 0.7 * sl.err2_prev;
-                    if (test || stall || sl.err2 <= 1e-4) sl.phase = 1;
+                    // FP32 residuals drive the sweeps until the stop test passes in
+                    // FP32 (or err2 stalls at the FP32 noise floor); the FP64
+                    // residual then verifies, and drives further sweeps if needed.
+                    if (sl.err2 > 0.9 * sl.err2_prev) sl.stall += 1;
+                    else sl.stall = 0;
+                    if (test || (sl.sweeps >= 4 && sl.stall >= 2)) sl.phase = 1;
                     if (sl.sweeps >= max_outer) done.push_back(i);
                 } else if (test || sl.sweeps >= max_outer) {
                     done.push_back(i);
@@ -562,7 +606,14 @@ struct Subspace {
                 std::vector<char> is_hole(nact, 0);
                 for (int h : holes) is_hole[h] = 1;
                 for (int h : holes) {
-                    if (next_k < order.size()) {
+                    if (warm) {
+                        if (seg_next[h] < seg_end[h]) {
+                            const int kn = order[seg_next[h]++];
+                            if ((s = continue_slot(h, kn)) != BLOCH_OK) return s;
+                            is_hole[h] = 0;
+                            fresh.push_back(h);
+                        }
+                    } else if (next_k < order.size()) {
                         if ((s = init_slot(h, order[next_k++])) != BLOCH_OK) return s;
                         is_hole[h] = 0;
                         fresh.push_back(h);
@@ -614,11 +665,11 @@ struct Subspace {
             dim3 gg(gblk, nact);
             const int npair = q * q;
             ++pl->launches;
-            k_gram<T><<<gg, 256, 0, pl->stream>>>(Ub, KU, q, n3, d_gpart);
+            k_gram2<T><<<gg, 256, 0, pl->stream>>>(Ub, KU, q, n3, d_gpart);
             ++pl->launches;
             k_gram_final<<<dim3((npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair, d_G);
             ++pl->launches;
-            k_gram<T><<<gg, 256, 0, pl->stream>>>(Ub, uniform ? Ub : MUb, q, n3, d_gpart);
+            k_gram2<T><<<gg, 256, 0, pl->stream>>>(Ub, uniform ? Ub : MUb, q, n3, d_gpart);
             ++pl->launches;
             k_gram_final<<<dim3((npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair,
                                                                                    d_G + (size_t)nact * npair);
@@ -678,6 +729,7 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     S.omega_out = omega_out;
     S.vecs_out = vecs_out;
     S.st = st;
+    S.warm = pl->opt.warm_start != 0;
     for (size_t i = 0; i < ks.size(); ++i) {
         const bool gamma = ks[i][0] == 0.0 && ks[i][1] == 0.0 && ks[i][2] == 0.0;
         if (gamma && !pl->uniform_rho)
@@ -696,6 +748,8 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     long long Bmax = std::max<long long>(1, (long long)(0.6 * (double)freeb / (double)per_slot));
     Bmax = std::min<long long>(Bmax, 10922 / S.q);
     int B = pl->opt.k_batch > 0 ? pl->opt.k_batch : (int)Bmax;
+    if (S.warm && pl->opt.k_batch <= 0)
+        B = std::min<int>(B, std::max<int>(1, ((int)S.order.size() + 7) / 8));   // segments of ~8 wave vectors
     B = std::max(1, std::min<int>(B, (int)std::max<size_t>(1, S.order.size())));
     S.B = B;
     if (S.order.empty()) return BLOCH_OK;
@@ -704,6 +758,373 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     s = S.run();
     if (s != BLOCH_OK) return s;
     if (S.any_unconverged) return set_error(BLOCH_ENOTCONV_EIG, "eigensolver reached its sweep cap");
+    return BLOCH_OK;
+}
+
+// ====================================================================
+// Shift-invert Lanczos with thick restart (Section 3.3, Eqs. shift and
+// def_invop): Lanczos on OP = A_k^-1 M in the M inner product; the n largest
+// Ritz values theta of OP give lambda = 1/theta.  Restarting keeps the
+// kk = n + (m - n)/2 wanted Ritz vectors and the residual vector (thick
+// restart, equivalent to implicit restart with exact shifts).  Each slot (one
+// wave vector) advances one Lanczos step per iteration; all slots share one
+// batched PCG per step.  Orthogonalisation: classical Gram-Schmidt applied
+// twice against the whole basis.
+// ====================================================================
+template <typename T>
+struct Lanczos {
+    using C = cplx_t<T>;
+    bloch_plan* pl;
+    int n_bands, m, B;
+    long long n3;
+    double rho_s, tol_eig, tol_lin;
+    int max_outer, max_cg;
+    const std::vector<std::array<double, 3>>* klist;
+    double* omega_out;
+    void* vecs_out;
+    bloch_stats* st;
+    bool any_unconverged = false;
+    std::vector<int> order;
+    size_t next_k = 0;
+
+    C *Vb = nullptr, *Tmp = nullptr, *Bc = nullptr, *Xc = nullptr;
+    double2 *d_part = nullptr, *d_h = nullptr, *d_Q = nullptr;
+    int* d_nv = nullptr;
+    long long *d_src = nullptr, *d_dst = nullptr;
+    double* d_s = nullptr;
+    int nblk = 0;
+
+    struct Slot {
+        int kidx = -1;
+        double k[3];
+        bool gamma = false;
+        int n_eff = 0;
+        int j = 0;
+        int restarts = 0;
+        std::vector<cd> H;   // (m+1) x m
+    };
+    std::vector<Slot> slots;
+    int nact = 0;
+    std::vector<void*> allocs;
+    ~Lanczos() {
+        cudaStreamSynchronize(pl->stream);
+        for (void* p : allocs) cudaFree(p);
+    }
+    template <typename X>
+    bloch_status alloc(X** p, size_t n_el) {
+        cudaError_t e = cudaMalloc((void**)p, n_el * sizeof(X));
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (Lanczos basis)");
+        allocs.push_back(*p);
+        return BLOCH_OK;
+    }
+    C* vb(int s, int i) const { return Vb + ((size_t)s * (m + 1) + i) * n3; }
+
+    bloch_status setup() {
+        bloch_status s;
+        nblk = (int)std::max(1LL, std::min<long long>((n3 + 255) / 256, std::max(1, 1024 / std::max(1, B))));
+        if ((s = alloc(&Vb, (size_t)B * (m + 1) * n3)) || (s = alloc(&Tmp, (size_t)m * n3)) ||
+            (s = alloc(&Bc, (size_t)B * n3)) || (s = alloc(&Xc, (size_t)B * n3)) ||
+            (s = alloc(&d_part, (size_t)B * nblk * (m + 1))) || (s = alloc(&d_h, (size_t)B * (m + 1))) ||
+            (s = alloc(&d_Q, (size_t)m * m)) || (s = alloc(&d_nv, (size_t)B)) || (s = alloc(&d_src, (size_t)B)) ||
+            (s = alloc(&d_dst, (size_t)B)) || (s = alloc(&d_s, (size_t)B)))
+            return s;
+        if ((s = ensure_cg<T>(pl, B)) != BLOCH_OK) return s;
+        slots.assign(B, Slot());
+        return BLOCH_OK;
+    }
+
+    bloch_status upload_ll(long long* d, const std::vector<long long>& h) {
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(d, h.data(), sizeof(long long) * h.size(), cudaMemcpyHostToDevice, pl->stream));
+        return BLOCH_OK;
+    }
+
+    // M-norms of Xc[0..nact) -> host
+    bloch_status xnorms(std::vector<double>& nrm) {
+        Workspace<T>& w = ws_of<T>(pl);
+        launch_dot<T>(pl, nact, Xc, Xc, n3, w.dots, w.part2);
+        std::vector<double2> d(nact);
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(d.data(), w.dots, sizeof(double2) * nact, cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        nrm.resize(nact);
+        for (int i = 0; i < nact; ++i) nrm[i] = std::sqrt(std::max(0.0, rho_s * d[i].x));
+        return BLOCH_OK;
+    }
+
+    bloch_status init_slot(int s, int kidx) {
+        Slot& sl = slots[s];
+        sl = Slot();
+        sl.kidx = kidx;
+        for (int a = 0; a < 3; ++a) sl.k[a] = (*klist)[kidx][a];
+        sl.gamma = sl.k[0] == 0.0 && sl.k[1] == 0.0 && sl.k[2] == 0.0;
+        sl.n_eff = sl.gamma ? n_bands - 3 : n_bands;
+        sl.j = 0;
+        sl.H.assign((size_t)(m + 1) * m, cd(0, 0));
+        ++pl->launches;
+        k_start_random<T><<<1024, 256, 0, pl->stream>>>(vb(s, 0), n3, pl->V, 12345ULL, sl.gamma ? 1 : 0);
+        // normalise in the M norm
+        Workspace<T>& w = ws_of<T>(pl);
+        launch_dot<T>(pl, 1, vb(s, 0), vb(s, 0), n3, w.dots, w.part2);
+        double2 d;
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(&d, w.dots, sizeof(double2), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        const double sc = 1.0 / std::sqrt(rho_s * d.x);
+        ++pl->launches;
+        k_scale<T><<<1024, 256, 0, pl->stream>>>(vb(s, 0), vb(s, 0), T(sc), (size_t)n3);
+        return BLOCH_OK;
+    }
+
+    // Ritz analysis of a slot whose basis is full: converge (output) or restart.
+    // Returns true when the slot is finished.
+    bool ritz(int s, bloch_status& err) {
+        Slot& sl = slots[s];
+        std::vector<cd> Hm((size_t)m * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j)
+                Hm[(size_t)i * m + j] = 0.5 * (sl.H[(size_t)i * m + j] + std::conj(sl.H[(size_t)j * m + i]));
+        std::vector<double> w;
+        std::vector<cd> Y;
+        herm_jacobi(m, Hm, w, Y);
+        const double beta = std::abs(sl.H[(size_t)m * m + (m - 1)]);
+        // wanted: largest theta (descending)
+        std::vector<int> idx(m);
+        for (int i = 0; i < m; ++i) idx[i] = m - 1 - i;
+        bool conv = true;
+        for (int i = 0; i < sl.n_eff; ++i) {
+            const double th = w[idx[i]];
+            const double res = beta * std::abs(Y[(size_t)(m - 1) * m + idx[i]]);
+            if (!(th > 0.0) || res > tol_eig * std::fabs(th)) conv = false;
+        }
+        sl.restarts += 1;
+        const bool done = conv || sl.restarts > max_outer;
+        const int kk = done ? sl.n_eff : std::min(m - 1, sl.n_eff + (m - sl.n_eff) / 2);
+        // Q: m x m, columns = the kept Ritz vectors (descending theta), rest zero
+        std::vector<double2> Qh((size_t)m * m, make_double2(0, 0));
+        for (int c = 0; c < kk; ++c)
+            for (int i = 0; i < m; ++i) {
+                const cd y = Y[(size_t)i * m + idx[c]];
+                Qh[(size_t)i * m + c] = make_double2(y.real(), y.imag());
+            }
+        cudaError_t e = cudaMemcpyAsync(d_Q, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice,
+                                        pl->stream);
+        if (e != cudaSuccess) {
+            err = set_cuda_error(e, "Lanczos restart upload");
+            return true;
+        }
+        dim3 gb((unsigned)std::min<long long>((n3 + 127) / 128, 8192), 1);
+        ++pl->launches;
+        k_basis<T><<<gb, 128, 0, pl->stream>>>(vb(s, 0), Tmp, d_Q, m, n3);
+        if (done) {
+            const double lam_scale = pl->Kscale / pl->rho_ref;
+            double* om = omega_out + (size_t)sl.kidx * n_bands;
+            int b0 = 0;
+            if (sl.gamma)
+                for (; b0 < std::min(3, n_bands); ++b0) om[b0] = 0.0;
+            // ascending lambda = descending theta = order of the kept columns
+            for (int i = 0; i < sl.n_eff; ++i) {
+                const double th = w[idx[i]];
+                om[b0 + i] = th > 0 ? std::sqrt(lam_scale / th) : 0.0;
+            }
+            st->outer_iterations += sl.restarts;
+            double mx = 0;
+            for (int i = 0; i < sl.n_eff; ++i) {
+                const double th = w[idx[i]];
+                mx = std::max(mx, beta * std::abs(Y[(size_t)(m - 1) * m + idx[i]]) / std::max(std::fabs(th), 1e-300));
+            }
+            st->max_rel_residual = std::max(st->max_rel_residual, mx);
+            if (!conv) any_unconverged = true;
+            if (vecs_out) {
+                C* out = (C*)vecs_out + (size_t)sl.kidx * n_bands * n3;
+                const double nv = 1.0 / std::sqrt(pl->rho_ref);
+                if (sl.gamma) {
+                    cudaMemsetAsync(out, 0, sizeof(C) * std::min(3, n_bands) * n3, pl->stream);
+                    std::vector<double2> one(1, make_double2(1.0 / std::sqrt(pl->rho_ref * rho_s), 0.0));
+                    for (int c = 0; c < std::min(3, n_bands); ++c) {
+                        const C cv = mk(T(one[0].x), T(0));
+                        cudaMemcpyAsync(out + (size_t)c * n3 + (size_t)c * pl->V, &cv, sizeof(C),
+                                        cudaMemcpyHostToDevice, pl->stream);
+                        cudaStreamSynchronize(pl->stream);
+                    }
+                }
+                ++pl->launches;
+                k_scale<T><<<1024, 256, 0, pl->stream>>>(Tmp, out + (size_t)b0 * n3, T(nv), (size_t)sl.n_eff * n3);
+            }
+            cudaStreamSynchronize(pl->stream);
+            return true;
+        }
+        // restart: V[0..kk) = V Y_kk, V[kk] = v_{m}; H = [diag(theta); b^T]
+        cudaMemcpyAsync(vb(s, 0), Tmp, sizeof(C) * kk * n3, cudaMemcpyDeviceToDevice, pl->stream);
+        cudaMemcpyAsync(vb(s, kk), vb(s, m), sizeof(C) * n3, cudaMemcpyDeviceToDevice, pl->stream);
+        std::fill(sl.H.begin(), sl.H.end(), cd(0, 0));
+        const cd bm = sl.H.size() ? cd(beta, 0) : cd(0, 0);
+        for (int c = 0; c < kk; ++c) {
+            sl.H[(size_t)c * m + c] = w[idx[c]];
+            sl.H[(size_t)kk * m + c] = bm * Y[(size_t)(m - 1) * m + idx[c]];
+        }
+        sl.j = kk;
+        return false;
+    }
+
+    bloch_status run() {
+        bloch_status s;
+        nact = 0;
+        while (nact < B && next_k < order.size()) {
+            if ((s = init_slot(nact, order[next_k++])) != BLOCH_OK) return s;
+            ++nact;
+        }
+        while (nact > 0) {
+            // gather v_j of every slot
+            std::vector<long long> src(nact), dst(nact);
+            std::vector<double> one(nact, 1.0);
+            std::vector<int> nv(nact);
+            for (int i = 0; i < nact; ++i) {
+                src[i] = ((long long)i * (m + 1) + slots[i].j) * n3;
+                dst[i] = (long long)i * n3;
+                nv[i] = slots[i].j + 1;
+            }
+            if ((s = upload_ll(d_src, src)) || (s = upload_ll(d_dst, dst))) return s;
+            BLOCH_CUDA_CHECK_RET(
+                cudaMemcpyAsync(d_s, one.data(), sizeof(double) * nact, cudaMemcpyHostToDevice, pl->stream));
+            BLOCH_CUDA_CHECK_RET(
+                cudaMemcpyAsync(d_nv, nv.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, pl->stream));
+            dim3 gc(nblk, nact);
+            ++pl->launches;
+            k_copy_scaled<T><<<gc, 256, 0, pl->stream>>>(Vb, d_src, Bc, d_dst, d_s, n3);
+            // w = A^-1 (M v_j)
+            std::vector<double> kv((size_t)nact * 3);
+            for (int i = 0; i < nact; ++i)
+                for (int a = 0; a < 3; ++a) kv[(size_t)i * 3 + a] = slots[i].k[a];
+            if ((s = set_k<T>(pl, nact, kv.data())) != BLOCH_OK) return s;
+            long long cg_it = 0;
+            s = pcg_run<T>(pl, nact, Bc, Xc, rho_s, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
+            st->cg_iterations += cg_it;
+            st->k_applies += cg_it;
+            st->linear_solves += nact;
+            if (s != BLOCH_OK && s != BLOCH_ENOTCONV_CG) return s;
+            // two passes of classical Gram-Schmidt in the M inner product
+            std::vector<cd> hsum((size_t)nact * (m + 1), cd(0, 0));
+            int maxnv = 0;
+            for (int i = 0; i < nact; ++i) maxnv = std::max(maxnv, nv[i]);
+            for (int pass = 0; pass < 2; ++pass) {
+                dim3 gd(nblk, maxnv, nact);
+                ++pl->launches;
+                k_vdots<T><<<gd, 256, 0, pl->stream>>>(Vb, (long long)(m + 1) * n3, Xc, n3, d_nv, n3, maxnv, d_part);
+                ++pl->launches;
+                k_vdots_final<<<nact, 64, 0, pl->stream>>>(d_part, nblk, maxnv, rho_s, d_h);
+                dim3 ga(nblk, nact);
+                ++pl->launches;
+                k_vaxpy<T><<<ga, 256, 0, pl->stream>>>(Vb, (long long)(m + 1) * n3, Xc, n3, d_h, d_nv, n3, maxnv);
+                std::vector<double2> hh((size_t)nact * maxnv);
+                BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(hh.data(), d_h, sizeof(double2) * hh.size(),
+                                                     cudaMemcpyDeviceToHost, pl->stream));
+                BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+                for (int i = 0; i < nact; ++i)
+                    for (int t = 0; t < nv[i]; ++t)
+                        hsum[(size_t)i * (m + 1) + t] += cd(hh[(size_t)i * maxnv + t].x, hh[(size_t)i * maxnv + t].y);
+            }
+            std::vector<double> nrm;
+            if ((s = xnorms(nrm)) != BLOCH_OK) return s;
+            std::vector<double> inv(nact);
+            for (int i = 0; i < nact; ++i) {
+                Slot& sl = slots[i];
+                for (int t = 0; t <= sl.j; ++t) sl.H[(size_t)t * m + sl.j] = hsum[(size_t)i * (m + 1) + t];
+                sl.H[(size_t)(sl.j + 1) * m + sl.j] = nrm[i];
+                inv[i] = nrm[i] > 0 ? 1.0 / nrm[i] : 0.0;
+                src[i] = (long long)i * n3;
+                dst[i] = ((long long)i * (m + 1) + sl.j + 1) * n3;
+            }
+            if ((s = upload_ll(d_src, src)) || (s = upload_ll(d_dst, dst))) return s;
+            BLOCH_CUDA_CHECK_RET(
+                cudaMemcpyAsync(d_s, inv.data(), sizeof(double) * nact, cudaMemcpyHostToDevice, pl->stream));
+            ++pl->launches;
+            k_copy_scaled<T><<<gc, 256, 0, pl->stream>>>(Xc, d_src, Vb, d_dst, d_s, n3);
+            BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+            // advance; analyse full bases
+            std::vector<int> finished;
+            for (int i = 0; i < nact; ++i) {
+                slots[i].j += 1;
+                if (slots[i].j == m) {
+                    bloch_status err = BLOCH_OK;
+                    if (ritz(i, err)) finished.push_back(i);
+                    if (err != BLOCH_OK) return err;
+                }
+            }
+            if (!finished.empty()) {
+                cudaStreamSynchronize(pl->stream);
+                std::vector<char> hole(nact, 0);
+                for (int f : finished) hole[f] = 1;
+                for (int f : finished)
+                    if (next_k < order.size()) {
+                        if ((s = init_slot(f, order[next_k++])) != BLOCH_OK) return s;
+                        hole[f] = 0;
+                    }
+                int last = nact - 1;
+                for (int h = 0; h < nact; ++h) {
+                    if (!hole[h]) continue;
+                    while (last > h && hole[last]) --last;
+                    if (last <= h) break;
+                    const int nvv = slots[last].j + 1;
+                    BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vb(h, 0), vb(last, 0), sizeof(C) * nvv * n3,
+                                                         cudaMemcpyDeviceToDevice, pl->stream));
+                    slots[h] = slots[last];
+                    hole[h] = 0;
+                    hole[last] = 1;
+                }
+                int na = 0;
+                for (int h = 0; h < nact; ++h)
+                    if (!hole[h]) na = h + 1;
+                nact = na;
+            }
+        }
+        return BLOCH_OK;
+    }
+};
+
+template <typename T>
+static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<double, 3>>& ks, int n_bands,
+                                double* omega_out, void* vecs_out, bloch_stats* st) {
+    if (!pl->uniform_rho)
+        return set_error(BLOCH_EUNSUPPORTED, "the Lanczos solver needs a uniform density (use subspace iteration)");
+    Lanczos<T> S;
+    S.pl = pl;
+    S.n3 = 3 * pl->V;
+    S.n_bands = n_bands;
+    S.m = pl->opt.ncv > 0 ? pl->opt.ncv : std::max(2 * n_bands + 1, 20);
+    S.m = (int)std::min<long long>(S.m, 3 * pl->V - 4);
+    if (S.m > 63) return set_error(BLOCH_EUNSUPPORTED, "Lanczos basis above 63 vectors is not supported");
+    if (S.m < n_bands + 1) return set_error(BLOCH_EINVAL, "Lanczos basis too small for the requested bands");
+    S.rho_s = pl->rho_uniform_scaled;
+    S.tol_eig = pl->opt.tol_eig;
+    S.tol_lin = pl->opt.tol_lin;
+    if (std::is_same<T, float>::value) S.tol_lin = std::max(S.tol_lin, 3e-6);
+    S.max_outer = pl->opt.max_outer;
+    S.max_cg = pl->opt.max_cg;
+    S.klist = &ks;
+    S.omega_out = omega_out;
+    S.vecs_out = vecs_out;
+    S.st = st;
+    for (size_t i = 0; i < ks.size(); ++i) {
+        const bool gamma = ks[i][0] == 0.0 && ks[i][1] == 0.0 && ks[i][2] == 0.0;
+        if (gamma && n_bands <= 3) {
+            for (int b = 0; b < n_bands; ++b) omega_out[i * n_bands + b] = 0.0;
+            continue;
+        }
+        S.order.push_back((int)i);
+    }
+    if (S.order.empty()) return BLOCH_OK;
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const size_t per_slot = (size_t)(S.m + 1 + 2 + 5) * S.n3 * sizeof(cplx_t<T>);
+    long long Bmax = std::max<long long>(1, (long long)(0.5 * (double)freeb / (double)per_slot));
+    Bmax = std::min<long long>(Bmax, 64);
+    int B = pl->opt.k_batch > 0 ? pl->opt.k_batch : (int)Bmax;
+    S.B = std::max(1, std::min<int>(B, (int)S.order.size()));
+    bloch_status s = S.setup();
+    if (s != BLOCH_OK) return s;
+    s = S.run();
+    if (s != BLOCH_OK) return s;
+    if (S.any_unconverged) return set_error(BLOCH_ENOTCONV_EIG, "Lanczos reached its restart cap");
     return BLOCH_OK;
 }
 
@@ -729,7 +1150,10 @@ bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_lis
         else
             s = run_subspace<double>(pl, ks, n_bands, omega_out, vecs_out, &st, false);
     } else {
-        s = set_error(BLOCH_EUNSUPPORTED, "Lanczos method not available in this build");
+        if (pl->opt.precision == BLOCH_FP32)
+            s = run_lanczos<float>(pl, ks, n_bands, omega_out, vecs_out, &st);
+        else
+            s = run_lanczos<double>(pl, ks, n_bands, omega_out, vecs_out, &st);
     }
     cudaStreamSynchronize(pl->stream);
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

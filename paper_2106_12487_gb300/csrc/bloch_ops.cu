@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -38,6 +39,9 @@ template <> const double2* tw_of<double>(const bloch_plan* pl, int axis) { retur
 template <typename T> static const T* ctab_of(const bloch_plan* pl);
 template <> const float* ctab_of<float>(const bloch_plan* pl) { return pl->d_Cf; }
 template <> const double* ctab_of<double>(const bloch_plan* pl) { return pl->d_Cd; }
+template <typename T> static const T* cpk_of(const bloch_plan* pl);
+template <> const float* cpk_of<float>(const bloch_plan* pl) { return pl->d_Cpf; }
+template <> const double* cpk_of<double>(const bloch_plan* pl) { return pl->d_Cpd; }
 template <typename T> static const T* rtab_of(const bloch_plan* pl);
 template <> const float* rtab_of<float>(const bloch_plan* pl) { return pl->d_rf; }
 template <> const double* rtab_of<double>(const bloch_plan* pl) { return pl->d_rd; }
@@ -205,7 +209,192 @@ bloch_status set_k(bloch_plan* pl, int nb, const double* k_host) {
 
 // ------------------------------------------------------------ operators
 template <typename T>
+void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale);
+
+// ------------------------------------------------ fast two-stage passes
+static bool fast_axis(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
+static bool fast_x(int N) { return N == 16 || N == 32 || N == 64 || N == 128; }
+
+template <typename K>
+static void fast_attr(K k) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
+template <typename T, int RA, int RB, bool Z>
+static void set_fast_attrs_n() {
+    fast_attr(k_fpass_axis<T, +1, 1, RA, RB>);
+    fast_attr(k_fpass_axis<T, -1, 1, RA, RB>);
+    if constexpr (Z) {
+        fast_attr(k_fpass_z_strain<T, RA, RB>);
+        fast_attr(k_fpass_z_div<T, RA, RB>);
+        if constexpr (RB <= 8) fast_attr(k_fpass_x_stress<T, RA, RB>);
+    }
+}
+
+// the z and x fast passes exist in FP32 only (their register budget)
+template <typename T>
+static void set_fast_attrs() {
+    constexpr bool Z = std::is_same<T, float>::value;
+    set_fast_attrs_n<T, 4, 4, Z>();
+    set_fast_attrs_n<T, 8, 4, Z>();
+    set_fast_attrs_n<T, 8, 8, Z>();
+    set_fast_attrs_n<T, 16, 8, Z>();
+    set_fast_attrs_n<T, 16, 16, false>();
+}
+
+// P for the fast y/z passes: 32 pencils (256 B rows in FP32), fewer if the axis has fewer
+static int fast_P(long long npen, int pmax) {
+    int P = pmax;
+    while (P > 1 && (long long)(P / 2) >= npen) P >>= 1;
+    return P;
+}
+
+template <typename T, int RA, int RB>
+static void fast_y(bloch_plan* pl, int DIR, int nb, cplx_t<T>* E) {
+    const Geo& g = geo_of<T>(pl);
+    constexpr int N = RA * RB;
+    const long long npen = (long long)pl->Nx * pl->Nz;
+    int P = fast_P(npen, 32);
+    while (P > 1 && (size_t)(N + N * P) * sizeof(cplx_t<T>) > 96 * 1024) P >>= 1;
+    const size_t smem = (size_t)(N + N * P) * sizeof(cplx_t<T>);
+    dim3 gr((unsigned)((npen + P - 1) / P), nb * 6);
+    ++pl->launches;
+    if (DIR > 0)
+        k_fpass_axis<T, +1, 1, RA, RB><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g, P, T(1));
+    else
+        k_fpass_axis<T, -1, 1, RA, RB><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g, P, T(1));
+}
+
+template <typename T, int RA, int RB>
+static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
+    const Geo& g = geo_of<T>(pl);
+    constexpr int N = RA * RB;
+    const long long npen = (long long)pl->Nx * pl->Ny;
+    const int P = 128 / RA;
+    const size_t smem = (size_t)(N + 2 * N * P) * sizeof(cplx_t<T>);
+    dim3 gr((unsigned)((npen + P - 1) / P), nb);
+    ++pl->launches;
+    k_fpass_z_strain<T, RA, RB><<<gr, P * RA, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
+                                                                    tw_of<T>(pl, 2), g, P);
+}
+
+template <typename T, int RA, int RB>
+static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale) {
+    const Geo& g = geo_of<T>(pl);
+    constexpr int N = RA * RB;
+    const long long npen = (long long)pl->Nx * pl->Ny;
+    const int P = 128 / RA;
+    const size_t smem = (size_t)(N + 2 * N * P) * sizeof(cplx_t<T>);
+    dim3 gr((unsigned)((npen + P - 1) / P), nb);
+    ++pl->launches;
+    k_fpass_z_div<T, RA, RB><<<gr, P * RA, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
+                                                                 tw_of<T>(pl, 2), g, P, out_scale);
+}
+
+template <typename T, int RA, int RB>
+static void fast_x3(bloch_plan* pl, int nb) {
+    const Geo& g = geo_of<T>(pl);
+    constexpr int N = RA * RB;
+    constexpr int LD = N + N / 16;
+    const int P = 128 / RA;
+    const size_t smem = (size_t)(N + 2 * P * LD) * sizeof(cplx_t<T>);
+    const long long rows = (long long)pl->Ny * pl->Nz;
+    dim3 gr((unsigned)((rows + P - 1) / P), nb);
+    ++pl->launches;
+    k_fpass_x_stress<T, RA, RB><<<gr, P * RA, smem, pl->stream>>>(ws_of<T>(pl).E, pl->d_ids, cpk_of<T>(pl),
+                                                                   tw_of<T>(pl, 0), g, P);
+}
+
+#define BLOCH_FAST_SWITCH(N, FN, ...)              \
+    switch (N) {                                    \
+        case 16: FN<T, 4, 4>(__VA_ARGS__); break;   \
+        case 32: FN<T, 8, 4>(__VA_ARGS__); break;   \
+        case 64: FN<T, 8, 8>(__VA_ARGS__); break;   \
+        case 128: FN<T, 16, 8>(__VA_ARGS__); break; \
+        default: FN<T, 16, 16>(__VA_ARGS__); break; \
+    }
+#define BLOCH_FAST_SWITCH_Z(N, FN, ...)             \
+    switch (N) {                                    \
+        case 16: FN<T, 4, 4>(__VA_ARGS__); break;   \
+        case 32: FN<T, 8, 4>(__VA_ARGS__); break;   \
+        case 64: FN<T, 8, 8>(__VA_ARGS__); break;   \
+        default: FN<T, 16, 8>(__VA_ARGS__); break;  \
+    }
+
+template <typename T>
 void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
+    if (pl->fast) {
+        Workspace<T>& w = ws_of<T>(pl);
+        const Geo& g = geo_of<T>(pl);
+        const TileCfg& t = tile_of<T>(pl);
+        const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,
+                        pyz = (long long)pl->Ny * pl->Nz;
+        const bool fz = fast_x(pl->Nz) && std::is_same<T, float>::value;
+        const bool fy = fast_axis(pl->Ny);
+        const bool fx = fast_x(pl->Nx) && std::is_same<T, float>::value;
+        dim3 g1((unsigned)((pxy + t.Pz5 - 1) / t.Pz5), nb);
+        dim3 g2((unsigned)((pxz + t.Py2 - 1) / t.Py2), nb * 6);
+        dim3 g3((unsigned)((pyz + t.Px7 - 1) / t.Px7), nb);
+        bool done1 = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (fz) {
+                BLOCH_FAST_SWITCH_Z(pl->Nz, fast_z1, pl, nb, u);
+                done1 = true;
+            }
+        }
+        if (!done1) {
+            ++pl->launches;
+            k_pass_z_strain<T><<<g1, 256, t.smem_z5, pl->stream>>>(u, w.E, w.qtab, tw_of<T>(pl, 2), g, t.Pz5);
+        }
+        if (fy) {
+            BLOCH_FAST_SWITCH(pl->Ny, fast_y, pl, +1, nb, w.E);
+        } else {
+            ++pl->launches;
+            k_pass_axis<T, +1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+        }
+        bool done3 = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (fx) {
+                switch (pl->Nx) {
+                    case 16: fast_x3<T, 4, 4>(pl, nb); break;
+                    case 32: fast_x3<T, 8, 4>(pl, nb); break;
+                    case 64: fast_x3<T, 8, 8>(pl, nb); break;
+                    default: fast_x3<T, 16, 8>(pl, nb); break;
+                }
+                done3 = true;
+            }
+        }
+        if (!done3) {
+            ++pl->launches;
+            k_pass_x_stress<T><<<g3, 256, t.smem_x7, pl->stream>>>(w.E, pl->d_ids, ctab_of<T>(pl), tw_of<T>(pl, 0),
+                                                                    g, t.Px7);
+        }
+        if (fy) {
+            BLOCH_FAST_SWITCH(pl->Ny, fast_y, pl, -1, nb, w.E);
+        } else {
+            ++pl->launches;
+            k_pass_axis<T, -1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+        }
+        bool done5 = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (fz) {
+                BLOCH_FAST_SWITCH_Z(pl->Nz, fast_z5, pl, nb, out, out_scale);
+                done5 = true;
+            }
+        }
+        if (!done5) {
+            ++pl->launches;
+            k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5,
+                                                                out_scale);
+        }
+        return;
+    }
+    launch_K_generic<T>(pl, nb, u, out, out_scale);
+}
+
+template <typename T>
+void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
     Workspace<T>& w = ws_of<T>(pl);
     const Geo& g = geo_of<T>(pl);
     const TileCfg& t = tile_of<T>(pl);
@@ -367,6 +556,8 @@ void bloch_default_options(bloch_options* opt) {
     opt->block = 0;
     opt->k_batch = 0;
     opt->ncv = 0;
+    opt->warm_start = 1;
+    opt->fft_variant = 0;
 }
 
 const char* bloch_last_error(void) { return g_last_error.c_str(); }
@@ -400,6 +591,8 @@ void bloch_plan_destroy(bloch_plan* pl) {
     cudaFree(pl->d_ids);
     cudaFree(pl->d_Cf);
     cudaFree(pl->d_Cd);
+    cudaFree(pl->d_Cpf);
+    cudaFree(pl->d_Cpd);
     cudaFree(pl->d_rf);
     cudaFree(pl->d_rd);
     for (int a = 0; a < 3; ++a) {
@@ -549,6 +742,20 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
             rd[g] = rho[g] / (pl->rho_ref * (double)V);
             rf[g] = (float)rd[g];
         }
+        std::vector<double> pd((size_t)G * 21);
+        std::vector<float> pf((size_t)G * 21);
+        for (int g = 0; g < G; ++g) {
+            int k = 0;
+            for (int i = 0; i < 6; ++i)
+                for (int j = i; j < 6; ++j, ++k) {
+                    pd[(size_t)g * 21 + k] = cd[(size_t)g * 36 + i * 6 + j];
+                    pf[(size_t)g * 21 + k] = (float)pd[(size_t)g * 21 + k];
+                }
+        }
+        CK(dmalloc(&pl->d_Cpd, pd.size(), acc));
+        CK(dmalloc(&pl->d_Cpf, pf.size(), acc));
+        CK(cudaMemcpy(pl->d_Cpd, pd.data(), sizeof(double) * pd.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pl->d_Cpf, pf.data(), sizeof(float) * pf.size(), cudaMemcpyHostToDevice));
         CK(dmalloc(&pl->d_Cd, cd.size(), acc));
         CK(dmalloc(&pl->d_Cf, cf.size(), acc));
         CK(dmalloc(&pl->d_rd, rd.size(), acc));
@@ -576,6 +783,9 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     CK(cudaMallocHost((void**)&pl->h_nactive, sizeof(int)));
     CK(set_smem_attrs<float>());
     CK(set_smem_attrs<double>());
+    set_fast_attrs<float>();
+    set_fast_attrs<double>();
+    pl->fast = pl->opt.fft_variant == 0;
 #undef CK
     for (Geo* gp : {&pl->geo_f, &pl->geo_d}) {
         gp->Nx = pl->Nx;

@@ -1,0 +1,378 @@
+// Two-stage register FFT pass kernels for power-of-two axes N = RA * RB
+// (N <= 256), the fast path of the stiffness operator.
+//
+// Each pencil is transformed in two Stockham stages: stage 1 (radix RA, no
+// twiddles) loads its RA inputs straight from HBM into registers and writes
+// to a shared-memory exchange buffer; stage 2 (radix RB, twiddles
+// w_N^(r j)) reads the exchange buffer and either writes HBM directly or
+// keeps its outputs in registers for the pointwise epilogue.  Only one
+// shared-memory round trip and one barrier per component remain, and every
+// global access is a coalesced row of consecutive pencils (y, z passes) or of
+// consecutive elements of a row (x pass).
+//
+// Stage indexing (Stockham autosort, Ns = 1 then Ns = RA):
+//   stage 1 task (p, j), j < RB: reads n = j + r RB, writes slot j RA + r
+//   stage 2 task (p, j), j < RA: reads slot j + r RA, twiddle w_N^(r j),
+//                                writes n = j + r RA
+// The inverse x transform uses radices (RA, RB) and the forward one (RB, RA),
+// so the elements a thread holds after the inverse are exactly the inputs of
+// its forward stage 1: the stress is applied in registers.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "passes.cuh"
+
+namespace bloch {
+
+template <typename C>
+__device__ __forceinline__ C twmul(C v, C w, int dir) {
+    if (dir > 0) w.y = -w.y;
+    return cmul(v, w);
+}
+
+// --------------------------------------------------- y / z pass (in place ok)
+// blockIdx.y = batch*ncomp + comp (offset blockIdx.y * V)
+template <typename T, int DIR, int AXIS, int RA, int RB>
+__global__ void __launch_bounds__(256) k_fpass_axis(const cplx_t<T>* in, cplx_t<T>* out,
+                                                    const cplx_t<T>* __restrict__ twa, Geo g, int P,
+                                                    T out_scale) {
+    using C = cplx_t<T>;
+    constexpr int N = RA * RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const long long npen = AXIS == 1 ? (long long)g.Nx * g.Nz : (long long)g.Nx * g.Ny;
+    const long long pi0 = (long long)blockIdx.x * P;
+    const int np = (int)min((long long)P, npen - pi0);
+    const size_t off = (size_t)blockIdx.y * g.V;
+    const C* src = in + off;
+    C* dst = out + off;
+    const long long plane = (long long)g.Nx * g.Ny;
+    auto addr = [&](int p, int n) -> size_t {
+        const long long pi = pi0 + p;
+        if (AXIS == 1) return (size_t)(pi / g.Nx) * plane + (size_t)n * g.Nx + (size_t)(pi % g.Nx);
+        return (size_t)n * plane + pi;
+    };
+    for (int i = tid; i < N; i += nthr) tw[i] = twa[i];
+    for (int t = tid; t < P * RB; t += nthr) {
+        const int p = t % P, j = t / P;
+        C v[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) v[r] = (p < np) ? src[addr(p, j + r * RB)] : mk(T(0), T(0));
+        RegDFT<RA, DIR, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < RA; ++r) buf[(j * RA + r) * P + p] = v[r];
+    }
+    __syncthreads();
+    for (int t = tid; t < P * RA; t += nthr) {
+        const int p = t % P, j = t / P;
+        C v[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) v[r] = buf[(j + r * RA) * P + p];
+#pragma unroll
+        for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j], DIR);
+        RegDFT<RB, DIR, C>::run(v);
+        if (p < np) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) dst[addr(p, j + r * RA)] = cscale(v[r], out_scale);
+        }
+    }
+}
+
+// --------------------------------------------------- pass 1: strain + inverse z
+// One thread per stage-2 task (blockDim.x == P * RA).  The z transform of
+// q_z U_k cannot be formed from that of U_k (q_z varies along the pencil), but
+// q_x, q_y are constant on a z pencil, so with a_k = F_z^-1(U_k) and
+// b_k = F_z^-1(q_z U_k) the six Voigt strains are
+//   g_xx = q_x a_x, g_yy = q_y a_y, g_zz = b_z, g_yz = q_y a_z + b_y,
+//   g_xz = q_x a_z + b_x, g_xy = q_y a_x + q_x a_y.
+// Each displacement component is read once; components are taken in the
+// order z, x, y so that only a_z and a_x are carried between them.
+template <typename T, int RA, int RB>
+__global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
+                                                        const T* __restrict__ qtab,
+                                                        const cplx_t<T>* __restrict__ twz, Geo g, int P) {
+    using C = cplx_t<T>;
+    constexpr int N = RA * RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* bufA = tw + N;        // N * P
+    C* bufB = bufA + N * P;  // N * P
+    const int tid = threadIdx.x;
+    const int b = blockIdx.y;
+    const long long plane = (long long)g.Nx * g.Ny;
+    const long long pi0 = (long long)blockIdx.x * P;
+    const int np = (int)min((long long)P, plane - pi0);
+    const C* Ub = U + (size_t)b * 3 * g.V;
+    C* Eb = E + (size_t)b * 6 * g.V;
+    const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
+    const T* qyt = qxt + g.Nx;
+    const T* qzt = qyt + g.Ny;
+    for (int i = tid; i < N; i += blockDim.x) tw[i] = twz[i];
+    // stage-2 task of this thread
+    const int p2 = tid % P, j2 = tid / P;
+    const int pp = p2 < np ? p2 : 0;
+    const long long pi = pi0 + pp;
+    const T qx = qxt[(int)(pi % g.Nx)], qy = qyt[(int)(pi / g.Nx)];
+    // stage-1 task (threads tid < P * RB)
+    const int p1 = tid % P, j1 = tid / P;
+    const bool st1 = tid < P * RB;
+    C az[RB], ax[RB];
+    auto store = [&](int c, int r, C v) {
+        if (p2 < np) Eb[(size_t)c * g.V + (size_t)(j2 + r * RA) * plane + pi0 + p2] = v;
+    };
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        const int k = kk == 0 ? 2 : kk - 1;   // z, x, y
+        if (st1) {
+            C u[RA], v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                const int n = j1 + r * RB;
+                u[r] = (p1 < np) ? Ub[(size_t)k * g.V + (size_t)n * plane + pi0 + p1] : mk(T(0), T(0));
+                v[r] = u[r];
+            }
+            RegDFT<RA, +1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) bufA[(j1 * RA + r) * P + p1] = v[r];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) u[r] = cscale(u[r], qzt[j1 + r * RB]);
+            RegDFT<RA, +1, C>::run(u);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) bufB[(j1 * RA + r) * P + p1] = u[r];
+        }
+        __syncthreads();
+        C a[RB], bb[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            a[r] = bufA[(j2 + r * RA) * P + p2];
+            bb[r] = bufB[(j2 + r * RA) * P + p2];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 1; r < RB; ++r) {
+            a[r] = twmul(a[r], tw[r * j2], +1);
+            bb[r] = twmul(bb[r], tw[r * j2], +1);
+        }
+        RegDFT<RB, +1, C>::run(a);
+        RegDFT<RB, +1, C>::run(bb);
+        if (k == 2) {          // z: g_zz; keep a_z
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                store(2, r, bb[r]);
+                az[r] = a[r];
+            }
+        } else if (k == 0) {   // x: g_xx, g_xz; keep a_x
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                store(0, r, cscale(a[r], qx));
+                store(4, r, cadd(cscale(az[r], qx), bb[r]));
+                ax[r] = a[r];
+            }
+        } else {               // y: g_yy, g_yz, g_xy
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                store(1, r, cscale(a[r], qy));
+                store(3, r, cadd(cscale(az[r], qy), bb[r]));
+                store(5, r, cadd(cscale(ax[r], qy), cscale(a[r], qx)));
+            }
+        }
+    }
+}
+
+// --------------------------------------------------- pass 5: forward z + divergence
+// One thread per stage-2 task (blockDim.x == P * RA); the three output
+// components of its RB elements are accumulated in registers:
+//   out_x = q_x S11 + q_y S12 + q_z S13, out_y = q_x S12 + q_y S22 + q_z S23,
+//   out_z = q_x S13 + q_y S23 + q_z S33   (S = forward z transform of sigma).
+template <typename T, int RA, int RB>
+__global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restrict__ E, cplx_t<T>* __restrict__ out,
+                                                     const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
+                                                     Geo g, int P, T out_scale) {
+    using C = cplx_t<T>;
+    constexpr int N = RA * RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* bufs = tw + N;   // 2 * N * P
+    const int tid = threadIdx.x;
+    const int b = blockIdx.y;
+    const long long plane = (long long)g.Nx * g.Ny;
+    const long long pi0 = (long long)blockIdx.x * P;
+    const int np = (int)min((long long)P, plane - pi0);
+    const C* Eb = E + (size_t)b * 6 * g.V;
+    C* ob = out + (size_t)b * 3 * g.V;
+    const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
+    const T* qyt = qxt + g.Nx;
+    const T* qzt = qyt + g.Ny;
+    for (int i = tid; i < N; i += blockDim.x) tw[i] = twz[i];
+    const int p2 = tid % P, j2 = tid / P;
+    const int pp = p2 < np ? p2 : 0;
+    const long long pi = pi0 + pp;
+    const T qv[2] = {qxt[(int)(pi % g.Nx)], qyt[(int)(pi / g.Nx)]};
+    const int p1 = tid % P, j1 = tid / P;
+    const bool st1 = tid < P * RB;
+    C acc[3][RB];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        C* buf = bufs + (c & 1) * N * P;
+        if (st1) {
+            C v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r)
+                v[r] = (p1 < np) ? Eb[(size_t)c * g.V + (size_t)(j1 + r * RB) * plane + pi0 + p1] : mk(T(0), T(0));
+            RegDFT<RA, -1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) buf[(j1 * RA + r) * P + p1] = v[r];
+        }
+        __syncthreads();
+        C v[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) v[r] = buf[(j2 + r * RA) * P + p2];
+#pragma unroll
+        for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], -1);
+        RegDFT<RB, -1, C>::run(v);
+        // sigma_c contributes q_b sigma to out_a and q_a sigma to out_b
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int ca = c < 3 ? c : (c == 3 ? 1 : 0);
+        const int cb = c < 3 ? c : (c == 5 ? 1 : 2);
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const T qz = qzt[j2 + r * RA];
+            const T qa = ca == 2 ? qz : qv[ca];
+            const T qb = cb == 2 ? qz : qv[cb];
+            if (c < 3) {
+                acc[ca][r] = cscale(v[r], qa);
+            } else {
+                acc[ca][r] = cadd(acc[ca][r], cscale(v[r], qb));
+                acc[cb][r] = cadd(acc[cb][r], cscale(v[r], qa));
+            }
+        }
+    }
+    if (p2 < np) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const size_t a = (size_t)(j2 + r * RA) * plane + pi0 + p2;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ob[(size_t)i * g.V + a] = cscale(acc[i][r], out_scale);
+        }
+    }
+}
+
+// --------------------------------------------------- pass 3: x rows, stress in registers
+// One thread owns one stage-2 task (row p, j < RA) for all six components:
+// blockDim.x == P * RA is required.  Shared rows are padded (one slot every 16)
+// to spread the strided Stockham writes over the banks.
+__device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
+
+template <typename T, int RA, int RB>
+__global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
+                                                        const T* __restrict__ Cpk,
+                                                        const cplx_t<T>* __restrict__ twx, Geo g, int P) {
+    using C = cplx_t<T>;
+    constexpr int N = RA * RB;
+    constexpr int LD = N + N / 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* bufs = tw + N;   // two exchange buffers of P * LD
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int b = blockIdx.y;
+    const long long rows = (long long)g.Ny * g.Nz;
+    const long long r0 = (long long)blockIdx.x * P;
+    const int nr = (int)min((long long)P, rows - r0);
+    C* Eb = E + (size_t)b * 6 * g.V;
+    for (int i = tid; i < N; i += nthr) tw[i] = twx[i];
+    // stage-2 task of this thread
+    const int j2 = tid % RA, p2 = tid / RA;
+    const bool own = p2 < nr;
+    C s[6][RB];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        C* buf = bufs + (c & 1) * P * LD;
+        // inverse stage 1 (radix RA): tasks (p, j < RB), j fastest
+        for (int t = tid; t < P * RB; t += nthr) {
+            const int j = t % RB, p = t / RB;
+            C v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r)
+                v[r] = (p < nr) ? Eb[(size_t)c * g.V + (size_t)(r0 + p) * N + j + r * RB] : mk(T(0), T(0));
+            RegDFT<RA, +1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) buf[p * LD + xpad(j * RA + r)] = v[r];
+        }
+        __syncthreads();
+        // inverse stage 2 (radix RB), kept in registers
+        {
+            C v[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) v[r] = buf[p2 * LD + xpad(j2 + r * RA)];
+#pragma unroll
+            for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], +1);
+            RegDFT<RB, +1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) s[c][r] = v[r];
+        }
+    }
+    // stress sigma = C_g gamma at the RB owned elements (packed symmetric table, 21 per grain)
+    if (own) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int n = j2 + r * RA;
+            const T* Cg = Cpk + (size_t)ids[(size_t)(r0 + p2) * N + n] * 21;
+            C gam[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) gam[c] = s[c][r];
+            int k = 0;
+            T cij[6][6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int jj = i; jj < 6; ++jj) {
+                    cij[i][jj] = __ldg(Cg + k++);
+                    cij[jj][i] = cij[i][jj];
+                }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                T sr = 0, si = 0;
+#pragma unroll
+                for (int jj = 0; jj < 6; ++jj) {
+                    sr = fma(cij[i][jj], gam[jj].x, sr);
+                    si = fma(cij[i][jj], gam[jj].y, si);
+                }
+                s[i][r] = mk(sr, si);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        C* buf = bufs + (c & 1) * P * LD;
+        // forward stage 1 (radix RB, Ns = 1): the owned elements j2 + r RA are its inputs
+        {
+            C v[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) v[r] = s[c][r];
+            RegDFT<RB, -1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) buf[p2 * LD + xpad(j2 * RB + r)] = v[r];
+        }
+        __syncthreads();
+        // forward stage 2 (radix RA, Ns = RB): tasks (p, j < RB)
+        for (int t = tid; t < P * RB; t += nthr) {
+            const int j = t % RB, p = t / RB;
+            C v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = buf[p * LD + xpad(j + r * RB)];
+#pragma unroll
+            for (int r = 1; r < RA; ++r) v[r] = twmul(v[r], tw[r * j], -1);
+            RegDFT<RA, -1, C>::run(v);
+            if (p < nr) {
+#pragma unroll
+                for (int r = 0; r < RA; ++r) Eb[(size_t)c * g.V + (size_t)(r0 + p) * N + j + r * RB] = v[r];
+            }
+        }
+    }
+}
+
+}  // namespace bloch

@@ -10,6 +10,7 @@
 #include "fft.cuh"
 #include "passes.cuh"
 #include "vec.cuh"
+#include "fpasses.cuh"
 
 namespace bloch {
 
@@ -69,6 +70,8 @@ struct bloch_plan {
     int32_t* d_ids = nullptr;
     float* d_Cf = nullptr;
     double* d_Cd = nullptr;
+    float* d_Cpf = nullptr;        // G x 21 packed upper triangle (fast x pass)
+    double* d_Cpd = nullptr;
     float* d_rf = nullptr;
     double* d_rd = nullptr;
     float2* d_twf[3] = {nullptr, nullptr, nullptr};
@@ -79,6 +82,7 @@ struct bloch_plan {
     bloch::Geo geo_f, geo_d;
     bloch::TileCfg tile_f, tile_d;
     int nblk_max;
+    bool fast = true;              // use the two-stage register FFT passes where the axis allows
 
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;

@@ -49,12 +49,15 @@ __global__ void k_scale(const cplx_t<T>* in, cplx_t<T>* out, T s, size_t n) {
         out[i] = cscale(in[i], s);
 }
 
+// voxel index -> (x, y, z) in 32-bit unsigned arithmetic (V < 2^31 for every
+// supported grid)
 template <typename T>
-__device__ __forceinline__ void voxel_q(const T* qb, const Geo& g, long long v, T& ax, T& ay, T& az) {
-    const int x = (int)(v % g.Nx);
-    const long long t = v / g.Nx;
-    const int y = (int)(t % g.Ny);
-    const int z = (int)(t / g.Ny);
+__device__ __forceinline__ void voxel_q(const T* qb, const Geo& g, unsigned v, T& ax, T& ay, T& az) {
+    const unsigned nx = (unsigned)g.Nx, ny = (unsigned)g.Ny;
+    const unsigned t = v / nx;
+    const int x = (int)(v - t * nx);
+    const unsigned z = t / ny;
+    const int y = (int)(t - z * ny);
     ax = qb[x];
     ay = qb[g.Nx + y];
     az = qb[g.Nx + g.Ny + z];
@@ -95,8 +98,7 @@ __global__ void k_precond(const cplx_t<T>* r, cplx_t<T>* z, const T* __restrict_
     const T* qb = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const C* rb = r + (size_t)b * 3 * g.V;
     C* zb = z + (size_t)b * 3 * g.V;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.V;
-         v += (long long)gridDim.x * blockDim.x) {
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
         T ax, ay, az;
         voxel_q(qb, g, v, ax, ay, az);
         C rv[3] = {rb[v], rb[g.V + v], rb[2 * g.V + v]};
@@ -178,8 +180,7 @@ __global__ void k_cg_init(const cplx_t<T>* bvec, const cplx_t<T>* Ax, cplx_t<T>*
     const size_t off = (size_t)b * 3 * g.V;
     const T* qb = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     T acc[3] = {T(0), T(0), T(0)};
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.V;
-         v += (long long)gridDim.x * blockDim.x) {
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
         C rv[3], zv[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -221,8 +222,7 @@ __global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, cons
     const T alpha = act ? T(sys[b].alpha) : T(0);
     T acc[2] = {T(0), T(0)};
     if (act) {
-        for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.V;
-             v += (long long)gridDim.x * blockDim.x) {
+        for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
             C rv[3], zv[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -264,8 +264,7 @@ __global__ void k_cg_pupdate(const cplx_t<T>* r, cplx_t<T>* p, const T* __restri
     const size_t off = (size_t)b * 3 * g.V;
     const T* qb = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T beta = T(sys[b].beta);
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.V;
-         v += (long long)gridDim.x * blockDim.x) {
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
         C rv[3], zv[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) rv[c] = r[off + c * g.V + v];

@@ -39,15 +39,19 @@ def rel(a, b):
 
 
 GRIDS = [(4, 4, 4), (6, 6, 6), (6, 4, 5), (16, 16, 16), (32, 32, 32), (24, 20, 12), (9, 7, 10),
-         (64, 32, 16), (8, 1, 1), (4, 4, 1), (1, 1, 1), (128, 2, 3)]
+         (64, 32, 16), (8, 1, 1), (4, 4, 1), (1, 1, 1), (128, 2, 3), (16, 128, 64), (256, 16, 32),
+         (64, 64, 256), (128, 15, 21)]
 
 
 @pytest.mark.parametrize("grid", GRIDS)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_apply_K_matches_oracle(B, grid, prec):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_apply_K_matches_oracle(B, grid, prec, variant):
+    """Both kernel variants (two-stage register FFT passes, shared-memory
+    Stockham passes) against the oracle."""
     p = synth.small_polycrystal(grid, 5, 3)
     med = O.Medium.from_problem(p)
-    plan = B.Plan.from_problem(p, precision=prec)
+    plan = B.Plan.from_problem(p, precision=prec, fft_variant=variant)
     ks = np.array([[0.31, -0.12, 0.77], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]]) * math.pi / 1e-3
     u = synth.random_field(grid, 11, batch=3)
     out = to_dev(np.zeros_like(u), prec)
