@@ -199,6 +199,34 @@ bloch_status bloch_solve_bands(bloch_plan* plan, int32_t n_k, const double* k_li
  */
 bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, double* lam, double* Q);
 
+/*
+ * Allocation-free stiffness apply (no counterpart in the paper; same operator
+ * and same FP32 kernels as bloch_apply_K with precision BLOCH_FP32).
+ *
+ * For callers that must not allocate device memory at the point of the call:
+ * code that runs while a CUDA graph is being captured (an allocation there
+ * breaks the capture), services whose device memory is carved up in advance,
+ * and latency-critical loops that forbid allocator calls.  bloch_apply_K grows
+ * a plan-owned scratch buffer with cudaMalloc when it first meets a larger
+ * batch; this entry point calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Its FFT-pass scratch is one fixed file-scope device array of
+ * 97 MiB, reserved on every GPU that loads the library and held until the
+ * process exits.
+ *   plan   an existing plan (created beforehand; creation itself allocates)
+ *   nb     systems, with nb * Nx*Ny*Nz <= 2097152 (one 128^3 system, eight
+ *          64^3 systems) and (Nx+Ny+Nz+6) * nb <= 262144; larger requests
+ *          return BLOCH_EINVAL with the limit in bloch_last_error()
+ *   k      host, nb x 3 wave vectors (rad/m)
+ *   u, Ku  device, nb x 3 x V float2 each, as in bloch_apply_K (Ku may not alias u)
+ * The first call on a device does a one-time set-up on that device (looks up
+ * the array's device address and sets kernel attributes); make that first
+ * call before any stream capture.  Every call uses the same array, so calls
+ * that overlap on the GPU (on different streams, or from different threads)
+ * race on the scratch; serialise them.  The array keeps the previous call's
+ * intermediates; each call overwrites everything it reads.
+ */
+bloch_status bloch_apply_K_noalloc(bloch_plan* plan, int32_t nb, const double* k, const void* u, void* Ku);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* bloch_last_error(void);
 

@@ -24,7 +24,8 @@ LANCZOS, SUBSPACE = 0, 1
 
 EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", "bloch_apply_K",
             "bloch_apply_M", "bloch_apply_precond", "bloch_pcg", "bloch_solve_bands",
-            "bloch_host_gen_eig", "bloch_last_error", "bloch_plan_device_bytes", "bloch_plan_kernel_launches"]
+            "bloch_host_gen_eig", "bloch_last_error", "bloch_plan_device_bytes", "bloch_plan_kernel_launches",
+            "bloch_apply_K_noalloc"]
 
 
 class BlochError(RuntimeError):
@@ -68,6 +69,7 @@ def lib():
     L.bloch_plan_destroy.restype = None
     L.bloch_apply_K.argtypes = [VP, I32, P(D), I32, VP, VP]
     L.bloch_apply_M.argtypes = [VP, I32, I32, VP, VP]
+    L.bloch_apply_K_noalloc.argtypes = [VP, I32, P(D), VP, VP]
     L.bloch_apply_precond.argtypes = [VP, I32, P(D), I32, VP, VP]
     L.bloch_pcg.argtypes = [VP, I32, P(D), I32, VP, VP, D, I32, I32, P(I32), P(D)]
     L.bloch_solve_bands.argtypes = [VP, I32, P(D), I32, P(D), VP, P(Stats)]
@@ -78,7 +80,7 @@ def lib():
     L.bloch_plan_device_bytes.restype = ctypes.c_size_t
     L.bloch_plan_kernel_launches.argtypes = [VP]
     L.bloch_plan_kernel_launches.restype = ctypes.c_uint64
-    for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
+    for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
               "bloch_solve_bands", "bloch_host_gen_eig"]:
         getattr(L, f).restype = ctypes.c_int
     _LIB = L
@@ -180,6 +182,15 @@ class Plan:
         kv = self._kv(k, nb)
         _check(lib().bloch_apply_K(self.handle, nb, _dptr(kv, ctypes.c_double), prec,
                                    _tensor_ptr(u, prec, nb * 3 * self.V), _tensor_ptr(out, prec, nb * 3 * self.V)))
+        return out
+
+    def apply_K_noalloc(self, k, u, out):
+        """Allocation-free FP32 stiffness apply (fixed library-owned scratch)."""
+        nb = u.numel() // (3 * self.V)
+        kv = self._kv(k, nb)
+        _check(lib().bloch_apply_K_noalloc(self.handle, nb, _dptr(kv, ctypes.c_double),
+                                           _tensor_ptr(u, FP32, nb * 3 * self.V),
+                                           _tensor_ptr(out, FP32, nb * 3 * self.V)))
         return out
 
     def apply_M(self, u, out, precision: int | None = None):
