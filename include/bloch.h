@@ -82,8 +82,10 @@ typedef struct {
                             vectors.  Default 1.                                        */
     int32_t fft_variant; /* 0 = two-stage register FFT passes where the axis length is a
                             power of two in [16, 256], shared-memory Stockham passes
-                            elsewhere; 1 = shared-memory Stockham passes everywhere.
-                            Both compute the same operator.  Default 0.                  */
+                            elsewhere; 1 = shared-memory Stockham passes everywhere;
+                            2 = plain-form baseline: cuFFT 3D transforms with unfused
+                            pointwise kernels.  All compute the same operator.
+                            Default 0.                                                  */
 } bloch_options;
 
 /* Statistics of the last bloch_solve_bands call (all counts summed over k). */
@@ -226,6 +228,69 @@ bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, dou
  * intermediates; each call overwrites everything it reads.
  */
 bloch_status bloch_apply_K_noalloc(bloch_plan* plan, int32_t nb, const double* k, const void* u, void* Ku);
+
+/*
+ * Learned Fourier-space preconditioner.  A small network rescales the branches
+ * of the Green preconditioner per Fourier voxel:
+ *   Z(q) = sum_a g_a v_a v_a^T / mu_a,  (mu_a, v_a) the eigenpairs of
+ *   P(q) = C0 : q q (Eq. matrixP), g_a = softplus(MLP(f_a)) > 0,
+ *   f_a = (qh_x^2, qh_y^2, qh_z^2, mu_a / |q|^2, log(1+|q|)/log(1+N/2)),
+ * with q in units of 2 pi / L and C0 in units of its largest diagonal entry;
+ * MLP 5 -> 16 -> 16 -> 1 with tanh.  Z is symmetric positive definite, so
+ * plain CG stays valid, and a fresh network gives g = 1, i.e. exactly the
+ * paper's preconditioner P^-1 (Eq. precond).  The paper has no learned part.
+ * Training data are per-Fourier-voxel moments of CG residuals r_j and errors
+ * e_j = x* - x_j (each pair scaled by 1/||r_j||); the loss is the mean of
+ * ||Z r_j - e_j||^2.  Parameters, data and optimiser state live on the
+ * device; the collection runs on the plan's stream, training on the default
+ * stream.
+ */
+typedef struct bloch_lp bloch_lp;
+
+/* Number of network parameters (flat order W1 (16x5), b1, W2 (16x16), b2, w3, b3). */
+int32_t bloch_lp_num_params(void);
+
+/* New network with deterministic seeded hidden weights and g = 1. */
+bloch_status bloch_lp_create(bloch_lp** out, uint64_t seed);
+
+/* Release the network and its data (NULL is ignored). */
+void bloch_lp_destroy(bloch_lp* lp);
+
+/* Copy parameters out (get != NULL) and/or in (set != NULL); host, bloch_lp_num_params() values. */
+bloch_status bloch_lp_params(bloch_lp* lp, double* get, const double* set);
+
+/*
+ * Record training data on a plan: for each of n_k wave vectors (host, n_k x 3),
+ * n_rhs seeded right-hand sides (weight 1/(1+|q|^2/16) in scaled units) are
+ * solved to 1e-6 in FP32 with the Green preconditioner, then PCG is rerun from
+ * zero and the moments of iterates 0..n_iters are added to a new data block.
+ */
+bloch_status bloch_lp_collect(bloch_lp* lp, bloch_plan* plan, int32_t n_k, const double* k_list, int32_t n_rhs,
+                              int32_t n_iters, uint64_t seed);
+
+/* Loss (mean over recorded iterates) and its gradient (host, bloch_lp_num_params() values; may be NULL). */
+bloch_status bloch_lp_loss_grad(bloch_lp* lp, double* loss, double* grad);
+
+/* `steps` full-batch Adam steps (beta 0.9/0.999) with learning rate lr; loss_out (host, steps) may be NULL. */
+bloch_status bloch_lp_train(bloch_lp* lp, int32_t steps, double lr, double* loss_out);
+
+/* Number of data blocks recorded so far. */
+int32_t bloch_lp_num_blocks(const bloch_lp* lp);
+
+/*
+ * Copy one data block to the host (any pointer may be NULL): grid {Nx,Ny,Nz};
+ * q = scaled xi + k tables (Nx+Ny+Nz values); mom = V x 13 moments
+ * (A: xx yy zz yz xz xy, B: same order, c); C0V = scaled 6x6 Voigt C0;
+ * samples = recorded iterates.
+ */
+bloch_status bloch_lp_export_block(const bloch_lp* lp, int32_t block, int32_t grid[3], double* q, double* mom,
+                                   double* C0V, int32_t* samples);
+
+/*
+ * Use a trained network in every PCG of this plan (NULL: back to the Green
+ * preconditioner).  The network must outlive its use by the plan.
+ */
+bloch_status bloch_plan_set_preconditioner(bloch_plan* plan, const bloch_lp* lp);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* bloch_last_error(void);

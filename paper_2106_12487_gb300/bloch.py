@@ -25,7 +25,9 @@ LANCZOS, SUBSPACE = 0, 1
 EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", "bloch_apply_K",
             "bloch_apply_M", "bloch_apply_precond", "bloch_pcg", "bloch_solve_bands",
             "bloch_host_gen_eig", "bloch_last_error", "bloch_plan_device_bytes", "bloch_plan_kernel_launches",
-            "bloch_apply_K_noalloc"]
+            "bloch_apply_K_noalloc", "bloch_lp_num_params", "bloch_lp_create", "bloch_lp_destroy", "bloch_lp_params",
+            "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train", "bloch_lp_num_blocks", "bloch_lp_export_block",
+            "bloch_plan_set_preconditioner"]
 
 
 class BlochError(RuntimeError):
@@ -80,6 +82,23 @@ def lib():
     L.bloch_plan_device_bytes.restype = ctypes.c_size_t
     L.bloch_plan_kernel_launches.argtypes = [VP]
     L.bloch_plan_kernel_launches.restype = ctypes.c_uint64
+    U64 = ctypes.c_uint64
+    L.bloch_lp_num_params.argtypes = []
+    L.bloch_lp_num_params.restype = ctypes.c_int32
+    L.bloch_lp_create.argtypes = [P(VP), U64]
+    L.bloch_lp_destroy.argtypes = [VP]
+    L.bloch_lp_destroy.restype = None
+    L.bloch_lp_params.argtypes = [VP, P(D), P(D)]
+    L.bloch_lp_collect.argtypes = [VP, VP, I32, P(D), I32, I32, U64]
+    L.bloch_lp_loss_grad.argtypes = [VP, P(D), P(D)]
+    L.bloch_lp_train.argtypes = [VP, I32, D, P(D)]
+    L.bloch_lp_num_blocks.argtypes = [VP]
+    L.bloch_lp_num_blocks.restype = ctypes.c_int32
+    L.bloch_lp_export_block.argtypes = [VP, I32, P(I32), P(D), P(D), P(D), P(I32)]
+    L.bloch_plan_set_preconditioner.argtypes = [VP, VP]
+    for f in ["bloch_lp_create", "bloch_lp_params", "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train",
+              "bloch_lp_export_block", "bloch_plan_set_preconditioner"]:
+        getattr(L, f).restype = ctypes.c_int
     for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
               "bloch_solve_bands", "bloch_host_gen_eig"]:
         getattr(L, f).restype = ctypes.c_int
@@ -247,3 +266,72 @@ def host_gen_eig(K: np.ndarray, M: np.ndarray):
     _check(lib().bloch_host_gen_eig(n, _dptr(Kc, ctypes.c_double), _dptr(Mc, ctypes.c_double),
                                     _dptr(lam, ctypes.c_double), _dptr(Qv, ctypes.c_double)))
     return lam, Q
+
+
+class LearnedPrecond:
+    """Learned Fourier-space preconditioner (bloch_lp_*): collect, train, use."""
+
+    def __init__(self, seed: int = 7):
+        h = ctypes.c_void_p()
+        _check(lib().bloch_lp_create(ctypes.byref(h), int(seed)))
+        self.handle = h
+        self.n = int(lib().bloch_lp_num_params())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().bloch_lp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, set_to=None):
+        out = np.zeros(self.n)
+        sp = None
+        if set_to is not None:
+            sv = np.ascontiguousarray(np.asarray(set_to, dtype=np.float64))
+            sp = _dptr(sv, ctypes.c_double)
+        _check(lib().bloch_lp_params(self.handle, _dptr(out, ctypes.c_double), sp))
+        return out
+
+    def collect(self, plan: Plan, k_list, n_rhs=4, n_iters=8, seed=11):
+        kl = np.ascontiguousarray(np.asarray(k_list, dtype=np.float64).reshape(-1, 3))
+        _check(lib().bloch_lp_collect(self.handle, plan.handle, kl.shape[0], _dptr(kl, ctypes.c_double),
+                                      int(n_rhs), int(n_iters), int(seed)))
+
+    def loss_grad(self):
+        L = np.zeros(1)
+        g = np.zeros(self.n)
+        _check(lib().bloch_lp_loss_grad(self.handle, _dptr(L, ctypes.c_double), _dptr(g, ctypes.c_double)))
+        return float(L[0]), g
+
+    def train(self, steps, lr=1e-2):
+        hist = np.zeros(max(steps, 1))
+        _check(lib().bloch_lp_train(self.handle, int(steps), float(lr), _dptr(hist, ctypes.c_double)))
+        return hist[:steps]
+
+    @property
+    def num_blocks(self):
+        return int(lib().bloch_lp_num_blocks(self.handle))
+
+    def export_block(self, i):
+        grid = np.zeros(3, dtype=np.int32)
+        _check(lib().bloch_lp_export_block(self.handle, i, _dptr(grid, ctypes.c_int32), None, None, None, None))
+        S = int(grid.sum())
+        V = int(np.prod(grid))
+        q = np.zeros(S)
+        mom = np.zeros(V * 13)
+        C0V = np.zeros(36)
+        ns = np.zeros(1, dtype=np.int32)
+        _check(lib().bloch_lp_export_block(self.handle, i, _dptr(grid, ctypes.c_int32), _dptr(q, ctypes.c_double),
+                                           _dptr(mom, ctypes.c_double), _dptr(C0V, ctypes.c_double),
+                                           _dptr(ns, ctypes.c_int32)))
+        return dict(grid=tuple(int(v) for v in grid), q=q, mom=mom.reshape(V, 13), C0V=C0V.reshape(6, 6),
+                    samples=int(ns[0]))
+
+
+def set_preconditioner(plan: Plan, lp: "LearnedPrecond | None"):
+    _check(lib().bloch_plan_set_preconditioner(plan.handle, lp.handle if lp is not None else None))

@@ -641,8 +641,10 @@ struct Subspace {
             }
             // inverse step on all active slots: delta = A^-1 R
             if ((s = set_k_range(0, nact)) != BLOCH_OK) return s;
+            if ((s = lp_activate<T>(pl, nact, q, q)) != BLOCH_OK) return s;
             long long cg_it = 0;
             s = pcg_run<T>(pl, nact * q, R, Ub, 1.0, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
+            lp_deactivate(pl);
             st->cg_iterations += cg_it;
             st->k_applies += cg_it;
             st->linear_solves += (long long)nact * q;
@@ -996,8 +998,10 @@ struct Lanczos {
             for (int i = 0; i < nact; ++i)
                 for (int a = 0; a < 3; ++a) kv[(size_t)i * 3 + a] = slots[i].k[a];
             if ((s = set_k<T>(pl, nact, kv.data())) != BLOCH_OK) return s;
+            if ((s = lp_activate<T>(pl, nact, 1, 1)) != BLOCH_OK) return s;
             long long cg_it = 0;
             s = pcg_run<T>(pl, nact, Bc, Xc, rho_s, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
+            lp_deactivate(pl);
             st->cg_iterations += cg_it;
             st->k_applies += cg_it;
             st->linear_solves += nact;

@@ -324,6 +324,12 @@ static void fast_x3(bloch_plan* pl, int nb) {
 
 template <typename T>
 void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
+    if (pl->variant == 2) {
+        Workspace<T>& w = ws_of<T>(pl);
+        if (!cufft_launch_K<T>(pl, nb, u, out, out_scale, w.E, w.qtab, ctab_of<T>(pl), geo_of<T>(pl)))
+            pl->pending = set_error(BLOCH_ECUDA, "cuFFT plan or execution failed");
+        return;
+    }
     if (pl->fast) {
         Workspace<T>& w = ws_of<T>(pl);
         const Geo& g = geo_of<T>(pl);
@@ -448,7 +454,7 @@ template <typename T>
 void launch_precond(bloch_plan* pl, int nb, const cplx_t<T>* r, cplx_t<T>* z, T out_scale) {
     dim3 gr(vec_blocks(pl, nb), nb);
     ++pl->launches;
-    k_precond<T><<<gr, 256, 0, pl->stream>>>(r, z, ws_of<T>(pl).qtab, geo_of<T>(pl), pl->pc, out_scale);
+    k_precond<T><<<gr, 256, 0, pl->stream>>>(r, z, ws_of<T>(pl).qtab, geo_of<T>(pl), pl->pc, pl->psel, out_scale);
 }
 
 template <typename T>
@@ -465,7 +471,8 @@ void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, 
 // ------------------------------------------------------------ PCG (Algorithm 2)
 template <typename T>
 bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
-                     int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters) {
+                     int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters,
+                     void (*hook)(void*, int), void* hook_ctx) {
     bloch_status st = ensure_cg<T>(pl, nb);
     if (st != BLOCH_OK) return st;
     Workspace<T>& w = ws_of<T>(pl);
@@ -475,7 +482,7 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     const double tol2 = tol * tol;
     if (use_x0) launch_K<T>(pl, nb, x, w.Ap, T(1));
     ++pl->launches;
-    k_cg_init<T><<<gr, 256, 0, pl->stream>>>(b, use_x0 ? w.Ap : nullptr, x, w.r, w.p, w.qtab, g, pl->pc,
+    k_cg_init<T><<<gr, 256, 0, pl->stream>>>(b, use_x0 ? w.Ap : nullptr, x, w.r, w.p, w.qtab, g, pl->pc, pl->psel,
                                               T(rhs_scale), use_x0 ? 0 : 1, w.part3);
     BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_nactive, 0, sizeof(int), pl->stream));
     ++pl->launches;
@@ -483,6 +490,7 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     BLOCH_CUDA_CHECK_RET(
         cudaMemcpyAsync(pl->h_nactive, pl->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
     BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+    if (hook) hook(hook_ctx, 0);
     int it = 0;
     long long tot = 0;
     while (*pl->h_nactive > 0 && it < max_iter) {
@@ -492,19 +500,25 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
         ++pl->launches;
         k_cg_scalars<<<nb, 32, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 1, tol2, pl->d_nactive);
         ++pl->launches;
-        k_cg_update<T><<<gr, 256, 0, pl->stream>>>(x, w.r, w.p, w.Ap, w.qtab, g, pl->pc, w.sys, w.part3);
+        k_cg_update<T><<<gr, 256, 0, pl->stream>>>(x, w.r, w.p, w.Ap, w.qtab, g, pl->pc, pl->psel, w.sys, w.part3);
         BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_nactive, 0, sizeof(int), pl->stream));
         ++pl->launches;
         k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 2, tol2, pl->d_nactive);
         BLOCH_CUDA_CHECK_RET(
             cudaMemcpyAsync(pl->h_nactive, pl->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
         ++it;
+        if (hook) hook(hook_ctx, it);
         BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
         if (*pl->h_nactive == 0) break;
         ++pl->launches;
-        k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, w.qtab, g, pl->pc, w.sys);
+        k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, w.qtab, g, pl->pc, pl->psel, w.sys);
     }
     BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    if (pl->pending != BLOCH_OK) {
+        const bloch_status p = pl->pending;
+        pl->pending = BLOCH_OK;
+        return p;
+    }
     std::vector<CGSys> hs(nb);
     BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(hs.data(), w.sys, sizeof(CGSys) * nb, cudaMemcpyDeviceToHost, pl->stream));
     BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
@@ -532,7 +546,7 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     template void launch_dot<T>(bloch_plan*, int, const cplx_t<T>*, const cplx_t<T>*, long long,         \
                                 double2*, double2*);                                                     \
     template bloch_status pcg_run<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, double, double, int, \
-                                     bool, int*, double*, long long*);
+                                     bool, int*, double*, long long*, void (*)(void*, int), void*);
 INST(float)
 INST(double)
 #undef INST
@@ -586,6 +600,7 @@ static void free_ws_all(bloch_plan* pl) {
 void bloch_plan_destroy(bloch_plan* pl) {
     if (!pl) return;
     cudaStreamSynchronize(pl->stream);
+    cufft_release(pl);
     free_ws_all(pl);
     cudaFree(pl->d_xi);
     cudaFree(pl->d_ids);
@@ -601,6 +616,7 @@ void bloch_plan_destroy(bloch_plan* pl) {
     }
     cudaFree(pl->d_nactive);
     cudaFreeHost(pl->h_nactive);
+    cudaFree(pl->d_ztab);
     delete pl;
 }
 
@@ -666,6 +682,10 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     pl->G = G;
     if (opt) pl->opt = *opt;
     else bloch_default_options(&pl->opt);
+    if (pl->opt.fft_variant < 0 || pl->opt.fft_variant > 2) {
+        delete pl;
+        return set_error(BLOCH_EINVAL, "fft_variant must be 0, 1 or 2");
+    }
     pl->stream = (cudaStream_t)cuda_stream;
     std::memset(&pl->last_stats, 0, sizeof(pl->last_stats));
     pl->ids_host.assign(grain_ids, grain_ids + V);
@@ -786,6 +806,7 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     set_fast_attrs<float>();
     set_fast_attrs<double>();
     pl->fast = pl->opt.fft_variant == 0;
+    pl->variant = pl->opt.fft_variant;
 #undef CK
     for (Geo* gp : {&pl->geo_f, &pl->geo_d}) {
         gp->Nx = pl->Nx;
@@ -826,6 +847,11 @@ bloch_status bloch_apply_K(bloch_plan* pl, int32_t nb, const double* k, int32_t 
         launch_K<double>(pl, nb, (const double2*)u, (double2*)Ku, pl->Kscale);
     }
     BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    if (pl->pending != BLOCH_OK) {
+        const bloch_status p = pl->pending;
+        pl->pending = BLOCH_OK;
+        return p;
+    }
     return BLOCH_OK;
 }
 
@@ -851,11 +877,14 @@ bloch_status bloch_apply_precond(bloch_plan* pl, int32_t nb, const double* k, in
     if (!k || !r || !z) return set_error(BLOCH_EINVAL, "NULL argument");
     if (precision == BLOCH_FP32) {
         if ((st = set_k<float>(pl, nb, k)) != BLOCH_OK) return st;
+        if ((st = lp_activate<float>(pl, nb, 1, 1)) != BLOCH_OK) return st;
         launch_precond<float>(pl, nb, (const float2*)r, (float2*)z, (float)(1.0 / pl->Kscale));
     } else {
         if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
+        if ((st = lp_activate<double>(pl, nb, 1, 1)) != BLOCH_OK) return st;
         launch_precond<double>(pl, nb, (const double2*)r, (double2*)z, 1.0 / pl->Kscale);
     }
+    lp_deactivate(pl);
     BLOCH_CUDA_CHECK_RET(cudaGetLastError());
     return BLOCH_OK;
 }
@@ -868,12 +897,17 @@ bloch_status bloch_pcg(bloch_plan* pl, int32_t nb, const double* k, int32_t prec
     if (!(tol > 0.0) || max_iter < 0) return set_error(BLOCH_EINVAL, "tol must be > 0 and max_iter >= 0");
     if (precision == BLOCH_FP32) {
         if ((st = set_k<float>(pl, nb, k)) != BLOCH_OK) return st;
-        return pcg_run<float>(pl, nb, (const float2*)b, (float2*)x, 1.0 / pl->Kscale, tol, max_iter, use_x0 != 0,
-                              iters, rel_res, nullptr);
+        if ((st = lp_activate<float>(pl, nb, 1, 1)) != BLOCH_OK) return st;
+        st = pcg_run<float>(pl, nb, (const float2*)b, (float2*)x, 1.0 / pl->Kscale, tol, max_iter, use_x0 != 0, iters,
+                            rel_res, nullptr);
+    } else {
+        if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
+        if ((st = lp_activate<double>(pl, nb, 1, 1)) != BLOCH_OK) return st;
+        st = pcg_run<double>(pl, nb, (const double2*)b, (double2*)x, 1.0 / pl->Kscale, tol, max_iter, use_x0 != 0,
+                             iters, rel_res, nullptr);
     }
-    if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
-    return pcg_run<double>(pl, nb, (const double2*)b, (double2*)x, 1.0 / pl->Kscale, tol, max_iter, use_x0 != 0,
-                           iters, rel_res, nullptr);
+    lp_deactivate(pl);
+    return st;
 }
 
 bloch_status bloch_solve_bands(bloch_plan* pl, int32_t n_k, const double* k_list, int32_t n_bands,

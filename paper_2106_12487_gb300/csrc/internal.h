@@ -83,6 +83,14 @@ struct bloch_plan {
     bloch::TileCfg tile_f, tile_d;
     int nblk_max;
     bool fast = true;              // use the two-stage register FFT passes where the axis allows
+    int variant = 0;               // options.fft_variant
+    bloch_status pending = BLOCH_OK;   // failure inside a launcher, reported by the entry point
+    // learned preconditioner (bloch_plan_set_preconditioner): parameters and
+    // the per-wave-vector Z tables the CG kernels read while it is active
+    const struct bloch_lp* lp = nullptr;
+    bloch::PrecondSel psel{nullptr, 1};
+    float* d_ztab = nullptr;
+    size_t zcap = 0;
 
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;
@@ -111,13 +119,27 @@ template <typename T> void launch_precond(bloch_plan* pl, int nb, const cplx_t<T
 // Batched PCG on the scaled operator: A~ x = rhs_scale * b.
 template <typename T>
 bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
-                     int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters);
+                     int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters,
+                     void (*hook)(void*, int) = nullptr, void* hook_ctx = nullptr);
 // dots[b] = sum conj(a_b) c_b over n_per elements per system (device result).
 template <typename T>
 void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, long long n_per, double2* out,
                 double2* partial);
 
 int vec_blocks(const bloch_plan* pl, int nb);
+
+// plain-form baseline (bloch_cufft.cu): Eq. (hatA) with cuFFT 3D transforms
+template <typename T>
+bool cufft_launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale, cplx_t<T>* E,
+                    const T* qtab, const T* Ctab, const Geo& g);
+void cufft_release(const bloch_plan* pl);
+
+// learned preconditioner (learned.cu): build the Z tables of ntab system
+// groups (group t uses the q table of system t * qstride_sys, T-typed q
+// tables) and make the CG kernels use them; no-op when no network is set.
+template <typename T>
+bloch_status lp_activate(bloch_plan* pl, int ntab, int qstride_sys, int zgroup);
+void lp_deactivate(bloch_plan* pl);
 
 }  // namespace bloch
 

@@ -90,9 +90,32 @@ __device__ __forceinline__ void green_apply(const PrecondCoef& pc, T qx, T qy, T
     z[2] = cscale(cadd(cadd(cscale(r[0], Ee), cscale(r[1], D)), cscale(r[2], Cc)), id);
 }
 
+// Preconditioner selection: the Green operator P^-1 computed per voxel, or a
+// precomputed symmetric 3x3 table per voxel (the learned preconditioner), one
+// table per group of `zgroup` consecutive systems.
+struct PrecondSel {
+    const float* ztab;   // nullptr: Green operator
+    int zgroup;
+};
+
+template <typename T>
+__device__ __forceinline__ void zsym_apply(const float* __restrict__ Z, const cplx_t<T> r[3], cplx_t<T> z[3]) {
+    const T a = T(Z[0]), b = T(Z[1]), c = T(Z[2]), d = T(Z[3]), e = T(Z[4]), f = T(Z[5]);
+    z[0] = cadd(cadd(cscale(r[0], a), cscale(r[1], f)), cscale(r[2], e));
+    z[1] = cadd(cadd(cscale(r[0], f), cscale(r[1], b)), cscale(r[2], d));
+    z[2] = cadd(cadd(cscale(r[0], e), cscale(r[1], d)), cscale(r[2], c));
+}
+
+template <typename T>
+__device__ __forceinline__ void pre_apply(const PrecondSel& ps, const PrecondCoef& pc, int sys, unsigned v,
+                                          long long V, T qx, T qy, T qz, const cplx_t<T> r[3], cplx_t<T> z[3]) {
+    if (ps.ztab) zsym_apply<T>(ps.ztab + ((size_t)(sys / ps.zgroup) * V + v) * 6, r, z);
+    else green_apply(pc, qx, qy, qz, r, z);
+}
+
 template <typename T>
 __global__ void k_precond(const cplx_t<T>* r, cplx_t<T>* z, const T* __restrict__ qtab, Geo g, PrecondCoef pc,
-                          T out_scale) {
+                          PrecondSel ps, T out_scale) {
     using C = cplx_t<T>;
     const int b = blockIdx.y;
     const T* qb = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
@@ -103,7 +126,7 @@ __global__ void k_precond(const cplx_t<T>* r, cplx_t<T>* z, const T* __restrict_
         voxel_q(qb, g, v, ax, ay, az);
         C rv[3] = {rb[v], rb[g.V + v], rb[2 * g.V + v]};
         C zv[3];
-        green_apply(pc, ax, ay, az, rv, zv);
+        pre_apply<T>(ps, pc, b, v, g.V, ax, ay, az, rv, zv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) zb[c * g.V + v] = cscale(zv[c], out_scale);
     }
@@ -174,7 +197,8 @@ static __global__ void k_dot_final(const double2* partial, int nblk, double2* ou
 // partials (r,z), (r,r), (s b, s b).
 template <typename T>
 __global__ void k_cg_init(const cplx_t<T>* bvec, const cplx_t<T>* Ax, cplx_t<T>* x, cplx_t<T>* r, cplx_t<T>* p,
-                          const T* __restrict__ qtab, Geo g, PrecondCoef pc, T s, int zero_x, double* partial) {
+                          const T* __restrict__ qtab, Geo g, PrecondCoef pc, PrecondSel ps, T s, int zero_x,
+                          double* partial) {
     using C = cplx_t<T>;
     const int b = blockIdx.y;
     const size_t off = (size_t)b * 3 * g.V;
@@ -193,7 +217,7 @@ __global__ void k_cg_init(const cplx_t<T>* bvec, const cplx_t<T>* Ax, cplx_t<T>*
         }
         T ax, ay, az;
         voxel_q(qb, g, v, ax, ay, az);
-        green_apply(pc, ax, ay, az, rv, zv);
+        pre_apply<T>(ps, pc, b, v, g.V, ax, ay, az, rv, zv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             p[off + c * g.V + v] = zv[c];
@@ -213,7 +237,8 @@ __global__ void k_cg_init(const cplx_t<T>* bvec, const cplx_t<T>* Ax, cplx_t<T>*
 // x += alpha p; r -= alpha Ap; partials (r, P^-1 r), (r, r)
 template <typename T>
 __global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, const cplx_t<T>* Ap,
-                            const T* __restrict__ qtab, Geo g, PrecondCoef pc, const CGSys* sys, double* partial) {
+                            const T* __restrict__ qtab, Geo g, PrecondCoef pc, PrecondSel ps, const CGSys* sys,
+                            double* partial) {
     using C = cplx_t<T>;
     const int b = blockIdx.y;
     const size_t off = (size_t)b * 3 * g.V;
@@ -237,7 +262,7 @@ __global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, cons
             }
             T ax, ay, az;
             voxel_q(qb, g, v, ax, ay, az);
-            green_apply(pc, ax, ay, az, rv, zv);
+            pre_apply<T>(ps, pc, b, v, g.V, ax, ay, az, rv, zv);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 acc[0] += rv[c].x * zv[c].x + rv[c].y * zv[c].y;
@@ -257,7 +282,7 @@ __global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, cons
 // p = P^-1 r + beta p for active systems
 template <typename T>
 __global__ void k_cg_pupdate(const cplx_t<T>* r, cplx_t<T>* p, const T* __restrict__ qtab, Geo g, PrecondCoef pc,
-                             const CGSys* sys) {
+                             PrecondSel ps, const CGSys* sys) {
     using C = cplx_t<T>;
     const int b = blockIdx.y;
     if (!sys[b].active) return;
@@ -270,7 +295,7 @@ __global__ void k_cg_pupdate(const cplx_t<T>* r, cplx_t<T>* p, const T* __restri
         for (int c = 0; c < 3; ++c) rv[c] = r[off + c * g.V + v];
         T ax, ay, az;
         voxel_q(qb, g, v, ax, ay, az);
-        green_apply(pc, ax, ay, az, rv, zv);
+        pre_apply<T>(ps, pc, b, v, g.V, ax, ay, az, rv, zv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t i = off + c * g.V + v;

@@ -45,10 +45,10 @@ GRIDS = [(4, 4, 4), (6, 6, 6), (6, 4, 5), (16, 16, 16), (32, 32, 32), (24, 20, 1
 
 @pytest.mark.parametrize("grid", GRIDS)
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_apply_K_matches_oracle(B, grid, prec, variant):
-    """Both kernel variants (two-stage register FFT passes, shared-memory
-    Stockham passes) against the oracle."""
+    """The kernel variants (two-stage register FFT passes, shared-memory
+    Stockham passes, cuFFT plain-form baseline) against the oracle."""
     p = synth.small_polycrystal(grid, 5, 3)
     med = O.Medium.from_problem(p)
     plan = B.Plan.from_problem(p, precision=prec, fft_variant=variant)
