@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rve128_g200")
-    ap.add_argument("--form", default="chosen", choices=["chosen", "plain"])
+    ap.add_argument("--form", default="chosen", choices=["chosen", "chosen-subspace", "plain"])
     ap.add_argument("--k-per-step", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -245,8 +245,13 @@ def run_ours(args, ws, rank, local):
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
     p = synth.workload(args.workload)
-    prec = bloch.FP32 if args.form == "chosen" else bloch.FP64
+    prec = bloch.FP64 if args.form == "plain" else bloch.FP32
     if args.form == "chosen":
+        # FP32 fields and PCG: FP32 shift-invert Lanczos, then Algorithm 1 refinement
+        # sweeps with the FP64 residual check
+        opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-5, tol_eig=1e-6, max_cg=500,
+                   max_outer=args.max_outer, fft_variant=args.fft_variant)
+    elif args.form == "chosen-subspace":
         # FP32 fields and PCG, subspace iteration with warm starts, FP64 residual check
         opt = dict(precision=prec, method=bloch.SUBSPACE, tol_lin=1e-3, tol_eig=1e-6, max_cg=500,
                    max_outer=args.max_outer, fft_variant=args.fft_variant)

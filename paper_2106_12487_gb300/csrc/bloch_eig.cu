@@ -305,6 +305,8 @@ struct Subspace {
     size_t next_k = 0;
     std::vector<int> order;   // k indices needing an iterative solve
     bool warm = false;        // warm start along segments of the k list
+    // optional start blocks (q vectors per k = order[i] at init_blocks + i*q*n3)
+    const C* init_blocks = nullptr;
     // segments: slot s walks order[seg_next[s] .. seg_end[s]) when warm starting
     std::vector<size_t> seg_next, seg_end;
 
@@ -363,6 +365,13 @@ struct Subspace {
         sl.gamma = sl.k[0] == 0.0 && sl.k[1] == 0.0 && sl.k[2] == 0.0;
         sl.n_eff = sl.gamma ? n_bands - 3 : n_bands;
         sl.phase = 0;
+        if (init_blocks) {
+            size_t pos = 0;
+            while (pos < order.size() && order[pos] != kidx) ++pos;
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(U, s), init_blocks + pos * (size_t)q * n3,
+                                                 sizeof(C) * q * n3, cudaMemcpyDeviceToDevice, pl->stream));
+            return BLOCH_OK;
+        }
         std::vector<StartEntry> se = start_vectors(pl, sl.k, q, sl.gamma);
         BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(vec(U, s), 0, sizeof(C) * q * n3, pl->stream));
         std::vector<long long> idx(se.size());
@@ -708,7 +717,8 @@ struct Subspace {
 
 template <typename T>
 static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<double, 3>>& ks, int n_bands,
-                                 double* omega_out, void* vecs_out, bloch_stats* st, bool fp64res) {
+                                 double* omega_out, void* vecs_out, bloch_stats* st, bool fp64res,
+                                 const cplx_t<T>* init_blocks = nullptr) {
     Subspace<T> S;
     S.pl = pl;
     S.n3 = 3 * pl->V;
@@ -731,7 +741,8 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     S.omega_out = omega_out;
     S.vecs_out = vecs_out;
     S.st = st;
-    S.warm = pl->opt.warm_start != 0;
+    S.warm = pl->opt.warm_start != 0 && init_blocks == nullptr;
+    S.init_blocks = init_blocks;
     for (size_t i = 0; i < ks.size(); ++i) {
         const bool gamma = ks[i][0] == 0.0 && ks[i][1] == 0.0 && ks[i][2] == 0.0;
         if (gamma && !pl->uniform_rho)
@@ -788,6 +799,10 @@ struct Lanczos {
     bool any_unconverged = false;
     std::vector<int> order;
     size_t next_k = 0;
+    // optional hand-off to the refinement: the q_out leading Ritz vectors of
+    // k = order[i] go to ritz_out + i * q_out * n3 (M-orthonormal)
+    C* ritz_out = nullptr;
+    int q_out = 0;
 
     C *Vb = nullptr, *Tmp = nullptr, *Bc = nullptr, *Xc = nullptr;
     double2 *d_part = nullptr, *d_h = nullptr, *d_Q = nullptr;
@@ -900,7 +915,8 @@ struct Lanczos {
         }
         sl.restarts += 1;
         const bool done = conv || sl.restarts > max_outer;
-        const int kk = done ? sl.n_eff : std::min(m - 1, sl.n_eff + (m - sl.n_eff) / 2);
+        const int kk = done ? (ritz_out ? std::min(m, q_out) : sl.n_eff)
+                            : std::min(m - 1, sl.n_eff + (m - sl.n_eff) / 2);
         // Q: m x m, columns = the kept Ritz vectors (descending theta), rest zero
         std::vector<double2> Qh((size_t)m * m, make_double2(0, 0));
         for (int c = 0; c < kk; ++c)
@@ -936,6 +952,14 @@ struct Lanczos {
             }
             st->max_rel_residual = std::max(st->max_rel_residual, mx);
             if (!conv) any_unconverged = true;
+            if (ritz_out) {
+                size_t pos = 0;
+                while (pos < order.size() && order[pos] != sl.kidx) ++pos;
+                C* dst = ritz_out + pos * (size_t)q_out * n3;
+                cudaMemcpyAsync(dst, Tmp, sizeof(C) * (size_t)kk * n3, cudaMemcpyDeviceToDevice, pl->stream);
+                if (kk < q_out)
+                    cudaMemsetAsync(dst + (size_t)kk * n3, 0, sizeof(C) * (size_t)(q_out - kk) * n3, pl->stream);
+            }
             if (vecs_out) {
                 C* out = (C*)vecs_out + (size_t)sl.kidx * n_bands * n3;
                 const double nv = 1.0 / std::sqrt(pl->rho_ref);
@@ -1087,7 +1111,8 @@ struct Lanczos {
 
 template <typename T>
 static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<double, 3>>& ks, int n_bands,
-                                double* omega_out, void* vecs_out, bloch_stats* st) {
+                                double* omega_out, void* vecs_out, bloch_stats* st, cplx_t<T>* ritz_out = nullptr,
+                                int q_out = 0, double tol_override = 0.0) {
     if (!pl->uniform_rho)
         return set_error(BLOCH_EUNSUPPORTED, "the Lanczos solver needs a uniform density (use subspace iteration)");
     Lanczos<T> S;
@@ -1099,9 +1124,12 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     if (S.m > 63) return set_error(BLOCH_EUNSUPPORTED, "Lanczos basis above 63 vectors is not supported");
     if (S.m < n_bands + 1) return set_error(BLOCH_EINVAL, "Lanczos basis too small for the requested bands");
     S.rho_s = pl->rho_uniform_scaled;
-    S.tol_eig = pl->opt.tol_eig;
+    S.tol_eig = tol_override > 0 ? tol_override : pl->opt.tol_eig;
     S.tol_lin = pl->opt.tol_lin;
     if (std::is_same<T, float>::value) S.tol_lin = std::max(S.tol_lin, 3e-6);
+    S.ritz_out = ritz_out;
+    S.q_out = q_out;
+    if (q_out > S.m) S.m = std::min<int>(q_out + 4, 63);
     S.max_outer = pl->opt.max_outer;
     S.max_cg = pl->opt.max_cg;
     S.klist = &ks;
@@ -1132,6 +1160,46 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     return BLOCH_OK;
 }
 
+// FP32 chosen form with method = Lanczos: FP32 shift-invert Lanczos (inner PCG
+// at the FP32 tolerance) delivers the q leading Ritz vectors of every wave
+// vector; Algorithm 1 sweeps then refine that block to the requested
+// tolerance, with the FP64 residual check of the FP32 form.  Wave vectors go
+// through in chunks so the hand-off buffer stays bounded.
+static bloch_status run_hybrid(bloch_plan* pl, const std::vector<std::array<double, 3>>& ks, int n_bands,
+                               double* omega_out, void* vecs_out, bloch_stats* st) {
+    using C = float2;
+    const int q = pl->opt.block > 0 ? pl->opt.block : std::min(2 * n_bands, n_bands + 8);
+    const long long n3 = 3 * pl->V;
+    const int chunk = std::max(1, std::min<int>((int)ks.size(), pl->opt.k_batch > 0 ? pl->opt.k_batch : 8));
+    C* buf = nullptr;
+    cudaError_t e = cudaMalloc((void**)&buf, sizeof(C) * (size_t)chunk * q * n3);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (Lanczos hand-off)");
+    std::vector<double> om_tmp;
+    bloch_status s = BLOCH_OK;
+    bool unconverged = false;
+    const double tol_l = std::max(1e-5, 10.0 * pl->opt.tol_eig);
+    for (size_t c0 = 0; c0 < ks.size() && s == BLOCH_OK; c0 += chunk) {
+        std::vector<std::array<double, 3>> sub(ks.begin() + c0, ks.begin() + std::min(ks.size(), c0 + chunk));
+        om_tmp.assign(sub.size() * n_bands, 0.0);
+        s = run_lanczos<float>(pl, sub, n_bands, om_tmp.data(), nullptr, st, buf, q, tol_l);
+        if (s == BLOCH_ENOTCONV_EIG) s = BLOCH_OK;   // the refinement decides convergence
+        if (s != BLOCH_OK) break;
+        const long long lanczos_outer = st->outer_iterations;
+        void* vsub = vecs_out ? (void*)((C*)vecs_out + c0 * (size_t)n_bands * n3) : nullptr;
+        s = run_subspace<float>(pl, sub, n_bands, omega_out + c0 * n_bands, vsub, st, true, buf);
+        if (s == BLOCH_ENOTCONV_EIG) {
+            unconverged = true;
+            s = BLOCH_OK;
+        }
+        (void)lanczos_outer;
+    }
+    cudaStreamSynchronize(pl->stream);
+    cudaFree(buf);
+    if (s != BLOCH_OK) return s;
+    if (unconverged) return set_error(BLOCH_ENOTCONV_EIG, "refinement reached its sweep cap");
+    return BLOCH_OK;
+}
+
 }  // namespace bloch
 
 using namespace bloch;
@@ -1155,7 +1223,7 @@ bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_lis
             s = run_subspace<double>(pl, ks, n_bands, omega_out, vecs_out, &st, false);
     } else {
         if (pl->opt.precision == BLOCH_FP32)
-            s = run_lanczos<float>(pl, ks, n_bands, omega_out, vecs_out, &st);
+            s = run_hybrid(pl, ks, n_bands, omega_out, vecs_out, &st);
         else
             s = run_lanczos<double>(pl, ks, n_bands, omega_out, vecs_out, &st);
     }

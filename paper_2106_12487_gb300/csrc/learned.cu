@@ -89,7 +89,10 @@ __global__ void k_lp_moments(const float2* __restrict__ r, const float2* __restr
 #pragma unroll
         for (int i = 0; i < kMom; ++i) acc[i] = 0.f;
         for (int s = 0; s < nsys; ++s) {
-            const float sc = sys[s].rr > 0 ? (float)(1.0 / sys[s].rr) : 0.f;   // 1/||r||^2
+            // pairs are recorded while ||r_j|| > 1e-4 ||b||: below that the error
+            // e_j is dominated by the 1e-6 accuracy of x* itself
+            if (!(sys[s].rr > 1e-8 * sys[s].bb)) continue;
+            const float sc = (float)(1.0 / sys[s].rr);   // 1/||r||^2
             float2 rv[3], ev[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {

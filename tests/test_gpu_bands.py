@@ -76,6 +76,28 @@ def test_lanczos_matches_oracle(B, batch):
     assert stats["outer_iterations"] >= 4
 
 
+@pytest.mark.parametrize("chunk", [1, 8])
+def test_fp32_lanczos_hybrid_matches_oracle(B, chunk):
+    """FP32 chosen form with method = Lanczos: FP32 shift-invert Lanczos hands
+    its Ritz block to Algorithm 1 sweeps with the FP64 residual check."""
+    p = synth.small_polycrystal((8, 8, 8), 6, 5, n_bands=6)
+    med = O.Medium.from_problem(p)
+    ks = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [1.0, 1.0, 0.0], [0.3, 0.6, 0.9]]) * math.pi / 1e-3
+    want = O.solve_bands(med, ks, 6, 1e-12, 1e-12, method="lanczos").omega
+    plan = B.Plan.from_problem(p, precision=1, method=0, tol_lin=1e-5, tol_eig=1e-6, k_batch=chunk)
+    got, stats, _ = plan.solve_bands(ks, 6)
+    assert freq_err(got, want) < 1e-6
+    assert stats["max_rel_residual"] < 1e-5
+
+
+def test_fp32_lanczos_hybrid_rve16(B):
+    g = json.load(open(os.path.join(GOLDEN, "rve16_g8_bands.json")))
+    p = synth.workload("rve16_g8")
+    plan = B.Plan.from_problem(p, precision=1, method=0, tol_lin=1e-5, tol_eig=1e-6)
+    got, stats, _ = plan.solve_bands(p.k_list, p.n_bands)
+    assert freq_err(got, np.asarray(g["omega"])) < 1e-6
+
+
 def test_lanczos_rve16_workload(B):
     g = json.load(open(os.path.join(GOLDEN, "rve16_g8_bands.json")))
     p = synth.workload("rve16_g8")

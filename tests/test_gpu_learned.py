@@ -128,6 +128,8 @@ def test_training_lowers_loss_and_reports_cg_gain(B, capsys):
     L0, _ = lp.loss_grad()
     hist = lp.train(300, lr=3e-3)
     L1, _ = lp.loss_grad()
+    with capsys.disabled():
+        print(f"\nloss history: {hist[0]:.5e} {hist[50]:.5e} {hist[150]:.5e} {hist[-1]:.5e}")
     assert L1 < L0 and hist[-1] <= hist[0]
     # held-out cell
     p = synth.small_polycrystal((24, 24, 24), 15, 77)
