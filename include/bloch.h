@@ -80,6 +80,12 @@ typedef struct {
                             each k starts from the converged block of the previous k
                             (Section 3.3); 0 = every k starts from the plane-wave start
                             vectors.  Default 1.                                        */
+    int32_t cuda_graph;  /* 1 = each PCG loop runs as one CUDA graph launch: a conditional
+                            WHILE node whose body is one iteration and whose condition is
+                            set on the device (systems still active, iteration cap not
+                            reached), so no host synchronisation happens per iteration;
+                            0 = host-driven loop with one synchronisation per iteration.
+                            Default 1.                                                  */
     int32_t fft_variant; /* 0 = two-stage register FFT passes where the axis length is a
                             power of two in [16, 256], shared-memory Stockham passes
                             elsewhere; 1 = shared-memory Stockham passes everywhere;

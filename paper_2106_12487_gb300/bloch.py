@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("method", ctypes.c_int32), ("tol_lin", ctypes.c_double),
                 ("tol_eig", ctypes.c_double), ("max_cg", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("k_batch", ctypes.c_int32), ("ncv", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("fft_variant", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("cuda_graph", ctypes.c_int32), ("fft_variant", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

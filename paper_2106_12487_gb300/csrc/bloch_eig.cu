@@ -1184,14 +1184,17 @@ static bloch_status run_hybrid(bloch_plan* pl, const std::vector<std::array<doub
         s = run_lanczos<float>(pl, sub, n_bands, om_tmp.data(), nullptr, st, buf, q, tol_l);
         if (s == BLOCH_ENOTCONV_EIG) s = BLOCH_OK;   // the refinement decides convergence
         if (s != BLOCH_OK) break;
-        const long long lanczos_outer = st->outer_iterations;
         void* vsub = vecs_out ? (void*)((C*)vecs_out + c0 * (size_t)n_bands * n3) : nullptr;
+        // the refinement's inner solves only correct a small residual (reading of
+        // Algorithm 1 in residual-correction form): 1e-3 relative is enough
+        const double tol_lin_saved = pl->opt.tol_lin;
+        pl->opt.tol_lin = std::max(tol_lin_saved, 1e-3);
         s = run_subspace<float>(pl, sub, n_bands, omega_out + c0 * n_bands, vsub, st, true, buf);
+        pl->opt.tol_lin = tol_lin_saved;
         if (s == BLOCH_ENOTCONV_EIG) {
             unconverged = true;
             s = BLOCH_OK;
         }
-        (void)lanczos_outer;
     }
     cudaStreamSynchronize(pl->stream);
     cudaFree(buf);

@@ -41,8 +41,9 @@ static cudaError_t smem_attr(K k) {
 template <int RA, int RB>
 static cudaError_t attrs_n() {
     cudaError_t e;
-    if ((e = smem_attr(k_fpass_axis<float, +1, 1, RA, RB>)) != cudaSuccess) return e;
-    if ((e = smem_attr(k_fpass_axis<float, -1, 1, RA, RB>)) != cudaSuccess) return e;
+    constexpr int PT = (RA * RB * 32 * sizeof(float2) <= 64 * 1024) ? 32 : 16;
+    if ((e = smem_attr(k_fpass_y<float, +1, RA, RB, PT>)) != cudaSuccess) return e;
+    if ((e = smem_attr(k_fpass_y<float, -1, RA, RB, PT>)) != cudaSuccess) return e;
     if constexpr (RB <= 8) {
         if ((e = smem_attr(k_fpass_z_strain<float, RA, RB>)) != cudaSuccess) return e;
         if ((e = smem_attr(k_fpass_z_div<float, RA, RB>)) != cudaSuccess) return e;
@@ -94,15 +95,14 @@ static bool fast_len(int N) { return N == 16 || N == 32 || N == 64 || N == 128; 
 template <int RA, int RB>
 static void y_pass(bloch_plan* pl, int DIR, int nb, float2* E) {
     constexpr int N = RA * RB;
+    constexpr int PT = (N * 32 * sizeof(float2) <= 64 * 1024) ? 32 : 16;
     const long long npen = (long long)pl->Nx * pl->Nz;
-    int P = 32;
-    while (P > 1 && (long long)(P / 2) >= npen) P >>= 1;
-    const size_t smem = (size_t)(N + N * P) * sizeof(float2);
-    dim3 gr((unsigned)((npen + P - 1) / P), nb * 6);
+    const size_t smem = (size_t)(N + N * PT) * sizeof(float2);
+    dim3 gr((unsigned)((npen + PT - 1) / PT), nb * 6);
     if (DIR > 0)
-        k_fpass_axis<float, +1, 1, RA, RB><<<gr, 256, smem, pl->stream>>>(E, E, pl->d_twf[1], pl->geo_f, P, 1.0f);
+        k_fpass_y<float, +1, RA, RB, PT><<<gr, 256, smem, pl->stream>>>(E, E, pl->d_twf[1], pl->geo_f);
     else
-        k_fpass_axis<float, -1, 1, RA, RB><<<gr, 256, smem, pl->stream>>>(E, E, pl->d_twf[1], pl->geo_f, P, 1.0f);
+        k_fpass_y<float, -1, RA, RB, PT><<<gr, 256, smem, pl->stream>>>(E, E, pl->d_twf[1], pl->geo_f);
 }
 
 template <int RA, int RB>

@@ -223,8 +223,9 @@ static void fast_attr(K k) {
 
 template <typename T, int RA, int RB, bool Z>
 static void set_fast_attrs_n() {
-    fast_attr(k_fpass_axis<T, +1, 1, RA, RB>);
-    fast_attr(k_fpass_axis<T, -1, 1, RA, RB>);
+    constexpr int PT = (RA * RB * 32 * sizeof(cplx_t<T>) <= 64 * 1024) ? 32 : 16;
+    fast_attr(k_fpass_y<T, +1, RA, RB, PT>);
+    fast_attr(k_fpass_y<T, -1, RA, RB, PT>);
     if constexpr (Z) {
         fast_attr(k_fpass_z_strain<T, RA, RB>);
         fast_attr(k_fpass_z_div<T, RA, RB>);
@@ -254,16 +255,15 @@ template <typename T, int RA, int RB>
 static void fast_y(bloch_plan* pl, int DIR, int nb, cplx_t<T>* E) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
+    constexpr int PT = (N * 32 * sizeof(cplx_t<T>) <= 64 * 1024) ? 32 : 16;
     const long long npen = (long long)pl->Nx * pl->Nz;
-    int P = fast_P(npen, 32);
-    while (P > 1 && (size_t)(N + N * P) * sizeof(cplx_t<T>) > 96 * 1024) P >>= 1;
-    const size_t smem = (size_t)(N + N * P) * sizeof(cplx_t<T>);
-    dim3 gr((unsigned)((npen + P - 1) / P), nb * 6);
+    const size_t smem = (size_t)(N + N * PT) * sizeof(cplx_t<T>);
+    dim3 gr((unsigned)((npen + PT - 1) / PT), nb * 6);
     ++pl->launches;
     if (DIR > 0)
-        k_fpass_axis<T, +1, 1, RA, RB><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g, P, T(1));
+        k_fpass_y<T, +1, RA, RB, PT><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g);
     else
-        k_fpass_axis<T, -1, 1, RA, RB><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g, P, T(1));
+        k_fpass_y<T, -1, RA, RB, PT><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g);
 }
 
 template <typename T, int RA, int RB>
@@ -469,6 +469,106 @@ void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, 
 }
 
 // ------------------------------------------------------------ PCG (Algorithm 2)
+// Loop condition of the graph-resident PCG: continue while a system is active
+// and the iteration cap is not reached (the cap bounds every launch).
+static __global__ void k_cg_cond(cudaGraphConditionalHandle h, const int* __restrict__ n_active, int* iter,
+                                 int max_iter) {
+    const int i = ++(*iter);
+    cudaGraphSetConditional(h, (*n_active > 0 && i < max_iter) ? 1u : 0u);
+}
+
+// One PCG iteration (operator, (p, Ap), alpha, updates, beta, p-update, loop
+// condition) enqueued on the plan's stream; captured into the WHILE body.
+template <typename T>
+static void pcg_iteration(bloch_plan* pl, int nb, cplx_t<T>* x, double tol2, int nblk,
+                          cudaGraphConditionalHandle* h, int max_iter) {
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    dim3 gr(nblk, nb);
+    launch_K<T>(pl, nb, w.p, w.Ap, T(1));
+    launch_dot<T>(pl, nb, w.p, w.Ap, 3 * pl->V, w.dots, w.part2);
+    ++pl->launches;
+    k_cg_scalars<<<nb, 32, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 1, tol2, pl->d_nactive);
+    ++pl->launches;
+    k_cg_update<T><<<gr, 256, 0, pl->stream>>>(x, w.r, w.p, w.Ap, w.qtab, g, pl->pc, pl->psel, w.sys, w.part3);
+    // (mode 1 above zeroed the active count that mode 2 accumulates)
+    ++pl->launches;
+    k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 2, tol2, pl->d_nactive);
+    ++pl->launches;
+    k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, w.qtab, g, pl->pc, pl->psel, w.sys);
+    if (h) {
+        ++pl->launches;
+        k_cg_cond<<<1, 1, 0, pl->stream>>>(*h, pl->d_nactive, pl->d_iter, max_iter);
+    }
+}
+
+template <typename T>
+static bloch_status pcg_graph(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double tol2, int nblk,
+                              int max_iter, cudaGraphExec_t* out) {
+    Workspace<T>& w = ws_of<T>(pl);
+    const int prec = std::is_same<T, float>::value ? 1 : 0;
+    for (auto& e : pl->pcg_graphs)
+        if (e.prec == prec && e.nb == nb && e.max_iter == max_iter && e.b == b && e.x == x && e.E == w.E &&
+            e.r == w.r && e.ztab == pl->psel.ztab && e.zgroup == pl->psel.zgroup) {
+            *out = e.exec;
+            return BLOCH_OK;
+        }
+    if (pl->pcg_graphs.size() >= 16) {
+        cudaGraphExecDestroy(pl->pcg_graphs.front().exec);
+        cudaGraphDestroy(pl->pcg_graphs.front().graph);
+        pl->pcg_graphs.erase(pl->pcg_graphs.begin());
+    }
+    cudaGraph_t graph;
+    BLOCH_CUDA_CHECK_RET(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_cuda_error(e, "cudaGraphConditionalHandleCreate");
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_cuda_error(e, "cudaGraphAddNode (conditional)");
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // capture on the plan's private stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured); capturing runs nothing
+    e = cudaStreamBeginCaptureToGraph(pl->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_cuda_error(e, "cudaStreamBeginCaptureToGraph");
+    }
+    const unsigned long long l0 = pl->launches;
+    cudaStream_t user = pl->stream;
+    pl->stream = pl->cap_stream;
+    pcg_iteration<T>(pl, nb, x, tol2, nblk, &h, max_iter);
+    pl->stream = user;
+    pl->launches = l0;   // counted per executed iteration, not at capture
+    cudaGraph_t captured;
+    e = cudaStreamEndCapture(pl->cap_stream, &captured);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_cuda_error(e, "cudaStreamEndCapture");
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_cuda_error(e, "cudaGraphInstantiate");
+    }
+    bloch_plan::PcgGraph pg{prec, nb, max_iter, b, x, w.E, w.r, pl->psel.ztab, pl->psel.zgroup, graph, exec};
+    pl->pcg_graphs.push_back(pg);
+    *out = exec;
+    return BLOCH_OK;
+}
+
 template <typename T>
 bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
                      int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters,
@@ -493,7 +593,23 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     if (hook) hook(hook_ctx, 0);
     int it = 0;
     long long tot = 0;
-    while (*pl->h_nactive > 0 && it < max_iter) {
+    // graph-resident loop (not with a per-iteration host hook, nor with the
+    // cuFFT baseline, whose plans are created on first use)
+    const bool use_graph = pl->opt.cuda_graph != 0 && hook == nullptr && pl->variant != 2;
+    if (use_graph && *pl->h_nactive > 0 && max_iter > 0) {
+        cudaGraphExec_t exec;
+        bloch_status gs = pcg_graph<T>(pl, nb, b, x, tol2, nblk, max_iter, &exec);
+        if (gs != BLOCH_OK) return gs;
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_iter, 0, sizeof(int), pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaGraphLaunch(exec, pl->stream));
+        int iters_done = 0;
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(&iters_done, pl->d_iter, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        pl->launches += (unsigned long long)iters_done * (pl->fast ? 11 : 11);
+        it = iters_done;
+    }
+    while (!use_graph && *pl->h_nactive > 0 && it < max_iter) {
         tot += *pl->h_nactive;
         launch_K<T>(pl, nb, w.p, w.Ap, T(1));
         launch_dot<T>(pl, nb, w.p, w.Ap, 3 * pl->V, w.dots, w.part2);
@@ -529,6 +645,10 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
         if (iters) iters[i] = hs[i].iters;
         if (relres) relres[i] = rel;
         if (!(rel <= tol)) all = false;
+    }
+    if (use_graph) {
+        tot = 0;
+        for (int i = 0; i < nb; ++i) tot += hs[i].iters;
     }
     if (total_iters) *total_iters += tot;
     if (!finite) return set_error(BLOCH_ENONFINITE, "PCG met a non-finite residual");
@@ -571,6 +691,7 @@ void bloch_default_options(bloch_options* opt) {
     opt->k_batch = 0;
     opt->ncv = 0;
     opt->warm_start = 1;
+    opt->cuda_graph = 1;
     opt->fft_variant = 0;
 }
 
@@ -601,6 +722,12 @@ void bloch_plan_destroy(bloch_plan* pl) {
     if (!pl) return;
     cudaStreamSynchronize(pl->stream);
     cufft_release(pl);
+    for (auto& e : pl->pcg_graphs) {
+        cudaGraphExecDestroy(e.exec);
+        cudaGraphDestroy(e.graph);
+    }
+    cudaFree(pl->d_iter);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     free_ws_all(pl);
     cudaFree(pl->d_xi);
     cudaFree(pl->d_ids);
@@ -800,6 +927,8 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         CK(cudaMemcpy(pl->d_twf[a], tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
     }
     CK(dmalloc(&pl->d_nactive, 1, acc));
+    CK(dmalloc(&pl->d_iter, 1, acc));
+    CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
     CK(cudaMallocHost((void**)&pl->h_nactive, sizeof(int)));
     CK(set_smem_attrs<float>());
     CK(set_smem_attrs<double>());

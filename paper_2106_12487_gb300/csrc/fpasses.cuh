@@ -31,52 +31,62 @@ __device__ __forceinline__ C twmul(C v, C w, int dir) {
     return cmul(v, w);
 }
 
-// --------------------------------------------------- y / z pass (in place ok)
-// blockIdx.y = batch*ncomp + comp (offset blockIdx.y * V)
-template <typename T, int DIR, int AXIS, int RA, int RB>
-__global__ void __launch_bounds__(256) k_fpass_axis(const cplx_t<T>* in, cplx_t<T>* out,
-                                                    const cplx_t<T>* __restrict__ twa, Geo g, int P,
-                                                    T out_scale) {
+// --------------------------------------------------- y pass (in place ok)
+// blockIdx.y = batch*ncomp + comp (offset blockIdx.y * V).  PT pencils (PT
+// consecutive x of the (x, z) plane) per CTA; one 32-bit division per task
+// locates the pencil, elements step by Nx along it.
+template <typename T, int DIR, int RA, int RB, int PT>
+__global__ void __launch_bounds__(256) k_fpass_y(const cplx_t<T>* in, cplx_t<T>* out,
+                                                 const cplx_t<T>* __restrict__ twa, Geo g) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
+    constexpr int NT = 256;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const long long npen = AXIS == 1 ? (long long)g.Nx * g.Nz : (long long)g.Nx * g.Ny;
-    const long long pi0 = (long long)blockIdx.x * P;
-    const int np = (int)min((long long)P, npen - pi0);
+    const int tid = threadIdx.x;
+    const unsigned nx = (unsigned)g.Nx;
+    const unsigned npen = nx * (unsigned)g.Nz;
+    const unsigned pi0 = blockIdx.x * PT;
+    const unsigned plane = nx * (unsigned)g.Ny;
     const size_t off = (size_t)blockIdx.y * g.V;
     const C* src = in + off;
     C* dst = out + off;
-    const long long plane = (long long)g.Nx * g.Ny;
-    auto addr = [&](int p, int n) -> size_t {
-        const long long pi = pi0 + p;
-        if (AXIS == 1) return (size_t)(pi / g.Nx) * plane + (size_t)n * g.Nx + (size_t)(pi % g.Nx);
-        return (size_t)n * plane + pi;
-    };
-    for (int i = tid; i < N; i += nthr) tw[i] = twa[i];
-    for (int t = tid; t < P * RB; t += nthr) {
-        const int p = t % P, j = t / P;
-        C v[RA];
+    for (int i = tid; i < N; i += NT) tw[i] = twa[i];
 #pragma unroll
-        for (int r = 0; r < RA; ++r) v[r] = (p < np) ? src[addr(p, j + r * RB)] : mk(T(0), T(0));
+    for (int t = tid; t < PT * RB; t += NT) {
+        const int p = t % PT, j = t / PT;
+        const unsigned pi = pi0 + p;
+        C v[RA];
+        if (pi < npen) {
+            const unsigned z = pi / nx;
+            const C* a = src + (z * plane + (pi - z * nx) + (unsigned)j * nx);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = a[(unsigned)(r * RB) * nx];
+        } else {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = mk(T(0), T(0));
+        }
         RegDFT<RA, DIR, C>::run(v);
 #pragma unroll
-        for (int r = 0; r < RA; ++r) buf[(j * RA + r) * P + p] = v[r];
+        for (int r = 0; r < RA; ++r) buf[(j * RA + r) * PT + p] = v[r];
     }
     __syncthreads();
-    for (int t = tid; t < P * RA; t += nthr) {
-        const int p = t % P, j = t / P;
+#pragma unroll
+    for (int t = tid; t < PT * RA; t += NT) {
+        const int p = t % PT, j = t / PT;
         C v[RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) v[r] = buf[(j + r * RA) * P + p];
+        for (int r = 0; r < RB; ++r) v[r] = buf[(j + r * RA) * PT + p];
 #pragma unroll
         for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j], DIR);
         RegDFT<RB, DIR, C>::run(v);
-        if (p < np) {
+        const unsigned pi = pi0 + p;
+        if (pi < npen) {
+            const unsigned z = pi / nx;
+            C* a = dst + (z * plane + (pi - z * nx) + (unsigned)j * nx);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) dst[addr(p, j + r * RA)] = cscale(v[r], out_scale);
+            for (int r = 0; r < RB; ++r) a[(unsigned)(r * RA) * nx] = v[r];
         }
     }
 }

@@ -91,6 +91,17 @@ struct bloch_plan {
     bloch::PrecondSel psel{nullptr, 1};
     float* d_ztab = nullptr;
     size_t zcap = 0;
+    // instantiated PCG-loop graphs (conditional WHILE node), keyed by their bound pointers
+    struct PcgGraph {
+        int prec, nb, max_iter;
+        const void *b, *x, *E, *r, *ztab;
+        int zgroup;
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+    };
+    std::vector<PcgGraph> pcg_graphs;
+    int* d_iter = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
 
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;

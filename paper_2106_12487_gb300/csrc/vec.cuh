@@ -332,6 +332,7 @@ static __global__ void k_cg_scalars(const double* partial3, const double2* dots,
         s.active = (s.rr > tol2 * s.bb) ? 1 : 0;
         if (s.active) atomicAdd(n_active, 1);
     } else if (mode == 1) {
+        if (b == 0) *n_active = 0;   // recount in mode 2 (kernels of one stream are ordered)
         s.pAp = dots[b].x;
         s.alpha = (s.active && s.pAp > 0.0) ? s.rz / s.pAp : 0.0;
     } else {

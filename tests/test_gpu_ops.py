@@ -136,6 +136,28 @@ def test_pcg_fp64_matches_oracle(B, grid):
         assert O.norm(b[i] - A(got[i])) / O.norm(b[i]) < 5e-11
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pcg_graph_loop_equals_host_loop(B, prec):
+    """The graph-resident PCG loop (conditional WHILE node, device-side
+    condition) takes the same iterations and returns the same solutions as
+    the host-driven loop; the iteration cap ends the loop."""
+    grid = (16, 12, 10)
+    p = synth.small_polycrystal(grid, 6, 12)
+    ks = np.array([[0.5, 0.1, 0.0], [1.0, 1.0, 0.0], [0.05, 0.0, 0.02]]) * math.pi / 1e-3
+    b = synth.random_field(grid, 2, batch=3) * 1e20
+    tol = 1e-10 if prec == 0 else 1e-5
+    res = {}
+    for graph in (0, 1):
+        plan = B.Plan.from_problem(p, precision=prec, cuda_graph=graph)
+        x = to_dev(np.zeros_like(b), prec)
+        iters, rel, _ = plan.pcg(ks, to_dev(b, prec), x, tol, 5000)
+        res[graph] = (iters, x.cpu().numpy())
+        capped, _, st = plan.pcg(ks, to_dev(b, prec), x, tol, 3, allow_nonconv=True)
+        assert st == 4 and np.all(capped == 3)
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+
+
 def test_pcg_fp32_reaches_fp32_tolerance(B):
     grid = (16, 16, 16)
     p = synth.small_polycrystal(grid, 6, 13)
