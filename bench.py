@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
     ap.add_argument("--fft-variant", type=int, default=0, choices=[0, 1, 2],
                     help="0: two-stage register FFT passes, 1: shared-memory Stockham passes, 2: cuFFT baseline")
+    ap.add_argument("--cuda-graph", type=int, default=1, choices=[0, 1],
+                    help="1: PCG loop as one CUDA graph with a device-side while node; 0: host-driven loop "
+                         "(same kernels; used for per-launch profiling)")
     return ap.parse_args()
 
 
@@ -250,15 +253,16 @@ def run_ours(args, ws, rank, local):
         # FP32 fields and PCG: FP32 shift-invert Lanczos, then Algorithm 1 refinement
         # sweeps with the FP64 residual check
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-5, tol_eig=1e-5, max_cg=500,
-                   max_outer=args.max_outer, fft_variant=args.fft_variant)
+                   max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph)
     elif args.form == "chosen-subspace":
         # FP32 fields and PCG, subspace iteration with warm starts, FP64 residual check
         opt = dict(precision=prec, method=bloch.SUBSPACE, tol_lin=1e-3, tol_eig=1e-6, max_cg=500,
-                   max_outer=args.max_outer, fft_variant=args.fft_variant)
+                   max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph)
     else:
         # the paper's plain form: FP64, shift-invert Lanczos, cuFFT operator
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-10, tol_eig=1e-10, max_cg=2000,
-                   max_outer=args.max_outer, fft_variant=2 if args.fft_variant == 0 else args.fft_variant)
+                   max_outer=args.max_outer, fft_variant=2 if args.fft_variant == 0 else args.fft_variant,
+                   cuda_graph=args.cuda_graph)
     plan = bloch.Plan.from_problem(p, **opt)
     if args.kapply_only:
         roof = kapply_roofline(plan, p, prec, args.kapply_nb)
@@ -333,7 +337,7 @@ def run_ours(args, ws, rank, local):
                 "config": {"workload": args.workload, "grid": list(p.grid), "grains": int(p.G),
                            "n_bands": p.n_bands, "n_k_path": int(nk), "k_per_step": kps,
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
-                           "fft_variant": opt["fft_variant"], "method": "subspace" if opt["method"] else "lanczos",
+                           "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"], "method": "subspace" if opt["method"] else "lanczos",
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,

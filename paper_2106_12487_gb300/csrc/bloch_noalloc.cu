@@ -108,32 +108,32 @@ static void y_pass(bloch_plan* pl, int DIR, int nb, float2* E) {
 template <int RA, int RB>
 static void z_strain(bloch_plan* pl, int nb, const float2* u, float2* E, const float* qtab) {
     constexpr int N = RA * RB;
-    const int P = 128 / RA;
+    constexpr int P = 128 / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
-    k_fpass_z_strain<float, RA, RB><<<gr, P * RA, (size_t)(N + 2 * N * P) * sizeof(float2), pl->stream>>>(
-        u, E, qtab, pl->d_twf[2], pl->geo_f, P);
+    k_fpass_z_strain<float, RA, RB><<<gr, 128, (size_t)(N + 4 * N * P) * sizeof(float2), pl->stream>>>(
+        u, E, qtab, pl->d_twf[2], pl->geo_f);
 }
 
 template <int RA, int RB>
 static void x_stress(bloch_plan* pl, int nb, float2* E) {
     constexpr int N = RA * RB;
     constexpr int LD = N + N / 16;
-    const int P = 128 / RA;
+    constexpr int P = 128 / RA;
     const long long rows = (long long)pl->Ny * pl->Nz;
     dim3 gr((unsigned)((rows + P - 1) / P), nb);
-    k_fpass_x_stress<float, RA, RB><<<gr, P * RA, (size_t)(N + 2 * P * LD) * sizeof(float2), pl->stream>>>(
-        E, pl->d_ids, pl->d_Cpf, pl->d_twf[0], pl->geo_f, P);
+    k_fpass_x_stress<float, RA, RB><<<gr, 128, (size_t)(N + 3 * P * LD) * sizeof(float2), pl->stream>>>(
+        E, pl->d_ids, pl->d_Cpf, pl->d_twf[0], pl->geo_f);
 }
 
 template <int RA, int RB>
 static void z_div(bloch_plan* pl, int nb, const float2* E, float2* out, const float* qtab) {
     constexpr int N = RA * RB;
-    const int P = 128 / RA;
+    constexpr int P = 128 / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
-    k_fpass_z_div<float, RA, RB><<<gr, P * RA, (size_t)(N + 2 * N * P) * sizeof(float2), pl->stream>>>(
-        E, out, qtab, pl->d_twf[2], pl->geo_f, P, (float)pl->Kscale);
+    k_fpass_z_div<float, RA, RB><<<gr, 128, (size_t)(N + 3 * N * P) * sizeof(float2), pl->stream>>>(
+        E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale);
 }
 
 #define NOALLOC_SWITCH(N, FN, ...)                \

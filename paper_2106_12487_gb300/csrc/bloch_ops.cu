@@ -270,26 +270,26 @@ template <typename T, int RA, int RB>
 static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
+    constexpr int P = 128 / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
-    const int P = 128 / RA;
-    const size_t smem = (size_t)(N + 2 * N * P) * sizeof(cplx_t<T>);
+    const size_t smem = (size_t)(N + 4 * N * P) * sizeof(cplx_t<T>);
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
-    k_fpass_z_strain<T, RA, RB><<<gr, P * RA, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
-                                                                    tw_of<T>(pl, 2), g, P);
+    k_fpass_z_strain<T, RA, RB><<<gr, 128, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
+                                                                 tw_of<T>(pl, 2), g);
 }
 
 template <typename T, int RA, int RB>
 static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
+    constexpr int P = 128 / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
-    const int P = 128 / RA;
-    const size_t smem = (size_t)(N + 2 * N * P) * sizeof(cplx_t<T>);
+    const size_t smem = (size_t)(N + 3 * N * P) * sizeof(cplx_t<T>);
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
-    k_fpass_z_div<T, RA, RB><<<gr, P * RA, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
-                                                                 tw_of<T>(pl, 2), g, P, out_scale);
+    k_fpass_z_div<T, RA, RB><<<gr, 128, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
+                                                              tw_of<T>(pl, 2), g, out_scale);
 }
 
 template <typename T, int RA, int RB>
@@ -297,13 +297,13 @@ static void fast_x3(bloch_plan* pl, int nb) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
     constexpr int LD = N + N / 16;
-    const int P = 128 / RA;
-    const size_t smem = (size_t)(N + 2 * P * LD) * sizeof(cplx_t<T>);
+    constexpr int P = 128 / RA;
+    const size_t smem = (size_t)(N + 3 * P * LD) * sizeof(cplx_t<T>);
     const long long rows = (long long)pl->Ny * pl->Nz;
     dim3 gr((unsigned)((rows + P - 1) / P), nb);
     ++pl->launches;
-    k_fpass_x_stress<T, RA, RB><<<gr, P * RA, smem, pl->stream>>>(ws_of<T>(pl).E, pl->d_ids, cpk_of<T>(pl),
-                                                                   tw_of<T>(pl, 0), g, P);
+    k_fpass_x_stress<T, RA, RB><<<gr, 128, smem, pl->stream>>>(ws_of<T>(pl).E, pl->d_ids, cpk_of<T>(pl),
+                                                                 tw_of<T>(pl, 0), g);
 }
 
 #define BLOCH_FAST_SWITCH(N, FN, ...)              \

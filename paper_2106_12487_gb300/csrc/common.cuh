@@ -30,6 +30,21 @@ template <int DIR, typename C> __host__ __device__ __forceinline__ C cmul_i(C a)
     return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
 }
 
+// Asynchronous global -> shared copy of one complex value (8 or 16 bytes);
+// src_valid = false fills zeros without reading.
+template <typename C>
+__device__ __forceinline__ void cp_async_cplx(C* smem, const C* gmem, bool src_valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = src_valid ? (int)sizeof(C) : 0;
+    if (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 #define BLOCH_CUDA_CHECK_RET(expr)                                  \
     do {                                                            \
         cudaError_t _e = (expr);                                    \

@@ -92,41 +92,55 @@ __global__ void __launch_bounds__(256) k_fpass_y(const cplx_t<T>* in, cplx_t<T>*
 }
 
 // --------------------------------------------------- pass 1: strain + inverse z
-// One thread per stage-2 task (blockDim.x == P * RA).  The z transform of
-// q_z U_k cannot be formed from that of U_k (q_z varies along the pencil), but
-// q_x, q_y are constant on a z pencil, so with a_k = F_z^-1(U_k) and
-// b_k = F_z^-1(q_z U_k) the six Voigt strains are
+// One thread per stage-2 task (blockDim.x == P * RA, P = 128 / RA).  The z
+// transform of q_z U_k cannot be formed from that of U_k (q_z varies along
+// the pencil), but q_x, q_y are constant on a z pencil, so with
+// a_k = F_z^-1(U_k) and b_k = F_z^-1(q_z U_k) the six Voigt strains are
 //   g_xx = q_x a_x, g_yy = q_y a_y, g_zz = b_z, g_yz = q_y a_z + b_y,
 //   g_xz = q_x a_z + b_x, g_xy = q_y a_x + q_x a_y.
-// Each displacement component is read once; components are taken in the
-// order z, x, y so that only a_z and a_x are carried between them.
+// Each displacement component is read once, in the order z, x, y (only a_z
+// and a_x are carried between them); the next component's pencils stream
+// into shared memory (cp.async, double buffered) while the current one is
+// transformed.
 template <typename T, int RA, int RB>
 __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
-                                                        const T* __restrict__ qtab,
-                                                        const cplx_t<T>* __restrict__ twz, Geo g, int P) {
+                                                           const T* __restrict__ qtab,
+                                                           const cplx_t<T>* __restrict__ twz, Geo g) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
+    constexpr int P = 128 / RA;
+    constexpr int NP = N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* bufA = tw + N;        // N * P
-    C* bufB = bufA + N * P;  // N * P
+    C* stg = tw + N;          // 2 x NP staging
+    C* bufA = stg + 2 * NP;   // NP
+    C* bufB = bufA + NP;      // NP
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
-    const long long plane = (long long)g.Nx * g.Ny;
-    const long long pi0 = (long long)blockIdx.x * P;
-    const int np = (int)min((long long)P, plane - pi0);
+    const unsigned plane = (unsigned)g.Nx * (unsigned)g.Ny;
+    const unsigned pi0 = blockIdx.x * P;
+    const int np = (int)min((unsigned)P, plane - pi0);
     const C* Ub = U + (size_t)b * 3 * g.V;
     C* Eb = E + (size_t)b * 6 * g.V;
     const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T* qyt = qxt + g.Nx;
     const T* qzt = qyt + g.Ny;
-    for (int i = tid; i < N; i += blockDim.x) tw[i] = twz[i];
-    // stage-2 task of this thread
+    auto prefetch = [&](int k, C* dstb) {
+        const C* src = Ub + (size_t)k * g.V;
+#pragma unroll
+        for (int e = tid; e < NP; e += 128) {
+            const int n = e / P, p = e % P;
+            const bool ok = p < np;
+            cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+        }
+        cp_async_commit();
+    };
+    prefetch(2, stg);
+    prefetch(0, stg + NP);
+    for (int i = tid; i < N; i += 128) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
-    const int pp = p2 < np ? p2 : 0;
-    const long long pi = pi0 + pp;
-    const T qx = qxt[(int)(pi % g.Nx)], qy = qyt[(int)(pi / g.Nx)];
-    // stage-1 task (threads tid < P * RB)
+    const unsigned pi = pi0 + (p2 < np ? p2 : 0);
+    const T qx = qxt[pi % (unsigned)g.Nx], qy = qyt[pi / (unsigned)g.Nx];
     const int p1 = tid % P, j1 = tid / P;
     const bool st1 = tid < P * RB;
     C az[RB], ax[RB];
@@ -136,12 +150,15 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
         const int k = kk == 0 ? 2 : kk - 1;   // z, x, y
+        if (kk < 2) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
         if (st1) {
+            const C* sb = stg + (kk & 1) * NP;
             C u[RA], v[RA];
 #pragma unroll
             for (int r = 0; r < RA; ++r) {
-                const int n = j1 + r * RB;
-                u[r] = (p1 < np) ? Ub[(size_t)k * g.V + (size_t)n * plane + pi0 + p1] : mk(T(0), T(0));
+                u[r] = sb[(j1 + r * RB) * P + p1];
                 v[r] = u[r];
             }
             RegDFT<RA, +1, C>::run(v);
@@ -154,13 +171,13 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
             for (int r = 0; r < RA; ++r) bufB[(j1 * RA + r) * P + p1] = u[r];
         }
         __syncthreads();
+        if (kk == 0) prefetch(1, stg);   // y into the buffer z has left
         C a[RB], bb[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
             a[r] = bufA[(j2 + r * RA) * P + p2];
             bb[r] = bufB[(j2 + r * RA) * P + p2];
         }
-        __syncthreads();
 #pragma unroll
         for (int r = 1; r < RB; ++r) {
             a[r] = twmul(a[r], tw[r * j2], +1);
@@ -197,55 +214,72 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
 // components of its RB elements are accumulated in registers:
 //   out_x = q_x S11 + q_y S12 + q_z S13, out_y = q_x S12 + q_y S22 + q_z S23,
 //   out_z = q_x S13 + q_y S23 + q_z S33   (S = forward z transform of sigma).
+// Stress components stream into shared memory two ahead (cp.async).
 template <typename T, int RA, int RB>
 __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restrict__ E, cplx_t<T>* __restrict__ out,
-                                                     const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
-                                                     Geo g, int P, T out_scale) {
+                                                        const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
+                                                        Geo g, T out_scale) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
+    constexpr int P = 128 / RA;
+    constexpr int NP = N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* bufs = tw + N;   // 2 * N * P
+    C* stg = tw + N;          // 2 x NP staging
+    C* xb = stg + 2 * NP;     // NP exchange
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
-    const long long plane = (long long)g.Nx * g.Ny;
-    const long long pi0 = (long long)blockIdx.x * P;
-    const int np = (int)min((long long)P, plane - pi0);
+    const unsigned plane = (unsigned)g.Nx * (unsigned)g.Ny;
+    const unsigned pi0 = blockIdx.x * P;
+    const int np = (int)min((unsigned)P, plane - pi0);
     const C* Eb = E + (size_t)b * 6 * g.V;
     C* ob = out + (size_t)b * 3 * g.V;
     const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T* qyt = qxt + g.Nx;
     const T* qzt = qyt + g.Ny;
-    for (int i = tid; i < N; i += blockDim.x) tw[i] = twz[i];
+    auto prefetch = [&](int c, C* dstb) {
+        const C* src = Eb + (size_t)c * g.V;
+#pragma unroll
+        for (int e = tid; e < NP; e += 128) {
+            const int n = e / P, p = e % P;
+            const bool ok = p < np;
+            cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+        }
+        cp_async_commit();
+    };
+    prefetch(0, stg);
+    prefetch(1, stg + NP);
+    for (int i = tid; i < N; i += 128) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
-    const int pp = p2 < np ? p2 : 0;
-    const long long pi = pi0 + pp;
-    const T qv[2] = {qxt[(int)(pi % g.Nx)], qyt[(int)(pi / g.Nx)]};
+    const unsigned pi = pi0 + (p2 < np ? p2 : 0);
+    const T qv[2] = {qxt[pi % (unsigned)g.Nx], qyt[pi / (unsigned)g.Nx]};
     const int p1 = tid % P, j1 = tid / P;
     const bool st1 = tid < P * RB;
     C acc[3][RB];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        C* buf = bufs + (c & 1) * N * P;
+        if (c < 5) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
         if (st1) {
+            const C* sb = stg + (c & 1) * NP;
             C v[RA];
 #pragma unroll
-            for (int r = 0; r < RA; ++r)
-                v[r] = (p1 < np) ? Eb[(size_t)c * g.V + (size_t)(j1 + r * RB) * plane + pi0 + p1] : mk(T(0), T(0));
+            for (int r = 0; r < RA; ++r) v[r] = sb[(j1 + r * RB) * P + p1];
             RegDFT<RA, -1, C>::run(v);
 #pragma unroll
-            for (int r = 0; r < RA; ++r) buf[(j1 * RA + r) * P + p1] = v[r];
+            for (int r = 0; r < RA; ++r) xb[(j1 * RA + r) * P + p1] = v[r];
         }
         __syncthreads();
+        if (c + 2 < 6) prefetch(c + 2, stg + (c & 1) * NP);
+        else cp_async_commit();
         C v[RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) v[r] = buf[(j2 + r * RA) * P + p2];
+        for (int r = 0; r < RB; ++r) v[r] = xb[(j2 + r * RA) * P + p2];
 #pragma unroll
         for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], -1);
         RegDFT<RB, -1, C>::run(v);
         // sigma_c contributes q_b sigma to out_a and q_a sigma to out_b
-        constexpr int dummy = 0;
-        (void)dummy;
         const int ca = c < 3 ? c : (c == 3 ? 1 : 0);
         const int cb = c < 3 ? c : (c == 5 ? 1 : 2);
 #pragma unroll
@@ -279,51 +313,67 @@ __device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 
 template <typename T, int RA, int RB>
 __global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
-                                                        const T* __restrict__ Cpk,
-                                                        const cplx_t<T>* __restrict__ twx, Geo g, int P) {
+                                                           const T* __restrict__ Cpk,
+                                                           const cplx_t<T>* __restrict__ twx, Geo g) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int LD = N + N / 16;
+    constexpr int P = 128 / RA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* bufs = tw + N;   // two exchange buffers of P * LD
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    C* stg = tw + N;          // 2 x P*LD staging (rows unpadded inside), reused by the forward exchange
+    C* xb = stg + 2 * P * LD; // P*LD exchange of the inverse transform
+    const int tid = threadIdx.x;
     const int b = blockIdx.y;
-    const long long rows = (long long)g.Ny * g.Nz;
-    const long long r0 = (long long)blockIdx.x * P;
-    const int nr = (int)min((long long)P, rows - r0);
+    const unsigned rows = (unsigned)g.Ny * (unsigned)g.Nz;
+    const unsigned r0 = blockIdx.x * P;
+    const int nr = (int)min((unsigned)P, rows - r0);
     C* Eb = E + (size_t)b * 6 * g.V;
-    for (int i = tid; i < N; i += nthr) tw[i] = twx[i];
+    auto prefetch = [&](int c, C* dstb) {
+        const C* src = Eb + (size_t)c * g.V + (size_t)r0 * N;
+#pragma unroll
+        for (int e = tid; e < P * N; e += 128) {
+            const int p = e / N, n = e % N;
+            const bool ok = p < nr;
+            cp_async_cplx(dstb + p * LD + n, src + (ok ? e : 0), ok);
+        }
+        cp_async_commit();
+    };
+    prefetch(0, stg);
+    prefetch(1, stg + P * LD);
+    for (int i = tid; i < N; i += 128) tw[i] = twx[i];
     // stage-2 task of this thread
     const int j2 = tid % RA, p2 = tid / RA;
     const bool own = p2 < nr;
     C s[6][RB];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        C* buf = bufs + (c & 1) * P * LD;
+        if (c < 5) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();
         // inverse stage 1 (radix RA): tasks (p, j < RB), j fastest
-        for (int t = tid; t < P * RB; t += nthr) {
-            const int j = t % RB, p = t / RB;
+        if (tid < P * RB) {
+            const int j = tid % RB, p = tid / RB;
+            const C* sb = stg + (c & 1) * P * LD + p * LD;
             C v[RA];
 #pragma unroll
-            for (int r = 0; r < RA; ++r)
-                v[r] = (p < nr) ? Eb[(size_t)c * g.V + (size_t)(r0 + p) * N + j + r * RB] : mk(T(0), T(0));
+            for (int r = 0; r < RA; ++r) v[r] = sb[j + r * RB];
             RegDFT<RA, +1, C>::run(v);
 #pragma unroll
-            for (int r = 0; r < RA; ++r) buf[p * LD + xpad(j * RA + r)] = v[r];
+            for (int r = 0; r < RA; ++r) xb[p * LD + xpad(j * RA + r)] = v[r];
         }
         __syncthreads();
+        if (c + 2 < 6) prefetch(c + 2, stg + (c & 1) * P * LD);
+        else cp_async_commit();
         // inverse stage 2 (radix RB), kept in registers
-        {
-            C v[RB];
+        C v[RB];
 #pragma unroll
-            for (int r = 0; r < RB; ++r) v[r] = buf[p2 * LD + xpad(j2 + r * RA)];
+        for (int r = 0; r < RB; ++r) v[r] = xb[p2 * LD + xpad(j2 + r * RA)];
 #pragma unroll
-            for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], +1);
-            RegDFT<RB, +1, C>::run(v);
+        for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], +1);
+        RegDFT<RB, +1, C>::run(v);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) s[c][r] = v[r];
-        }
+        for (int r = 0; r < RB; ++r) s[c][r] = v[r];
     }
     // stress sigma = C_g gamma at the RB owned elements (packed symmetric table, 21 per grain)
     if (own) {
@@ -355,9 +405,10 @@ __global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const i
             }
         }
     }
+    __syncthreads();   // the staging buffers become the forward exchange buffers
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        C* buf = bufs + (c & 1) * P * LD;
+        C* buf = stg + (c & 1) * P * LD;
         // forward stage 1 (radix RB, Ns = 1): the owned elements j2 + r RA are its inputs
         {
             C v[RB];
@@ -369,8 +420,8 @@ __global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const i
         }
         __syncthreads();
         // forward stage 2 (radix RA, Ns = RB): tasks (p, j < RB)
-        for (int t = tid; t < P * RB; t += nthr) {
-            const int j = t % RB, p = t / RB;
+        if (tid < P * RB) {
+            const int j = tid % RB, p = tid / RB;
             C v[RA];
 #pragma unroll
             for (int r = 0; r < RA; ++r) v[r] = buf[p * LD + xpad(j + r * RB)];
