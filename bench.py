@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
     ap.add_argument("--fft-variant", type=int, default=0, choices=[0, 1, 2],
                     help="0: two-stage register FFT passes, 1: shared-memory Stockham passes, 2: cuFFT baseline")
+    ap.add_argument("--no-trace", action="store_true",
+                    help="skip the extra traced (untimed) step that reports the solver's phase breakdown")
     ap.add_argument("--cuda-graph", type=int, default=1, choices=[0, 1],
                     help="1: PCG loop as one CUDA graph with a device-side while node; 0: host-driven loop "
                          "(same kernels; used for per-launch profiling)")
@@ -329,6 +331,14 @@ def run_ours(args, ws, rank, local):
 
     roof = kapply_roofline(plan, p, prec, args.kapply_nb, opt["fft_variant"])
 
+    # phase breakdown of one more (untimed) step on the first timed k batch
+    phases = None
+    if not args.no_trace:
+        plan.trace(True)
+        plan.solve_bands(kbatch(args.warmup), p.n_bands, allow_nonconv=True)
+        tr = plan.trace(False)
+        phases = {k: round(v["ms"], 3) for k, v in tr.items()}
+
     # end to end through the public API with host buffers: plan upload from
     # host arrays, band solve, frequencies back to host
     e2e = None
@@ -367,7 +377,8 @@ def run_ours(args, ws, rank, local):
                 "solver": {"cg_iterations": cg, "k_applies": kap,
                            "outer_iterations": sum(s["outer_iterations"] for s in stats_all),
                            "max_rel_residual": max(s["max_rel_residual"] for s in stats_all),
-                           "k_applies_per_eigenpair": kap / (args.steps * kps * p.n_bands)}}
+                           "k_applies_per_eigenpair": kap / (args.steps * kps * p.n_bands)},
+                "phases_ms": phases}
         print(json.dumps(line), flush=True)
     plan.close()
 

@@ -52,7 +52,8 @@ typedef enum {
     BLOCH_ENOTCONV_CG = 4,   /* PCG hit its iteration cap before the tolerance   */
     BLOCH_ENOTCONV_EIG = 5,  /* the eigensolver hit its sweep/restart cap        */
     BLOCH_ENONFINITE = 6,    /* NaN or Inf met in inputs or iterates             */
-    BLOCH_EUNSUPPORTED = 7   /* grid size with a prime factor > 7, or too large  */
+    BLOCH_EUNSUPPORTED = 7   /* grid size with a prime factor > 7 or too large;
+                                Lanczos with a non-uniform density             */
 } bloch_status;
 
 typedef enum { BLOCH_FP64 = 0, BLOCH_FP32 = 1 } bloch_precision;
@@ -66,8 +67,10 @@ typedef struct {
                             BLOCH_FP32: fields and CG in FP32 complex with FP32
                             accumulation, then an FP64 Rayleigh-Ritz refinement of the
                             converged block.  Default BLOCH_FP64.                       */
-    int32_t method;      /* BLOCH_LANCZOS (shift-invert Lanczos with thick restart) or
-                            BLOCH_SUBSPACE (Algorithm 1).  Default BLOCH_SUBSPACE.       */
+    int32_t method;      /* BLOCH_LANCZOS (shift-invert Lanczos with thick restart; needs a
+                            uniform density, else bloch_solve_bands returns
+                            BLOCH_EUNSUPPORTED) or BLOCH_SUBSPACE (Algorithm 1, any
+                            density).  Default BLOCH_SUBSPACE.                          */
     double tol_lin;      /* PCG stop: ||Y - A U||_2 <= tol_lin ||Y||_2.  Default 1e-10.  */
     double tol_eig;      /* eigensolver stop (see bloch_solve_bands).  Default 1e-10.    */
     int32_t max_cg;      /* PCG iteration cap per solve.  Default 2000.                  */
@@ -92,7 +95,31 @@ typedef struct {
                             2 = plain-form baseline: cuFFT 3D transforms with unfused
                             pointwise kernels.  All compute the same operator.
                             Default 0.                                                  */
+    int32_t autotune;    /* 1 = the first bloch_solve_bands call on the plan runs
+                            bloch_plan_autotune (precision of these options, systems =
+                            the eigensolver's block size) and keeps its choice of FFT
+                            pass variant and tile sizes, overriding fft_variant;
+                            0 = use fft_variant as given.  Default 0.                   */
+    int32_t tile_pmax;   /* cap on pencils per CTA of the shared-memory passes (z and y
+                            passes; x passes use half of it), one of 4, 8, 16, 32; each
+                            pass lowers it further to fit its shared-memory budget.
+                            0 = 32.  Default 0.                                         */
 } bloch_options;
+
+/* Outcome of bloch_plan_autotune. */
+typedef struct {
+    int32_t fft_variant;         /* chosen pass variant (meaning as in bloch_options)       */
+    int32_t tile_pmax;           /* chosen cap on pencils per CTA of the shared-memory
+                                    passes (z and y passes; x passes use half of it)       */
+    int32_t saturating_systems;  /* smallest number of systems per launch whose time per
+                                    system is within 5 % of the best measured with the
+                                    chosen configuration (batches of systems, 2 systems,
+                                    4 systems ... up to 8 x systems, as memory allows)   */
+    int32_t candidates;          /* configurations timed                                    */
+    double ms_per_system[3];     /* best time of one A_k apply per system for variants 0,
+                                    1, 2 (milliseconds); -1 where the variant was not timed
+                                    (variant 0 when no axis has a fast pass)             */
+} bloch_tune_report;
 
 /* Statistics of the last bloch_solve_bands call (all counts summed over k). */
 typedef struct {
@@ -297,6 +324,51 @@ bloch_status bloch_lp_export_block(const bloch_lp* lp, int32_t block, int32_t gr
  * preconditioner).  The network must outlive its use by the plan.
  */
 bloch_status bloch_plan_set_preconditioner(bloch_plan* plan, const bloch_lp* lp);
+
+/*
+ * Autotuner of the batched operator (no counterpart in the paper; it serves
+ * the Algorithm 3 loop, which applies A_k to many systems at once).  Times,
+ * with CUDA events on the plan's stream, one A_k apply of `systems` systems
+ * (deterministic pseudo-random Fourier fields, one nonzero wave vector) for
+ * each candidate configuration: fft_variant 0 (when an axis has a fast pass)
+ * and 1, each with pencils-per-CTA caps {4, 8, 16, 32} for the shared-memory
+ * passes it uses, and 2 (cuFFT).  The fastest configuration is kept by the
+ * plan for both precisions (all compute the same operator) and reported in
+ * *report (may be NULL).  Then times batches of 2x, 4x, 8x systems with it
+ * to report the saturating batch size.
+ *   precision  BLOCH_FP32 or BLOCH_FP64: the field type timed
+ *   systems    systems per launch to tune for, in [1, 10922]
+ * Allocates 2 x systems x 3 x V complex of scratch for the call (more for the
+ * batch sweep, skipped where memory is short) and grows the plan's operator
+ * workspace.  Must not run concurrently with other calls on the same plan.
+ * Errors: BLOCH_EINVAL (arguments), BLOCH_ENOMEM, BLOCH_ECUDA.
+ */
+bloch_status bloch_plan_autotune(bloch_plan* plan, int32_t precision, int32_t systems, bloch_tune_report* report);
+
+/*
+ * Phase tracer of bloch_solve_bands (no counterpart in the paper).  While
+ * enabled, every solve records CUDA-event pairs on the plan's stream around
+ * its phases and adds their durations (milliseconds) to the slots:
+ *   0 PCG solves in FP32            1 PCG solves in FP64
+ *   2 FP32 residual applies (A_k u, M u, Rayleigh quotients, residual norms)
+ *   3 FP64 residual applies (the FP64 check of the FP32 form, incl. conversion)
+ *   4 Lanczos orthogonalisation (inner products, updates, normalisation)
+ *   5 Algorithm 1 projections (correction, Gram matrices, basis rotation)
+ *   6 GPU span of the solve (first to last event; 6 minus the sum of 0-5 is
+ *     idle time and untraced work on the stream)
+ *   7 host wall time of the solve
+ * count[i] = intervals recorded.  bloch_plan_trace synchronises the plan's
+ * stream, writes the totals since the previous call to *out (may be NULL),
+ * resets them, and then turns tracing on (enable = 1) or off (0).  Tracing
+ * costs two event records per phase interval (none per PCG iteration).
+ * Errors: BLOCH_EINVAL, BLOCH_ECUDA.
+ */
+typedef struct {
+    double ms[8];
+    int64_t count[8];
+} bloch_trace;
+
+bloch_status bloch_plan_trace(bloch_plan* plan, int32_t enable, bloch_trace* out);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* bloch_last_error(void);

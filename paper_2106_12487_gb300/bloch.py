@@ -27,7 +27,8 @@ EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", 
             "bloch_host_gen_eig", "bloch_last_error", "bloch_plan_device_bytes", "bloch_plan_kernel_launches",
             "bloch_apply_K_noalloc", "bloch_lp_num_params", "bloch_lp_create", "bloch_lp_destroy", "bloch_lp_params",
             "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train", "bloch_lp_num_blocks", "bloch_lp_export_block",
-            "bloch_plan_set_preconditioner"]
+            "bloch_plan_set_preconditioner", "bloch_plan_autotune",
+            "bloch_plan_trace"]
 
 
 class BlochError(RuntimeError):
@@ -40,7 +41,29 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("method", ctypes.c_int32), ("tol_lin", ctypes.c_double),
                 ("tol_eig", ctypes.c_double), ("max_cg", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("k_batch", ctypes.c_int32), ("ncv", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("cuda_graph", ctypes.c_int32), ("fft_variant", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("cuda_graph", ctypes.c_int32), ("fft_variant", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("tile_pmax", ctypes.c_int32)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_int64 * 8)]
+
+    PHASES = ("pcg_fp32", "pcg_fp64", "residual_fp32", "residual_fp64", "lanczos_orth", "projection",
+              "gpu_span", "wall")
+
+    def as_dict(self):
+        return {ph: {"ms": self.ms[i], "count": int(self.count[i])} for i, ph in enumerate(self.PHASES)}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("fft_variant", ctypes.c_int32), ("tile_pmax", ctypes.c_int32),
+                ("saturating_systems", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("ms_per_system", ctypes.c_double * 3)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_[:4]}
+        d["ms_per_system"] = list(self.ms_per_system)
+        return d
 
 
 class Stats(ctypes.Structure):
@@ -96,11 +119,13 @@ def lib():
     L.bloch_lp_num_blocks.restype = ctypes.c_int32
     L.bloch_lp_export_block.argtypes = [VP, I32, P(I32), P(D), P(D), P(D), P(I32)]
     L.bloch_plan_set_preconditioner.argtypes = [VP, VP]
+    L.bloch_plan_autotune.argtypes = [VP, I32, I32, P(TuneReport)]
+    L.bloch_plan_trace.argtypes = [VP, I32, P(Trace)]
     for f in ["bloch_lp_create", "bloch_lp_params", "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train",
               "bloch_lp_export_block", "bloch_plan_set_preconditioner"]:
         getattr(L, f).restype = ctypes.c_int
     for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
-              "bloch_solve_bands", "bloch_host_gen_eig"]:
+              "bloch_solve_bands", "bloch_host_gen_eig", "bloch_plan_autotune", "bloch_plan_trace"]:
         getattr(L, f).restype = ctypes.c_int
     _LIB = L
     return L
@@ -189,6 +214,20 @@ class Plan:
     @property
     def device_bytes(self) -> int:
         return int(lib().bloch_plan_device_bytes(self.handle))
+
+    def trace(self, enable: bool) -> dict:
+        """bloch_plan_trace: phase times since the previous call (ms), then
+        switch tracing on or off."""
+        tr = Trace()
+        _check(lib().bloch_plan_trace(self.handle, 1 if enable else 0, ctypes.byref(tr)))
+        return tr.as_dict()
+
+    def autotune(self, precision: int, systems: int) -> dict:
+        """bloch_plan_autotune: time the operator's pass configurations on
+        `systems` systems and keep the fastest; returns the report."""
+        rep = TuneReport()
+        _check(lib().bloch_plan_autotune(self.handle, int(precision), int(systems), ctypes.byref(rep)))
+        return rep.as_dict()
 
     # ---------------------------------------------------------------- ops
     def _kv(self, k, nb):

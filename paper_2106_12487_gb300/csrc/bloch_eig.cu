@@ -287,6 +287,7 @@ struct Subspace {
     long long* d_idx = nullptr;
     double2 *U64 = nullptr, *KU64 = nullptr, *MU64 = nullptr;
     int gblk = 0, dblk = 0;
+    size_t gsmem = 0;
 
     struct Slot {
         int kidx = -1;
@@ -333,9 +334,13 @@ struct Subspace {
             if ((s = alloc(&MU, blk)) || (s = alloc(&MUb, blk))) return s;
         }
         dblk = (int)std::max(1LL, std::min<long long>((n3 + 255) / 256, std::max(1, 2048 / std::max(1, B * q))));
-        gblk = (int)std::max(1LL, std::min<long long>((n3 + kG2Chunk - 1) / kG2Chunk, std::max(1, 608 / B)));
+        gblk = (int)std::max(1LL, std::min<long long>((n3 + kGKChunk - 1) / kGKChunk, std::max(1, 608 / B)));
+        gsmem = gk_smem<T>(q, !uniform);
+        if (cudaFuncSetAttribute(k_gram_km<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem) !=
+            cudaSuccess)
+            return set_error(BLOCH_ECUDA, "cudaFuncSetAttribute (Gram kernel)");
         if ((s = alloc(&d_part, (size_t)B * q * dblk * 3)) || (s = alloc(&d_scal, (size_t)B * q * 2)) ||
-            (s = alloc(&d_gpart, (size_t)B * gblk * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
+            (s = alloc(&d_gpart, (size_t)B * gblk * 2 * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
             (s = alloc(&d_Q, (size_t)B * q * q)) || (s = alloc(&d_idx, (size_t)3 * q)) ||
             (s = alloc(&d_val, (size_t)3 * q)))
             return s;
@@ -466,6 +471,7 @@ struct Subspace {
                 int j = i;
                 while (j < first + count && (slots[j].phase == 0 || !fp64res)) ++j;
                 if ((s = set_k_range(i, j - i)) != BLOCH_OK) return s;
+                TraceScope tr(pl, std::is_same<T, float>::value ? TR_RES32 : TR_RES64);
                 launch_K<T>(pl, (j - i) * q, vec(U, i), vec(KU, i), T(1));
                 if (!uniform) launch_M<T>(pl, (j - i) * q, vec(U, i), vec(MU, i), T(1));
                 if ((s = residual_run<T>(i, j - i, vec(U, i), vec(KU, i), uniform ? nullptr : vec(MU, i))) != BLOCH_OK)
@@ -473,6 +479,7 @@ struct Subspace {
                 i = j;
             } else {
                 // FP64 refinement: residual of the FP32 block from an FP64 operator apply
+                TraceScope tr(pl, TR_RES64);
                 const size_t ne = (size_t)q * n3;
                 ++pl->launches;
                 k_convert<T, double><<<1024, 256, 0, pl->stream>>>(vec(U, i), U64, ne);
@@ -659,6 +666,7 @@ struct Subspace {
             st->linear_solves += (long long)nact * q;
             if (s != BLOCH_OK && s != BLOCH_ENOTCONV_CG) return s;
             // U_bar = delta + U / lam
+            const int tr_proj = trace_begin(pl, TR_PROJECT);
             std::vector<double> inv((size_t)nact * q);
             for (int i = 0; i < nact; ++i)
                 for (int j = 0; j < q; ++j) inv[(size_t)i * q + j] = slots[i].lam[j] > 0 ? 1.0 / slots[i].lam[j] : 0.0;
@@ -672,18 +680,15 @@ struct Subspace {
             ++pl->launches;
             k_kn<T><<<4096, 256, 0, pl->stream>>>(U, uniform ? nullptr : MU, rho_s, ws_of<T>(pl).r, KU, ne);
             if (!uniform) launch_M<T>(pl, nact * q, Ub, MUb, T(1));
-            // projections K = Ub^H Kn, M = Ub^H Mn
+            // projections K = Ub^H Kn, M = Ub^H Mn in one pass over the block
             dim3 gg(gblk, nact);
             const int npair = q * q;
             ++pl->launches;
-            k_gram2<T><<<gg, 256, 0, pl->stream>>>(Ub, KU, q, n3, d_gpart);
+            k_gram_km<T><<<gg, kGKThreads, gsmem, pl->stream>>>(Ub, KU, uniform ? nullptr : MUb, q, n3, d_gpart);
             ++pl->launches;
-            k_gram_final<<<dim3((npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair, d_G);
-            ++pl->launches;
-            k_gram2<T><<<gg, 256, 0, pl->stream>>>(Ub, uniform ? Ub : MUb, q, n3, d_gpart);
-            ++pl->launches;
-            k_gram_final<<<dim3((npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair,
-                                                                                   d_G + (size_t)nact * npair);
+            k_gram_final<<<dim3((2 * npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair, nact,
+                                                                                       d_G);
+            trace_end(pl, tr_proj);
             std::vector<double2> G((size_t)2 * nact * npair);
             BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(G.data(), d_G, sizeof(double2) * G.size(), cudaMemcpyDeviceToHost,
                                                  pl->stream));
@@ -706,8 +711,11 @@ struct Subspace {
             BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_Q, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice,
                                                  pl->stream));
             dim3 gb((unsigned)std::min<long long>((n3 + 127) / 128, 8192), nact);
-            ++pl->launches;
-            k_basis<T><<<gb, 128, 0, pl->stream>>>(Ub, U, d_Q, q, n3);
+            {
+                TraceScope tr(pl, TR_PROJECT);
+                ++pl->launches;
+                k_basis<T><<<gb, 128, 0, pl->stream>>>(Ub, U, d_Q, q, n3);
+            }
             BLOCH_CUDA_CHECK_RET(cudaGetLastError());
             if ((s = residual_step(0, nact)) != BLOCH_OK) return s;
         }
@@ -1031,6 +1039,7 @@ struct Lanczos {
             st->linear_solves += nact;
             if (s != BLOCH_OK && s != BLOCH_ENOTCONV_CG) return s;
             // two passes of classical Gram-Schmidt in the M inner product
+            const int tr_orth = trace_begin(pl, TR_ORTHO);
             std::vector<cd> hsum((size_t)nact * (m + 1), cd(0, 0));
             int maxnv = 0;
             for (int i = 0; i < nact; ++i) maxnv = std::max(maxnv, nv[i]);
@@ -1067,6 +1076,7 @@ struct Lanczos {
                 cudaMemcpyAsync(d_s, inv.data(), sizeof(double) * nact, cudaMemcpyHostToDevice, pl->stream));
             ++pl->launches;
             k_copy_scaled<T><<<gc, 256, 0, pl->stream>>>(Xc, d_src, Vb, d_dst, d_s, n3);
+            trace_end(pl, tr_orth);
             BLOCH_CUDA_CHECK_RET(cudaGetLastError());
             // advance; analyse full bases
             std::vector<int> finished;
@@ -1219,6 +1229,12 @@ bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_lis
     bloch_stats st;
     std::memset(&st, 0, sizeof(st));
     bloch_status s;
+    const int tr_span = trace_begin(pl, TR_SPAN);
+    if (pl->opt.autotune && !pl->tuned) {
+        const int q = pl->opt.block > 0 ? pl->opt.block : std::min(2 * n_bands, n_bands + 8);
+        s = bloch_plan_autotune(pl, pl->opt.precision, std::max(1, std::min(q, 10922)), nullptr);
+        if (s != BLOCH_OK) return s;
+    }
     if (pl->opt.method == BLOCH_SUBSPACE) {
         if (pl->opt.precision == BLOCH_FP32)
             s = run_subspace<float>(pl, ks, n_bands, omega_out, vecs_out, &st, true);
@@ -1230,8 +1246,11 @@ bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_lis
         else
             s = run_lanczos<double>(pl, ks, n_bands, omega_out, vecs_out, &st);
     }
+    trace_end(pl, tr_span);
     cudaStreamSynchronize(pl->stream);
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    trace_add(pl, TR_WALL, 1e3 * st.seconds);
+    trace_collect(pl);
     pl->last_stats = st;
     if (stats) *stats = st;
     return s;

@@ -84,16 +84,20 @@ static int choose_P(int N, int bufs, size_t elem, size_t budget, long long npen,
     return P;
 }
 
+// Pencils per CTA of the shared-memory passes: at most pmax (z, y) or pmax / 2
+// (x), reduced until the tile fits the shared-memory budget of its pass.
 template <typename T>
-static TileCfg make_tiles(int Nx, int Ny, int Nz) {
+static TileCfg make_tiles(int Nx, int Ny, int Nz, int pmax) {
     TileCfg t{};
     const size_t el = sizeof(cplx_t<T>);
     auto pad = [&](int N) { return (size_t)((N + 1) & ~1) * el; };
-    t.Pz5 = choose_P(Nz, 5, el, 96 * 1024, (long long)Nx * Ny, 32);
-    t.Py2 = choose_P(Ny, 2, el, 64 * 1024, (long long)Nx * Nz, 32);
-    t.Pz2 = choose_P(Nz, 2, el, 64 * 1024, (long long)Nx * Ny, 32);
-    t.Px7 = choose_P(Nx, 7, el, 96 * 1024, (long long)Ny * Nz, 16);
-    t.Px4 = choose_P(Nx, 4, el, 64 * 1024, (long long)Ny * Nz, 16);
+    const int px = std::max(1, pmax / 2);
+    t.pmax = pmax;
+    t.Pz5 = choose_P(Nz, 5, el, 96 * 1024, (long long)Nx * Ny, pmax);
+    t.Py2 = choose_P(Ny, 2, el, 64 * 1024, (long long)Nx * Nz, pmax);
+    t.Pz2 = choose_P(Nz, 2, el, 64 * 1024, (long long)Nx * Ny, pmax);
+    t.Px7 = choose_P(Nx, 7, el, 96 * 1024, (long long)Ny * Nz, px);
+    t.Px4 = choose_P(Nx, 4, el, 64 * 1024, (long long)Ny * Nz, px);
     t.smem_z5 = pad(Nz) + (size_t)5 * Nz * t.Pz5 * el;
     t.smem_y2 = pad(Ny) + (size_t)2 * Ny * t.Py2 * el;
     t.smem_z2 = pad(Nz) + (size_t)2 * Nz * t.Pz2 * el;
@@ -214,6 +218,33 @@ void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out
 // ------------------------------------------------ fast two-stage passes
 static bool fast_axis(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
 static bool fast_x(int N) { return N == 16 || N == 32 || N == 64 || N == 128; }
+
+void drop_pcg_graphs(bloch_plan* pl) {
+    for (auto& e : pl->pcg_graphs) {
+        cudaGraphExecDestroy(e.exec);
+        cudaGraphDestroy(e.graph);
+    }
+    pl->pcg_graphs.clear();
+}
+
+void configure_passes(bloch_plan* pl, int variant, int pmax) {
+    drop_pcg_graphs(pl);   // instantiated graphs hold the previous launch configuration
+    pl->variant = variant;
+    pl->fast = variant == 0;
+    pl->tile_f = make_tiles<float>(pl->Nx, pl->Ny, pl->Nz, pmax);
+    pl->tile_d = make_tiles<double>(pl->Nx, pl->Ny, pl->Nz, pmax);
+}
+
+bool has_fast_pass(const bloch_plan* pl, int precision) {
+    if (fast_axis(pl->Ny)) return true;
+    return precision == BLOCH_FP32 && (fast_x(pl->Nz) || fast_x(pl->Nx));
+}
+
+bool has_generic_pass(const bloch_plan* pl, int precision) {
+    if (!fast_axis(pl->Ny)) return true;
+    return precision != BLOCH_FP32 || !fast_x(pl->Nz) || !fast_x(pl->Nx);
+}
+
 
 template <typename K>
 static void fast_attr(K k) {
@@ -575,6 +606,7 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
                      void (*hook)(void*, int), void* hook_ctx) {
     bloch_status st = ensure_cg<T>(pl, nb);
     if (st != BLOCH_OK) return st;
+    TraceScope trace_pcg(pl, std::is_same<T, float>::value ? TR_PCG32 : TR_PCG64);
     Workspace<T>& w = ws_of<T>(pl);
     const Geo& g = geo_of<T>(pl);
     const int nblk = vec_blocks(pl, nb);
@@ -722,10 +754,8 @@ void bloch_plan_destroy(bloch_plan* pl) {
     if (!pl) return;
     cudaStreamSynchronize(pl->stream);
     cufft_release(pl);
-    for (auto& e : pl->pcg_graphs) {
-        cudaGraphExecDestroy(e.exec);
-        cudaGraphDestroy(e.graph);
-    }
+    drop_pcg_graphs(pl);
+    trace_release(pl);
     cudaFree(pl->d_iter);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     free_ws_all(pl);
@@ -809,6 +839,11 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     pl->G = G;
     if (opt) pl->opt = *opt;
     else bloch_default_options(&pl->opt);
+    if (pl->opt.tile_pmax != 0 && pl->opt.tile_pmax != 4 && pl->opt.tile_pmax != 8 && pl->opt.tile_pmax != 16 &&
+        pl->opt.tile_pmax != 32) {
+        delete pl;
+        return set_error(BLOCH_EINVAL, "tile_pmax must be 0, 4, 8, 16 or 32");
+    }
     if (pl->opt.fft_variant < 0 || pl->opt.fft_variant > 2) {
         delete pl;
         return set_error(BLOCH_EINVAL, "fft_variant must be 0, 1 or 2");
@@ -947,8 +982,9 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         pl->geo_f.ax[a] = make_axis(grid[a], 4);   // radices up to 16 in FP32
         pl->geo_d.ax[a] = make_axis(grid[a], 3);   // up to 8 in FP64 (register budget)
     }
-    pl->tile_f = make_tiles<float>(pl->Nx, pl->Ny, pl->Nz);
-    pl->tile_d = make_tiles<double>(pl->Nx, pl->Ny, pl->Nz);
+    const int pmax = pl->opt.tile_pmax > 0 ? pl->opt.tile_pmax : kDefaultPmax;
+    pl->tile_f = make_tiles<float>(pl->Nx, pl->Ny, pl->Nz, pmax);
+    pl->tile_d = make_tiles<double>(pl->Nx, pl->Ny, pl->Nz, pmax);
     pl->nblk_max = vec_blocks(pl, 1);
     *out = pl;
     return BLOCH_OK;

@@ -8,107 +8,113 @@
 
 namespace bloch {
 
-constexpr int kGramChunk = 32;
 constexpr int kQMax = 32;
 
-// partial[slot][blk][i][j] = sum_e conj(A[slot][i][e]) B[slot][j][e], i, j < q.
-// Vectors of one slot are contiguous: A + (slot*q + i)*n_per.
+// Fused projections of Algorithm 1, one pass over the block:
+//   K[slot][i][j] = sum_e conj(A[i][e]) Bk[i][e]                    (all i, j < q)
+//   M[slot][i][j] = sum_e conj(A[i][e]) Bm[j][e]    Bm != nullptr   (all i, j)
+//                 = sum_e conj(A[i][e]) A[j][e]     Bm == nullptr   (i <= j tiles, mirrored)
+// partial[slot][blk][0..1][q][q] (K, then M); vectors of one slot are
+// contiguous (A + (slot*q + i)*n_per).  Each thread owns a 4x4 tile of (i, j)
+// and one group of elements of every chunk.  Chunks of kGKChunk elements are
+// staged element-major (row length RS, odd, so consecutive elements fall in
+// different banks and the tile rows a warp reads are spread) by cp.async, two
+// chunks in flight; element groups are reduced through shared memory at the end.
+constexpr int kGKChunk = 64;
+constexpr int kGKThreads = 256;
+
+__host__ __device__ constexpr int gk_rs(int q) { return ((q + 3) / 4) * 4 + 1; }
+__host__ __device__ constexpr int gk_nmat(bool has_m) { return has_m ? 3 : 2; }
+// dynamic shared memory of k_gram_km: two stages of nmat element-major tiles
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const cplx_t<T>* __restrict__ A, const cplx_t<T>* __restrict__ B, int q,
-                                              long long n_per, double2* __restrict__ partial) {
-    using C = cplx_t<T>;
-    __shared__ C sA[kQMax][kGramChunk];
-    __shared__ C sB[kQMax][kGramChunk];
-    const int slot = blockIdx.y;
-    const C* Ab = A + (size_t)slot * q * n_per;
-    const C* Bb = B + (size_t)slot * q * n_per;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int npair = q * q;
-    T acc[4][2];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) acc[s][0] = acc[s][1] = T(0);
-    const long long nchunk = (n_per + kGramChunk - 1) / kGramChunk;
-    for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-        const long long e0 = ch * kGramChunk;
-        for (int t = tid; t < q * kGramChunk; t += nthr) {
-            const int i = t / kGramChunk, c = t - i * kGramChunk;
-            const long long e = e0 + c;
-            const C z = mk(T(0), T(0));
-            sA[i][c] = e < n_per ? Ab[(size_t)i * n_per + e] : z;
-            sB[i][c] = e < n_per ? Bb[(size_t)i * n_per + e] : z;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int pr = tid + s * nthr;
-            if (pr < npair) {
-                const int i = pr / q, j = pr - i * q;
-                T re = acc[s][0], im = acc[s][1];
-#pragma unroll 8
-                for (int c = 0; c < kGramChunk; ++c) {
-                    const C a = sA[i][c], b = sB[j][c];
-                    re = fma(a.x, b.x, fma(a.y, b.y, re));
-                    im = fma(a.x, b.y, fma(-a.y, b.x, im));
-                }
-                acc[s][0] = re;
-                acc[s][1] = im;
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int pr = tid + s * nthr;
-        if (pr < npair)
-            partial[((size_t)slot * gridDim.x + blockIdx.x) * npair + pr] = make_double2(acc[s][0], acc[s][1]);
-    }
+size_t gk_smem(int q, bool has_m) {
+    const size_t stage = (size_t)gk_nmat(has_m) * kGKChunk * gk_rs(q) * sizeof(cplx_t<T>);
+    const size_t red = (size_t)kGKThreads * 16 * sizeof(cplx_t<T>);
+    return 2 * stage > red ? 2 * stage : red;
 }
 
-// Register-tiled Gram: each thread owns a 4x4 tile of (i, j) pairs and one
-// group of elements of every chunk; element groups are reduced through shared
-// memory at the end.  partial layout as k_gram.
-constexpr int kG2Chunk = 64;
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram2(const cplx_t<T>* __restrict__ A, const cplx_t<T>* __restrict__ B, int q,
-                                               long long n_per, double2* __restrict__ partial) {
+__global__ void __launch_bounds__(kGKThreads) k_gram_km(const cplx_t<T>* __restrict__ A,
+                                                        const cplx_t<T>* __restrict__ Bk,
+                                                        const cplx_t<T>* __restrict__ Bm, int q, long long n_per,
+                                                        double2* __restrict__ partial) {
     using C = cplx_t<T>;
-    constexpr int QP = kQMax;   // padded rows
-    __shared__ C sA[QP][kG2Chunk];
-    __shared__ C sB[QP][kG2Chunk];
-    const int slot = blockIdx.y;
-    const C* Ab = A + (size_t)slot * q * n_per;
-    const C* Bb = B + (size_t)slot * q * n_per;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const bool has_m = Bm != nullptr;
+    const int nmat = gk_nmat(has_m);
+    const int RS = gk_rs(q);
     const int side = (q + 3) / 4;
-    const int ntile = side * side;
-    const int G = nthr / ntile;           // element groups
+    const int nk = side * side;
+    const int nm = has_m ? side * side : side * (side + 1) / 2;
+    const int ntile = nk + nm;
+    const int G = kGKThreads / ntile;   // element groups (>= 2 for q <= 32)
+    const int tid = threadIdx.x;
     const int tile = tid % ntile, grp = tid / ntile;
     const bool act = grp < G;
-    const int i0 = (tile / side) * 4, j0 = (tile % side) * 4;
+    // tile -> (matrix, i0, j0, operand pointers' matrix index)
+    int which, i0, j0;
+    if (tile < nk) {
+        which = 0;
+        i0 = (tile / side) * 4;
+        j0 = (tile % side) * 4;
+    } else if (has_m) {
+        which = 1;
+        i0 = ((tile - nk) / side) * 4;
+        j0 = ((tile - nk) % side) * 4;
+    } else {   // upper-triangular tile index t -> (ti <= tj)
+        which = 1;
+        int t = tile - nk, ti = 0;
+        while (t >= side - ti) {
+            t -= side - ti;
+            ++ti;
+        }
+        i0 = ti * 4;
+        j0 = (ti + t) * 4;
+    }
+    const int bmat = which == 0 ? 1 : (has_m ? 2 : 0);   // staged matrix of the right operand
+    const int slot = blockIdx.y;
+    const size_t sbase = (size_t)slot * q * n_per;
+    const int stage_elems = nmat * kGKChunk * RS;
+    auto stage_load = [&](long long ch, int buf) {
+        C* dst = sm + (size_t)buf * stage_elems;
+        const long long e0 = ch * kGKChunk;
+        const int rows = side * 4;
+        for (int t = tid; t < nmat * rows * kGKChunk; t += kGKThreads) {
+            const int m = t / (rows * kGKChunk);
+            const int r = t - m * rows * kGKChunk;
+            const int i = r / kGKChunk, c = r - i * kGKChunk;
+            const long long e = e0 + c;
+            const bool ok = i < q && e < n_per;
+            const C* src = (m == 0 ? A : (m == 1 ? Bk : Bm)) + sbase;
+            cp_async_cplx(dst + ((size_t)m * kGKChunk + c) * RS + i, src + (ok ? (size_t)i * n_per + e : 0), ok);
+        }
+        cp_async_commit();
+    };
     T acc[4][4][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c][0] = acc[a][c][1] = T(0);
-    const long long nchunk = (n_per + kG2Chunk - 1) / kG2Chunk;
-    const int rows = side * 4;
-    for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-        const long long e0 = ch * kG2Chunk;
-        for (int t = tid; t < rows * kG2Chunk; t += nthr) {
-            const int i = t / kG2Chunk, c = t - i * kG2Chunk;
-            const long long e = e0 + c;
-            const bool ok = i < q && e < n_per;
-            sA[i][c] = ok ? Ab[(size_t)i * n_per + e] : mk(T(0), T(0));
-            sB[i][c] = ok ? Bb[(size_t)i * n_per + e] : mk(T(0), T(0));
-        }
+    const long long nchunk = (n_per + kGKChunk - 1) / kGKChunk;
+    long long ch = blockIdx.x;
+    if (ch < nchunk) stage_load(ch, 0);
+    else cp_async_commit();
+    if (ch + gridDim.x < nchunk) stage_load(ch + gridDim.x, 1);
+    else cp_async_commit();
+    int buf = 0;
+    for (; ch < nchunk; ch += gridDim.x) {
+        cp_async_wait<1>();
         __syncthreads();
         if (act) {
-            for (int e = grp; e < kG2Chunk; e += G) {
+            const C* sa = sm + (size_t)buf * stage_elems;
+            const C* sb = sa + (size_t)bmat * kGKChunk * RS;
+            for (int e = grp; e < kGKChunk; e += G) {
                 C a[4], b[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    a[u] = sA[i0 + u][e];
-                    b[u] = sB[j0 + u][e];
+                    a[u] = sa[e * RS + i0 + u];
+                    b[u] = sb[e * RS + j0 + u];
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
@@ -119,11 +125,16 @@ __global__ void __launch_bounds__(256) k_gram2(const cplx_t<T>* __restrict__ A, 
                     }
             }
         }
-        __syncthreads();
+        __syncthreads();   // every thread is done with this stage before it is refilled
+        const long long nx = ch + 2 * (long long)gridDim.x;
+        if (nx < nchunk) stage_load(nx, buf);
+        else cp_async_commit();
+        buf ^= 1;
     }
-    // reduce the element groups: reuse sA as a [ntile][16] complex scratch per group pass
-    double2* out = partial + ((size_t)slot * gridDim.x + blockIdx.x) * q * q;
-    C* red = &sA[0][0];   // QP*kG2Chunk >= ntile*16 entries (ntile <= 64)
+    cp_async_wait<0>();
+    __syncthreads();
+    // reduce the element groups through shared memory: red[tile][16]
+    C* red = sm;
     for (int gsum = 0; gsum < G; ++gsum) {
         if (act && grp == gsum) {
 #pragma unroll
@@ -137,25 +148,42 @@ __global__ void __launch_bounds__(256) k_gram2(const cplx_t<T>* __restrict__ A, 
         }
         __syncthreads();
     }
-    for (int t = tid; t < q * q; t += nthr) {
-        const int i = t / q, j = t - i * q;
-        const int tl = (i / 4) * side + (j / 4);
+    const int npair = q * q;
+    double2* out = partial + ((size_t)slot * gridDim.x + blockIdx.x) * 2 * npair;
+    for (int t = tid; t < 2 * npair; t += kGKThreads) {
+        const int w = t / npair, pr = t - w * npair;
+        int i = pr / q, j = pr - i * q;
+        bool conj_it = false;
+        if (w == 1 && !has_m && i / 4 > j / 4) {   // lower tile of A^H A: mirror of (j, i)
+            const int tmp = i;
+            i = j;
+            j = tmp;
+            conj_it = true;
+        }
+        const int ti = i / 4, tj = j / 4;
+        int tl;
+        if (w == 0) tl = ti * side + tj;
+        else if (has_m) tl = nk + ti * side + tj;
+        else tl = nk + ti * side - ti * (ti - 1) / 2 + (tj - ti);
         const C r = red[tl * 16 + (i % 4) * 4 + (j % 4)];
-        out[t] = make_double2(r.x, r.y);
+        out[t] = make_double2(r.x, conj_it ? -r.y : r.y);
     }
 }
 
-static __global__ void k_gram_final(const double2* __restrict__ partial, int nblk, int npair, double2* __restrict__ out) {
+// G[w][slot][pr] = sum over blocks of partial[slot][blk][w][pr]  (w = 0: K, 1: M)
+static __global__ void k_gram_final(const double2* __restrict__ partial, int nblk, int npair, int nslot,
+                                    double2* __restrict__ out) {
     const int slot = blockIdx.y;
-    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pr >= npair) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * npair) return;
+    const int w = t / npair, pr = t - w * npair;
     double re = 0, im = 0;
     for (int b = 0; b < nblk; ++b) {
-        const double2 v = partial[((size_t)slot * nblk + b) * npair + pr];
+        const double2 v = partial[((size_t)slot * nblk + b) * 2 * npair + t];
         re += v.x;
         im += v.y;
     }
-    out[(size_t)slot * npair + pr] = make_double2(re, im);
+    out[((size_t)w * nslot + slot) * npair + pr] = make_double2(re, im);
 }
 
 // Out[slot][j][e] = sum_i In[slot][i][e] Q[slot][i][j]  (Q row-major q x q, double2)

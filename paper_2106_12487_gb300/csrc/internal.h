@@ -35,7 +35,28 @@ struct Workspace {
     CGSys* sys = nullptr;     // cg_cap
 };
 
+constexpr int kDefaultPmax = 32;
+
+// Phases of a band solve timed by the tracer (bloch_plan_trace).
+enum TracePhase { TR_PCG32 = 0, TR_PCG64, TR_RES32, TR_RES64, TR_ORTHO, TR_PROJECT, TR_SPAN, TR_WALL, TR_NPHASE };
+
+// Event-pair timing of solver phases on the plan's stream; pairs are read
+// back after the solve's final synchronisation.
+struct Tracer {
+    bool on = false;
+    struct Pair {
+        int phase;
+        cudaEvent_t a, b;
+        bool ended;
+    };
+    std::vector<Pair> open;
+    std::vector<cudaEvent_t> pool;
+    double ms[TR_NPHASE] = {};
+    long long count[TR_NPHASE] = {};
+};
+
 struct TileCfg {
+    int pmax;   // cap on pencils per CTA the tiles were made with
     int Pz5;    // pencils per CTA, z passes with 5 buffers (strain / divergence)
     int Py2;    // y pass, 2 buffers
     int Pz2;    // z pass, 2 buffers (mass operator)
@@ -83,7 +104,9 @@ struct bloch_plan {
     bloch::TileCfg tile_f, tile_d;
     int nblk_max;
     bool fast = true;              // use the two-stage register FFT passes where the axis allows
-    int variant = 0;               // options.fft_variant
+    int variant = 0;               // options.fft_variant, or the autotuner's choice
+    bool tuned = false;            // bloch_plan_autotune has configured the passes
+    bloch::Tracer trace;           // phase timing (bloch_plan_trace)
     bloch_status pending = BLOCH_OK;   // failure inside a launcher, reported by the entry point
     // learned preconditioner (bloch_plan_set_preconditioner): parameters and
     // the per-wave-vector Z tables the CG kernels read while it is active
@@ -138,6 +161,31 @@ void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, 
                 double2* partial);
 
 int vec_blocks(const bloch_plan* pl, int nb);
+
+// Tracer: start / end a phase interval on the plan's stream (no-ops when off),
+// add host milliseconds to a phase, and read back completed pairs (the stream
+// must have been synchronised).  TraceScope brackets a C++ scope.
+int trace_begin(bloch_plan* pl, int phase);
+void trace_end(bloch_plan* pl, int idx);
+void trace_add(bloch_plan* pl, int phase, double ms);
+void trace_collect(bloch_plan* pl);
+void trace_release(bloch_plan* pl);
+struct TraceScope {
+    bloch_plan* pl;
+    int idx;
+    TraceScope(bloch_plan* p, int phase) : pl(p), idx(trace_begin(p, phase)) {}
+    ~TraceScope() { trace_end(pl, idx); }
+};
+
+// Destroy the instantiated PCG-loop graphs of the plan.
+void drop_pcg_graphs(bloch_plan* pl);
+// Select the FFT pass variant (0, 1, 2) and the pencils-per-CTA cap of the
+// shared-memory passes for both precisions; drops cached graphs.
+void configure_passes(bloch_plan* pl, int variant, int pmax);
+// Whether the fast (two-stage register) passes serve at least one pass of the
+// chain in this precision, and whether a shared-memory pass remains in it.
+bool has_fast_pass(const bloch_plan* pl, int precision);
+bool has_generic_pass(const bloch_plan* pl, int precision);
 
 // plain-form baseline (bloch_cufft.cu): Eq. (hatA) with cuFFT 3D transforms
 template <typename T>

@@ -62,6 +62,13 @@ def test_default_options_and_errors_without_gpu(libb):
     st = libb.bloch_plan_create(ctypes.byref(h), grid, L, ids, 1, C, rho0, None, None)
     assert st == 1 and b"density" in libb.bloch_last_error()
     assert libb.bloch_apply_K(None, 1, None, 0, None, None) == 1
+    for field, bad, msg in (("tile_pmax", 5, b"tile_pmax"), ("fft_variant", 3, b"fft_variant")):
+        ob = bloch.default_options(**{field: bad})
+        st = libb.bloch_plan_create(ctypes.byref(h), grid, L, ids, 1, C, rho, ctypes.byref(ob), None)
+        assert st == 1 and not h.value and msg in libb.bloch_last_error()
+    assert bloch.default_options().autotune == 0 and bloch.default_options().tile_pmax == 0
+    rep = bloch.TuneReport()
+    assert libb.bloch_plan_autotune(None, bloch.FP32, 4, ctypes.byref(rep)) == 1
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 18, 32])

@@ -162,3 +162,24 @@ def test_bands_nonconvergence_reported(B):
     plan = B.Plan.from_problem(p, precision=0, max_outer=1)
     got, _, st = plan.solve_bands([[0.5 * math.pi / 1e-3, 0, 0]], 4, allow_nonconv=True)
     assert st == 5 and np.all(got > 0)
+
+
+@pytest.mark.parametrize("prec,bar,opt", FORMS)
+def test_bands_nonuniform_density(B, prec, bar, opt):
+    """Two-phase-like density contrast (per-grain rho from 2000 to 9000
+    kg/m^3) with subspace iteration: the mass operator is a real five-pass FFT
+    operator and the projected M is a full Gram matrix, not a multiple of
+    U^H U.  The Lanczos solver rejects a non-uniform density."""
+    import dataclasses
+    p = synth.small_polycrystal((10, 8, 12), 6, 9, n_bands=5)
+    rho = np.random.default_rng(4).uniform(2000.0, 9000.0, p.G)
+    p = dataclasses.replace(p, rho=rho)
+    med = O.Medium.from_problem(p)
+    ks = np.array([[0.5, 0.0, 0.0], [0.3, 0.6, 0.9]]) * math.pi / 1e-3
+    want = O.solve_bands(med, ks, 5, 1e-12, 1e-12, method="lanczos").omega
+    plan = B.Plan.from_problem(p, precision=prec, method=1, **opt)
+    got, stats, _ = plan.solve_bands(ks, 5)
+    assert freq_err(got, want) < bar
+    with pytest.raises(B.BlochError) as e:
+        B.Plan.from_problem(p, precision=prec, method=0, **opt).solve_bands(ks, 5)
+    assert e.value.status == 7
