@@ -349,7 +349,8 @@ bloch_status bloch_plan_autotune(bloch_plan* plan, int32_t precision, int32_t sy
  * Phase tracer of bloch_solve_bands (no counterpart in the paper).  While
  * enabled, every solve records CUDA-event pairs on the plan's stream around
  * its phases and adds their durations (milliseconds) to the slots:
- *   0 PCG solves in FP32            1 PCG solves in FP64
+ *   0 PCG solves of the Algorithm 1 inverse step (and bloch_pcg calls)
+ *   1 PCG solves of the Lanczos steps
  *   2 FP32 residual applies (A_k u, M u, Rayleigh quotients, residual norms)
  *   3 FP64 residual applies (the FP64 check of the FP32 form, incl. conversion)
  *   4 Lanczos orthogonalisation (inner products, updates, normalisation)

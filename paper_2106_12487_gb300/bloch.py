@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
 class Trace(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_int64 * 8)]
 
-    PHASES = ("pcg_fp32", "pcg_fp64", "residual_fp32", "residual_fp64", "lanczos_orth", "projection",
+    PHASES = ("pcg_subspace", "pcg_lanczos", "residual_fp32", "residual_fp64", "lanczos_orth", "projection",
               "gpu_span", "wall")
 
     def as_dict(self):

@@ -398,11 +398,22 @@ struct Subspace {
         return BLOCH_OK;
     }
 
-    // Rayleigh quotients and residuals of slots [first, first+count)
+    // Rayleigh quotients and residuals of vectors [vo, vo+nvs) of slots
+    // [first, first+count) (nvs == q when count > 1), staged per vector;
+    // residual_finish turns the staged values into the slots' lam, err1, err2.
+    std::vector<double> stg_ukv, stg_umu, stg_kk, stg_r2;
     template <typename TK>
-    bloch_status residual_run(int first, int count, const cplx_t<TK>* Uk, const cplx_t<TK>* KUk,
-                              const cplx_t<TK>* MUk) {
-        const int nv = count * q;
+    bloch_status residual_part(int first, int count, int vo, int nvs, const cplx_t<TK>* Uk, const cplx_t<TK>* KUk,
+                               const cplx_t<TK>* MUk) {
+        const int nv = count * nvs;
+        if (nv == 0) return BLOCH_OK;
+        const size_t need = (size_t)B * q;
+        if (stg_ukv.size() < need) {
+            stg_ukv.assign(need, 0.0);
+            stg_umu.assign(need, 0.0);
+            stg_kk.assign(need, 0.0);
+            stg_r2.assign(need, 0.0);
+        }
         dim3 gr(dblk, nv);
         ++pl->launches;
         k_rq_dots<TK><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, n3, d_part);
@@ -410,7 +421,7 @@ struct Subspace {
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
                                              cudaMemcpyDeviceToHost, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        std::vector<double> ukv(nv), umu(nv), kk(nv), inv(nv);
+        std::vector<double> inv(nv);
         for (int v = 0; v < nv; ++v) {
             double a = 0, b = 0, c = 0;
             for (int j = 0; j < dblk; ++j) {
@@ -418,20 +429,30 @@ struct Subspace {
                 b += part[((size_t)v * dblk + j) * 3 + 1];
                 c += part[((size_t)v * dblk + j) * 3 + 2];
             }
-            ukv[v] = a;
-            umu[v] = b;
-            kk[v] = c;
+            const size_t at = (size_t)(first + v / nvs) * q + vo + v % nvs;
+            stg_ukv[at] = a;
+            stg_umu[at] = b;
+            stg_kk[at] = c;
             const double lam = (b > 0) ? a / b : 0.0;
             inv[v] = lam > 0 ? 1.0 / lam : 0.0;
         }
         BLOCH_CUDA_CHECK_RET(
             cudaMemcpyAsync(d_scal, inv.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, pl->stream));
         ++pl->launches;
-        k_residual<TK, T><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, d_scal, vec(R, first), n3, d_part);
+        k_residual<TK, T><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, d_scal, vec(R, first, vo), n3, d_part);
         std::vector<double> rp((size_t)nv * dblk);
         BLOCH_CUDA_CHECK_RET(
             cudaMemcpyAsync(rp.data(), d_part, sizeof(double) * rp.size(), cudaMemcpyDeviceToHost, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        for (int v = 0; v < nv; ++v) {
+            double r2 = 0;
+            for (int j = 0; j < dblk; ++j) r2 += rp[(size_t)v * dblk + j];
+            stg_r2[(size_t)(first + v / nvs) * q + vo + v % nvs] = r2;
+        }
+        return BLOCH_OK;
+    }
+
+    void residual_finish(int first, int count) {
         for (int s = 0; s < count; ++s) {
             Slot& sl = slots[first + s];
             sl.lam_prev = sl.lam;
@@ -439,13 +460,11 @@ struct Subspace {
             sl.unorm2.assign(q, 0.0);
             double e2 = 0;
             for (int i = 0; i < q; ++i) {
-                const int v = s * q + i;
-                double r2 = 0;
-                for (int j = 0; j < dblk; ++j) r2 += rp[(size_t)v * dblk + j];
-                const double lam = umu[v] > 0 ? ukv[v] / umu[v] : 0.0;
+                const size_t at = (size_t)(first + s) * q + i;
+                const double lam = stg_umu[at] > 0 ? stg_ukv[at] / stg_umu[at] : 0.0;
                 sl.lam[i] = lam;
-                sl.unorm2[i] = umu[v];
-                if (i < sl.n_eff && kk[v] > 0) e2 = std::max(e2, lam * std::sqrt(r2) / std::sqrt(kk[v]));
+                sl.unorm2[i] = stg_umu[at];
+                if (i < sl.n_eff && stg_kk[at] > 0) e2 = std::max(e2, lam * std::sqrt(stg_r2[at]) / std::sqrt(stg_kk[at]));
             }
             sl.err2_prev = sl.err2;
             sl.err2 = e2;
@@ -460,7 +479,6 @@ struct Subspace {
             sl.has_prev = true;
             st->k_applies += q;
         }
-        return BLOCH_OK;
     }
 
     bloch_status residual_step(int first, int count) {
@@ -474,22 +492,36 @@ struct Subspace {
                 TraceScope tr(pl, std::is_same<T, float>::value ? TR_RES32 : TR_RES64);
                 launch_K<T>(pl, (j - i) * q, vec(U, i), vec(KU, i), T(1));
                 if (!uniform) launch_M<T>(pl, (j - i) * q, vec(U, i), vec(MU, i), T(1));
-                if ((s = residual_run<T>(i, j - i, vec(U, i), vec(KU, i), uniform ? nullptr : vec(MU, i))) != BLOCH_OK)
+                if ((s = residual_part<T>(i, j - i, 0, q, vec(U, i), vec(KU, i), uniform ? nullptr : vec(MU, i))) !=
+                    BLOCH_OK)
                     return s;
+                residual_finish(i, j - i);
                 i = j;
             } else {
-                // FP64 refinement: residual of the FP32 block from an FP64 operator apply
+                // FP64 refinement: residuals and Rayleigh quotients of the wanted
+                // vectors from an FP64 operator apply (once per eigenpair when the
+                // check passes); the guard vectors of the block stay FP32
                 TraceScope tr(pl, TR_RES64);
-                const size_t ne = (size_t)q * n3;
+                const int nw = std::max(1, std::min(q, slots[i].n_eff));
+                const size_t ne = (size_t)nw * n3;
                 ++pl->launches;
                 k_convert<T, double><<<1024, 256, 0, pl->stream>>>(vec(U, i), U64, ne);
                 std::vector<double> kv((size_t)q * 3);
                 for (int v = 0; v < q; ++v)
                     for (int a = 0; a < 3; ++a) kv[(size_t)v * 3 + a] = slots[i].k[a];
-                if ((s = set_k<double>(pl, q, kv.data())) != BLOCH_OK) return s;
-                launch_K<double>(pl, q, U64, KU64, 1.0);
-                if (!uniform) launch_M<double>(pl, q, U64, MU64, 1.0);
-                if ((s = residual_run<double>(i, 1, U64, KU64, uniform ? nullptr : MU64)) != BLOCH_OK) return s;
+                if ((s = set_k<double>(pl, nw, kv.data())) != BLOCH_OK) return s;
+                launch_K<double>(pl, nw, U64, KU64, 1.0);
+                if (!uniform) launch_M<double>(pl, nw, U64, MU64, 1.0);
+                if ((s = residual_part<double>(i, 1, 0, nw, U64, KU64, uniform ? nullptr : MU64)) != BLOCH_OK) return s;
+                if (nw < q) {
+                    if ((s = set_k<T>(pl, q - nw, kv.data())) != BLOCH_OK) return s;
+                    launch_K<T>(pl, q - nw, vec(U, i, nw), vec(KU, i, nw), T(1));
+                    if (!uniform) launch_M<T>(pl, q - nw, vec(U, i, nw), vec(MU, i, nw), T(1));
+                    if ((s = residual_part<T>(i, 1, nw, q - nw, vec(U, i, nw), vec(KU, i, nw),
+                                              uniform ? nullptr : vec(MU, i, nw))) != BLOCH_OK)
+                        return s;
+                }
+                residual_finish(i, 1);
                 ++i;
             }
         }
@@ -1032,7 +1064,9 @@ struct Lanczos {
             if ((s = set_k<T>(pl, nact, kv.data())) != BLOCH_OK) return s;
             if ((s = lp_activate<T>(pl, nact, 1, 1)) != BLOCH_OK) return s;
             long long cg_it = 0;
+            pl->trace_pcg = TR_PCG_LZ;
             s = pcg_run<T>(pl, nact, Bc, Xc, rho_s, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
+            pl->trace_pcg = TR_PCG_SUB;
             lp_deactivate(pl);
             st->cg_iterations += cg_it;
             st->k_applies += cg_it;

@@ -33,7 +33,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 // unit holds its own copies of the template kernels).
 template <typename K>
 static cudaError_t smem_attr(K k) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = allow_max_dyn_smem(k);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
@@ -133,7 +133,7 @@ static void z_div(bloch_plan* pl, int nb, const float2* E, float2* out, const fl
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     k_fpass_z_div<float, RA, RB><<<gr, 128, (size_t)(N + 3 * N * P) * sizeof(float2), pl->stream>>>(
-        E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale);
+        E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale, nullptr, nullptr);
 }
 
 #define NOALLOC_SWITCH(N, FN, ...)                \

@@ -47,6 +47,9 @@ template <> const float* rtab_of<float>(const bloch_plan* pl) { return pl->d_rf;
 template <> const double* rtab_of<double>(const bloch_plan* pl) { return pl->d_rd; }
 
 // ------------------------------------------------------------ host helpers
+static bool fast_axis(int N);
+static bool fast_x(int N);
+
 static bool factor_ok(int n) {
     for (int p : {2, 3, 5, 7})
         while (n % p == 0) n /= p;
@@ -108,10 +111,9 @@ static TileCfg make_tiles(int Nx, int Ny, int Nz, int pmax) {
 
 template <typename T>
 static cudaError_t set_smem_attrs() {
-    const int mx = 227 * 1024;
     cudaError_t e;
-#define SETA(f)                                                                     \
-    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);   \
+#define SETA(f)                   \
+    e = allow_max_dyn_smem(f);    \
     if (e != cudaSuccess) return e;
     SETA(k_pass_z_strain<T>);
     SETA((k_pass_axis<T, +1, 1>));
@@ -169,7 +171,9 @@ bloch_status ensure_cg(bloch_plan* pl, int nb) {
     cudaStreamSynchronize(pl->stream);
     const size_t vec = (size_t)3 * pl->V * sizeof(cplx_t<T>);
     if (w.r) pl->device_bytes -= (size_t)w.cg_cap * (3 * vec + pl->nblk_max * (3 * sizeof(double) + sizeof(double2)) +
-                                                     sizeof(double2) + sizeof(CGSys));
+                                                     sizeof(double2) + sizeof(CGSys) + w.zblk * sizeof(double2));
+    cudaFree(w.partz);
+    w.partz = nullptr;
     cudaFree(w.r);
     cudaFree(w.p);
     cudaFree(w.Ap);
@@ -190,6 +194,11 @@ bloch_status ensure_cg(bloch_plan* pl, int nb) {
     BLOCH_CUDA_CHECK_RET(dmalloc(&w.part2, (size_t)nb * pl->nblk_max, &pl->device_bytes));
     BLOCH_CUDA_CHECK_RET(dmalloc(&w.dots, (size_t)nb, &pl->device_bytes));
     BLOCH_CUDA_CHECK_RET(dmalloc(&w.sys, (size_t)nb, &pl->device_bytes));
+    // the fused (p, Ap) partials need one slot per CTA of the z pass, for any fast variant later chosen
+    w.zblk = std::is_same<T, float>::value && fast_x(pl->Nz)
+                 ? (int)(((long long)pl->Nx * pl->Ny + 1) / 2)   // >= CTAs per system for every P >= 2
+                 : 0;
+    if (w.zblk) BLOCH_CUDA_CHECK_RET(dmalloc(&w.partz, (size_t)nb * w.zblk, &pl->device_bytes));
     w.cg_cap = nb;
     return BLOCH_OK;
 }
@@ -235,6 +244,15 @@ void configure_passes(bloch_plan* pl, int variant, int pmax) {
     pl->tile_d = make_tiles<double>(pl->Nx, pl->Ny, pl->Nz, pmax);
 }
 
+// CTAs per system of the fast z passes (P = 128 / RA pencils each), 0 when
+// the fast z passes do not serve this plan in FP32
+int fast_z_blocks(const bloch_plan* pl) {
+    if (!pl->fast || !fast_x(pl->Nz)) return 0;
+    const int RA = pl->Nz == 16 ? 4 : (pl->Nz == 128 ? 16 : 8);
+    const long long npen = (long long)pl->Nx * pl->Ny;
+    return (int)((npen + 128 / RA - 1) / (128 / RA));
+}
+
 bool has_fast_pass(const bloch_plan* pl, int precision) {
     if (fast_axis(pl->Ny)) return true;
     return precision == BLOCH_FP32 && (fast_x(pl->Nz) || fast_x(pl->Nx));
@@ -248,7 +266,7 @@ bool has_generic_pass(const bloch_plan* pl, int precision) {
 
 template <typename K>
 static void fast_attr(K k) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    allow_max_dyn_smem(k);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
@@ -311,7 +329,7 @@ static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
 }
 
 template <typename T, int RA, int RB>
-static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale) {
+static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale, const cplx_t<T>* dotp, double2* dpart) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
     constexpr int P = 128 / RA;
@@ -320,7 +338,7 @@ static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale) {
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
     k_fpass_z_div<T, RA, RB><<<gr, 128, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
-                                                              tw_of<T>(pl, 2), g, out_scale);
+                                                              tw_of<T>(pl, 2), g, out_scale, dotp, dpart);
 }
 
 template <typename T, int RA, int RB>
@@ -354,13 +372,15 @@ static void fast_x3(bloch_plan* pl, int nb) {
     }
 
 template <typename T>
-void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
+int launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale, const cplx_t<T>* dotp,
+             double2* dpart) {
     if (pl->variant == 2) {
         Workspace<T>& w = ws_of<T>(pl);
         if (!cufft_launch_K<T>(pl, nb, u, out, out_scale, w.E, w.qtab, ctab_of<T>(pl), geo_of<T>(pl)))
             pl->pending = set_error(BLOCH_ECUDA, "cuFFT plan or execution failed");
-        return;
+        return 0;
     }
+    int fused = 0;
     if (pl->fast) {
         Workspace<T>& w = ws_of<T>(pl);
         const Geo& g = geo_of<T>(pl);
@@ -416,8 +436,9 @@ void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_
         bool done5 = false;
         if constexpr (std::is_same<T, float>::value) {
             if (fz) {
-                BLOCH_FAST_SWITCH_Z(pl->Nz, fast_z5, pl, nb, out, out_scale);
+                BLOCH_FAST_SWITCH_Z(pl->Nz, fast_z5, pl, nb, out, out_scale, dpart ? dotp : nullptr, dpart);
                 done5 = true;
+                if (dpart && dotp) fused = fast_z_blocks(pl);
             }
         }
         if (!done5) {
@@ -425,9 +446,10 @@ void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_
             k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5,
                                                                 out_scale);
         }
-        return;
+        return fused;
     }
     launch_K_generic<T>(pl, nb, u, out, out_scale);
+    return 0;
 }
 
 template <typename T>
@@ -516,17 +538,32 @@ static void pcg_iteration(bloch_plan* pl, int nb, cplx_t<T>* x, double tol2, int
     Workspace<T>& w = ws_of<T>(pl);
     const Geo& g = geo_of<T>(pl);
     dim3 gr(nblk, nb);
-    launch_K<T>(pl, nb, w.p, w.Ap, T(1));
-    launch_dot<T>(pl, nb, w.p, w.Ap, 3 * pl->V, w.dots, w.part2);
+    // A p for the systems still active (the passes skip converged ones), with
+    // the (p, A p) partials fused into the last pass where it can
+    static_assert(sizeof(CGSys) % sizeof(int) == 0, "CGSys must be a whole number of ints");
+    Geo& gk = std::is_same<T, float>::value ? pl->geo_f : pl->geo_d;
+    gk.skip = &w.sys[0].active;
+    gk.skip_stride = (int)(sizeof(CGSys) / sizeof(int));
+    gk.skip_ncomp = 6;
+    const int zb = launch_K<T>(pl, nb, w.p, w.Ap, T(1), w.p, w.partz);
+    gk.skip = nullptr;
+    gk.skip_stride = 1;
+    gk.skip_ncomp = 1;
+    if (zb > 0) {
+        ++pl->launches;
+        k_dot_final<<<nb, 256, 0, pl->stream>>>(w.partz, zb, w.dots);
+    } else {
+        launch_dot<T>(pl, nb, w.p, w.Ap, 3 * pl->V, w.dots, w.part2);
+    }
     ++pl->launches;
     k_cg_scalars<<<nb, 32, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 1, tol2, pl->d_nactive);
     ++pl->launches;
-    k_cg_update<T><<<gr, 256, 0, pl->stream>>>(x, w.r, w.p, w.Ap, w.qtab, g, pl->pc, pl->psel, w.sys, w.part3);
+    k_cg_update<T><<<gr, 256, 0, pl->stream>>>(w.r, w.Ap, w.qtab, g, pl->pc, pl->psel, w.sys, w.part3);
     // (mode 1 above zeroed the active count that mode 2 accumulates)
     ++pl->launches;
     k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 2, tol2, pl->d_nactive);
     ++pl->launches;
-    k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, w.qtab, g, pl->pc, pl->psel, w.sys);
+    k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, x, w.qtab, g, pl->pc, pl->psel, w.sys);
     if (h) {
         ++pl->launches;
         k_cg_cond<<<1, 1, 0, pl->stream>>>(*h, pl->d_nactive, pl->d_iter, max_iter);
@@ -535,13 +572,14 @@ static void pcg_iteration(bloch_plan* pl, int nb, cplx_t<T>* x, double tol2, int
 
 template <typename T>
 static bloch_status pcg_graph(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double tol2, int nblk,
-                              int max_iter, cudaGraphExec_t* out) {
+                              int max_iter, cudaGraphExec_t* out, int* launches_per_iter) {
     Workspace<T>& w = ws_of<T>(pl);
     const int prec = std::is_same<T, float>::value ? 1 : 0;
     for (auto& e : pl->pcg_graphs)
         if (e.prec == prec && e.nb == nb && e.max_iter == max_iter && e.b == b && e.x == x && e.E == w.E &&
             e.r == w.r && e.ztab == pl->psel.ztab && e.zgroup == pl->psel.zgroup) {
             *out = e.exec;
+            *launches_per_iter = e.launches_per_iter;
             return BLOCH_OK;
         }
     if (pl->pcg_graphs.size() >= 16) {
@@ -581,6 +619,7 @@ static bloch_status pcg_graph(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t
     pl->stream = pl->cap_stream;
     pcg_iteration<T>(pl, nb, x, tol2, nblk, &h, max_iter);
     pl->stream = user;
+    const int per_iter = (int)(pl->launches - l0);
     pl->launches = l0;   // counted per executed iteration, not at capture
     cudaGraph_t captured;
     e = cudaStreamEndCapture(pl->cap_stream, &captured);
@@ -594,9 +633,10 @@ static bloch_status pcg_graph(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t
         cudaGraphDestroy(graph);
         return set_cuda_error(e, "cudaGraphInstantiate");
     }
-    bloch_plan::PcgGraph pg{prec, nb, max_iter, b, x, w.E, w.r, pl->psel.ztab, pl->psel.zgroup, graph, exec};
+    bloch_plan::PcgGraph pg{prec, nb, max_iter, per_iter, b, x, w.E, w.r, pl->psel.ztab, pl->psel.zgroup, graph, exec};
     pl->pcg_graphs.push_back(pg);
     *out = exec;
+    *launches_per_iter = per_iter;
     return BLOCH_OK;
 }
 
@@ -606,7 +646,7 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
                      void (*hook)(void*, int), void* hook_ctx) {
     bloch_status st = ensure_cg<T>(pl, nb);
     if (st != BLOCH_OK) return st;
-    TraceScope trace_pcg(pl, std::is_same<T, float>::value ? TR_PCG32 : TR_PCG64);
+    TraceScope trace_pcg(pl, pl->trace_pcg);
     Workspace<T>& w = ws_of<T>(pl);
     const Geo& g = geo_of<T>(pl);
     const int nblk = vec_blocks(pl, nb);
@@ -630,7 +670,8 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     const bool use_graph = pl->opt.cuda_graph != 0 && hook == nullptr && pl->variant != 2;
     if (use_graph && *pl->h_nactive > 0 && max_iter > 0) {
         cudaGraphExec_t exec;
-        bloch_status gs = pcg_graph<T>(pl, nb, b, x, tol2, nblk, max_iter, &exec);
+        int per_iter = 0;
+        bloch_status gs = pcg_graph<T>(pl, nb, b, x, tol2, nblk, max_iter, &exec, &per_iter);
         if (gs != BLOCH_OK) return gs;
         BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_iter, 0, sizeof(int), pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaGraphLaunch(exec, pl->stream));
@@ -638,28 +679,17 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
         BLOCH_CUDA_CHECK_RET(
             cudaMemcpyAsync(&iters_done, pl->d_iter, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        pl->launches += (unsigned long long)iters_done * (pl->fast ? 11 : 11);
+        pl->launches += (unsigned long long)iters_done * per_iter;
         it = iters_done;
     }
     while (!use_graph && *pl->h_nactive > 0 && it < max_iter) {
         tot += *pl->h_nactive;
-        launch_K<T>(pl, nb, w.p, w.Ap, T(1));
-        launch_dot<T>(pl, nb, w.p, w.Ap, 3 * pl->V, w.dots, w.part2);
-        ++pl->launches;
-        k_cg_scalars<<<nb, 32, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 1, tol2, pl->d_nactive);
-        ++pl->launches;
-        k_cg_update<T><<<gr, 256, 0, pl->stream>>>(x, w.r, w.p, w.Ap, w.qtab, g, pl->pc, pl->psel, w.sys, w.part3);
-        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_nactive, 0, sizeof(int), pl->stream));
-        ++pl->launches;
-        k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 2, tol2, pl->d_nactive);
+        pcg_iteration<T>(pl, nb, x, tol2, nblk, nullptr, max_iter);
         BLOCH_CUDA_CHECK_RET(
             cudaMemcpyAsync(pl->h_nactive, pl->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
         ++it;
         if (hook) hook(hook_ctx, it);
         BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        if (*pl->h_nactive == 0) break;
-        ++pl->launches;
-        k_cg_pupdate<T><<<gr, 256, 0, pl->stream>>>(w.r, w.p, w.qtab, g, pl->pc, pl->psel, w.sys);
     }
     BLOCH_CUDA_CHECK_RET(cudaGetLastError());
     if (pl->pending != BLOCH_OK) {
@@ -692,7 +722,7 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     template bloch_status ensure_ws<T>(bloch_plan*, int);                                                \
     template bloch_status ensure_cg<T>(bloch_plan*, int);                                                \
     template bloch_status set_k<T>(bloch_plan*, int, const double*);                                     \
-    template void launch_K<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                        \
+    template int launch_K<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T, const cplx_t<T>*, double2*); \
     template void launch_M<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                        \
     template void launch_precond<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                  \
     template void launch_dot<T>(bloch_plan*, int, const cplx_t<T>*, const cplx_t<T>*, long long,         \

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_fpass_y(const cplx_t<T>* in, cplx_t<T>*
     const unsigned npen = nx * (unsigned)g.Nz;
     const unsigned pi0 = blockIdx.x * PT;
     const unsigned plane = nx * (unsigned)g.Ny;
+    if (sys_idle(g, (int)blockIdx.y / g.skip_ncomp)) return;
     const size_t off = (size_t)blockIdx.y * g.V;
     const C* src = in + off;
     C* dst = out + off;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
     C* bufB = bufA + NP;      // NP
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const unsigned plane = (unsigned)g.Nx * (unsigned)g.Ny;
     const unsigned pi0 = blockIdx.x * P;
     const int np = (int)min((unsigned)P, plane - pi0);
@@ -215,10 +217,14 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
 //   out_x = q_x S11 + q_y S12 + q_z S13, out_y = q_x S12 + q_y S22 + q_z S23,
 //   out_z = q_x S13 + q_y S23 + q_z S33   (S = forward z transform of sigma).
 // Stress components stream into shared memory two ahead (cp.async).
+// With dotp != nullptr the CTA also forms sum conj(dotp) * out over its
+// pencils (the (p, A p) product of the PCG iteration, Algorithm 2) and writes
+// it to dpart[b * gridDim.x + blockIdx.x].
 template <typename T, int RA, int RB>
 __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restrict__ E, cplx_t<T>* __restrict__ out,
                                                         const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
-                                                        Geo g, T out_scale) {
+                                                        Geo g, T out_scale, const cplx_t<T>* __restrict__ dotp,
+                                                        double2* __restrict__ dpart) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int P = 128 / RA;
@@ -229,6 +235,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restr
     C* xb = stg + 2 * NP;     // NP exchange
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const unsigned plane = (unsigned)g.Nx * (unsigned)g.Ny;
     const unsigned pi0 = blockIdx.x * P;
     const int np = (int)min((unsigned)P, plane - pi0);
@@ -295,13 +302,40 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restr
             }
         }
     }
+    T dre = T(0), dim = T(0);
+    const C* pb = dotp ? dotp + (size_t)b * 3 * g.V : nullptr;
     if (p2 < np) {
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
             const size_t a = (size_t)(j2 + r * RA) * plane + pi0 + p2;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) ob[(size_t)i * g.V + a] = cscale(acc[i][r], out_scale);
+            for (int i = 0; i < 3; ++i) {
+                const C o = cscale(acc[i][r], out_scale);
+                ob[(size_t)i * g.V + a] = o;
+                if (pb) {
+                    const C pv = pb[(size_t)i * g.V + a];
+                    dre += pv.x * o.x + pv.y * o.y;
+                    dim += pv.x * o.y - pv.y * o.x;
+                }
+            }
         }
+    }
+    if (dotp) {   // block reduction (4 warps); deterministic order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dre += __shfl_xor_sync(0xffffffffu, dre, o);
+            dim += __shfl_xor_sync(0xffffffffu, dim, o);
+        }
+        __shared__ T red[2][4];
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = dre;
+            red[1][tid >> 5] = dim;
+        }
+        __syncthreads();
+        if (tid == 0)
+            dpart[(size_t)b * gridDim.x + blockIdx.x] =
+                make_double2((double)red[0][0] + red[0][1] + red[0][2] + red[0][3],
+                             (double)red[1][0] + red[1][1] + red[1][2] + red[1][3]);
     }
 }
 
@@ -325,6 +359,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const i
     C* xb = stg + 2 * P * LD; // P*LD exchange of the inverse transform
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const unsigned rows = (unsigned)g.Ny * (unsigned)g.Nz;
     const unsigned r0 = blockIdx.x * P;
     const int nr = (int)min((unsigned)P, rows - r0);

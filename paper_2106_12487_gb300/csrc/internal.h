@@ -33,12 +33,14 @@ struct Workspace {
     double2* part2 = nullptr; // cg_cap x nblk_max
     double2* dots = nullptr;  // cg_cap
     CGSys* sys = nullptr;     // cg_cap
+    double2* partz = nullptr; // cg_cap x zblk: (p, Ap) partials of the fused z-divergence pass
+    int zblk = 0;
 };
 
 constexpr int kDefaultPmax = 32;
 
 // Phases of a band solve timed by the tracer (bloch_plan_trace).
-enum TracePhase { TR_PCG32 = 0, TR_PCG64, TR_RES32, TR_RES64, TR_ORTHO, TR_PROJECT, TR_SPAN, TR_WALL, TR_NPHASE };
+enum TracePhase { TR_PCG_SUB = 0, TR_PCG_LZ, TR_RES32, TR_RES64, TR_ORTHO, TR_PROJECT, TR_SPAN, TR_WALL, TR_NPHASE };
 
 // Event-pair timing of solver phases on the plan's stream; pairs are read
 // back after the solve's final synchronisation.
@@ -107,6 +109,7 @@ struct bloch_plan {
     int variant = 0;               // options.fft_variant, or the autotuner's choice
     bool tuned = false;            // bloch_plan_autotune has configured the passes
     bloch::Tracer trace;           // phase timing (bloch_plan_trace)
+    int trace_pcg = 0;             // phase PCG solves are traced under (TR_PCG_SUB or TR_PCG_LZ)
     bloch_status pending = BLOCH_OK;   // failure inside a launcher, reported by the entry point
     // learned preconditioner (bloch_plan_set_preconditioner): parameters and
     // the per-wave-vector Z tables the CG kernels read while it is active
@@ -116,7 +119,7 @@ struct bloch_plan {
     size_t zcap = 0;
     // instantiated PCG-loop graphs (conditional WHILE node), keyed by their bound pointers
     struct PcgGraph {
-        int prec, nb, max_iter;
+        int prec, nb, max_iter, launches_per_iter;
         const void *b, *x, *E, *r, *ztab;
         int zgroup;
         cudaGraph_t graph;
@@ -145,7 +148,12 @@ template <typename T> bloch_status ensure_cg(bloch_plan* pl, int nb);
 // Upload nb wave vectors (host, rad/m) and build the scaled q tables.
 template <typename T> bloch_status set_k(bloch_plan* pl, int nb, const double* k_host);
 // Scaled stiffness operator on nb systems whose q tables are set: out = out_scale * A~ u.
-template <typename T> void launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale);
+// With dotp / dpart, a pass that can also forms per-CTA partials of
+// sum conj(dotp) * out per system in dpart and the call returns the number of
+// partials per system; it returns 0 when no pass did (the caller forms the dot).
+template <typename T>
+int launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale,
+             const cplx_t<T>* dotp = nullptr, double2* dpart = nullptr);
 // Scaled mass operator: out = out_scale * M~ u (M~ = M / rho_ref).  out may alias u.
 template <typename T> void launch_M(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale);
 // Scaled preconditioner on nb systems: z = out_scale * P~^-1 r.
@@ -185,6 +193,8 @@ void configure_passes(bloch_plan* pl, int variant, int pmax);
 // Whether the fast (two-stage register) passes serve at least one pass of the
 // chain in this precision, and whether a shared-memory pass remains in it.
 bool has_fast_pass(const bloch_plan* pl, int precision);
+// CTAs per system of the fast FP32 z passes (0 when they do not serve the plan).
+int fast_z_blocks(const bloch_plan* pl);
 bool has_generic_pass(const bloch_plan* pl, int precision);
 
 // plain-form baseline (bloch_cufft.cu): Eq. (hatA) with cuFFT 3D transforms

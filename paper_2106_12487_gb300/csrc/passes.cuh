@@ -24,7 +24,17 @@ struct Geo {
     int Nx, Ny, Nz;
     long long V;
     AxisPlan ax[3];
+    // PCG convergence mask: system b is skipped when skip[b * skip_stride] == 0
+    // (nullptr: every system runs); blockIdx.y / skip_ncomp is the system of a
+    // per-component pass.
+    const int* skip = nullptr;
+    int skip_stride = 1;
+    int skip_ncomp = 1;
 };
+
+__device__ __forceinline__ bool sys_idle(const Geo& g, int b) {
+    return g.skip != nullptr && g.skip[(size_t)b * g.skip_stride] == 0;
+}
 
 __device__ __forceinline__ int pad_even(int n) { return (n + 1) & ~1; }
 
@@ -44,6 +54,7 @@ __global__ void __launch_bounds__(256) k_pass_z_strain(const cplx_t<T>* __restri
     C* sB = sA + NP;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const long long plane = (long long)g.Nx * g.Ny;
     const long long pi0 = (long long)blockIdx.x * P;
     const int np = (int)min((long long)P, plane - pi0);
@@ -106,6 +117,7 @@ __global__ void __launch_bounds__(256) k_pass_axis(const cplx_t<T>* in, cplx_t<T
     const long long npen = AXIS == 1 ? (long long)g.Nx * g.Nz : (long long)g.Nx * g.Ny;
     const long long pi0 = (long long)blockIdx.x * P;
     const int np = (int)min((long long)P, npen - pi0);
+    if (sys_idle(g, (int)blockIdx.y / g.skip_ncomp)) return;
     const size_t off = (size_t)blockIdx.y * g.V;
     const C* src = in + off;
     C* dst = out + off;
@@ -154,6 +166,7 @@ __global__ void __launch_bounds__(256) k_pass_x_stress(cplx_t<T>* E, const int32
     C* s0 = tw + pad_even(N);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const long long rows = (long long)g.Ny * g.Nz;
     const long long r0 = (long long)blockIdx.x * P;
     const int nr = (int)min((long long)P, rows - r0);
@@ -226,6 +239,7 @@ __global__ void __launch_bounds__(256) k_pass_z_div(const cplx_t<T>* __restrict_
     C* sB = sA + NP;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const long long plane = (long long)g.Nx * g.Ny;
     const long long pi0 = (long long)blockIdx.x * P;
     const int np = (int)min((long long)P, plane - pi0);
@@ -285,6 +299,7 @@ __global__ void __launch_bounds__(256) k_pass_x_rho(cplx_t<T>* W, const int32_t*
     C* s0 = tw + pad_even(N);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int b = blockIdx.y;
+    if (sys_idle(g, b)) return;
     const long long rows = (long long)g.Ny * g.Nz;
     const long long r0 = (long long)blockIdx.x * P;
     const int nr = (int)min((long long)P, rows - r0);

@@ -27,6 +27,7 @@ struct CGSys {
     double beta;
     int active;
     int iters;
+    int upd;         // took a step this iteration (x += alpha p is still to be applied)
 };
 
 // qtab[b][.] = ((xi + k_b) * qscale) for the x, y and z axes.
@@ -234,9 +235,10 @@ __global__ void k_cg_init(const cplx_t<T>* bvec, const cplx_t<T>* Ax, cplx_t<T>*
     }
 }
 
-// x += alpha p; r -= alpha Ap; partials (r, P^-1 r), (r, r)
+// r -= alpha Ap; partials (r, P^-1 r), (r, r).  The matching x += alpha p is
+// applied by k_cg_pupdate, which reads p anyway (one pass less over x here).
 template <typename T>
-__global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, const cplx_t<T>* Ap,
+__global__ void k_cg_update(cplx_t<T>* __restrict__ r, const cplx_t<T>* __restrict__ Ap,
                             const T* __restrict__ qtab, Geo g, PrecondCoef pc, PrecondSel ps, const CGSys* sys,
                             double* partial) {
     using C = cplx_t<T>;
@@ -252,9 +254,6 @@ __global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, cons
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const size_t i = off + c * g.V + v;
-                const C pv = p[i];
-                const C xv = x[i];
-                x[i] = mk(fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
                 const C av = Ap[i];
                 const C ro = r[i];
                 rv[c] = mk(fma(-alpha, av.x, ro.x), fma(-alpha, av.y, ro.y));
@@ -279,28 +278,38 @@ __global__ void k_cg_update(cplx_t<T>* x, cplx_t<T>* r, const cplx_t<T>* p, cons
     }
 }
 
-// p = P^-1 r + beta p for active systems
+// For systems that took a step: x += alpha p (old p); then, if still active,
+// p = P^-1 r + beta p.
 template <typename T>
-__global__ void k_cg_pupdate(const cplx_t<T>* r, cplx_t<T>* p, const T* __restrict__ qtab, Geo g, PrecondCoef pc,
-                             PrecondSel ps, const CGSys* sys) {
+__global__ void k_cg_pupdate(const cplx_t<T>* __restrict__ r, cplx_t<T>* __restrict__ p, cplx_t<T>* __restrict__ x,
+                             const T* __restrict__ qtab, Geo g, PrecondCoef pc, PrecondSel ps, const CGSys* sys) {
     using C = cplx_t<T>;
     const int b = blockIdx.y;
-    if (!sys[b].active) return;
+    if (!sys[b].upd) return;
+    const bool act = sys[b].active != 0;
     const size_t off = (size_t)b * 3 * g.V;
     const T* qb = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
+    const T alpha = T(sys[b].alpha);
     const T beta = T(sys[b].beta);
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
-        C rv[3], zv[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) rv[c] = r[off + c * g.V + v];
-        T ax, ay, az;
-        voxel_q(qb, g, v, ax, ay, az);
-        pre_apply<T>(ps, pc, b, v, g.V, ax, ay, az, rv, zv);
+        C pv[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t i = off + c * g.V + v;
-            const C pv = p[i];
-            p[i] = mk(fma(beta, pv.x, zv[c].x), fma(beta, pv.y, zv[c].y));
+            pv[c] = p[i];
+            const C xv = x[i];
+            x[i] = mk(fma(alpha, pv[c].x, xv.x), fma(alpha, pv[c].y, xv.y));
+        }
+        if (act) {
+            C rv[3], zv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rv[c] = r[off + c * g.V + v];
+            T ax, ay, az;
+            voxel_q(qb, g, v, ax, ay, az);
+            pre_apply<T>(ps, pc, b, v, g.V, ax, ay, az, rv, zv);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                p[off + c * g.V + v] = mk(fma(beta, pv[c].x, zv[c].x), fma(beta, pv[c].y, zv[c].y));
         }
     }
 }
@@ -329,12 +338,14 @@ static __global__ void k_cg_scalars(const double* partial3, const double2* dots,
         s.rr = acc[1];
         s.bb = acc[2];
         s.iters = 0;
+        s.upd = 0;
         s.active = (s.rr > tol2 * s.bb) ? 1 : 0;
         if (s.active) atomicAdd(n_active, 1);
     } else if (mode == 1) {
         if (b == 0) *n_active = 0;   // recount in mode 2 (kernels of one stream are ordered)
         s.pAp = dots[b].x;
         s.alpha = (s.active && s.pAp > 0.0) ? s.rz / s.pAp : 0.0;
+        s.upd = s.active;
     } else {
         if (!s.active) return;
         s.iters += 1;

@@ -97,8 +97,8 @@ def test_solve_with_autotune_matches_untuned(B):
 @pytest.mark.parametrize("prec,method", [(1, 0), (1, 1), (0, 1)])
 def test_trace_phases_are_consistent(B, prec, method):
     """The phase tracer: traced phases fit inside the GPU span, the span
-    inside the host wall time; PCG is recorded; the FP64 check appears only
-    in the FP32 form; tracing off records nothing."""
+    inside the host wall time; PCG is recorded under the solver that ran it;
+    FP32 residuals appear only in the FP32 form; tracing off records nothing."""
     p = synth.small_polycrystal((16, 16, 16), 6, 8, n_bands=4)
     ks = np.array([[0.4, 0.1, 0.0], [0.2, 0.3, 0.6]]) * math.pi / 1e-3
     opt = dict(tol_lin=1e-3, tol_eig=1e-6) if prec == 1 else dict(tol_lin=1e-10, tol_eig=1e-10)
@@ -106,13 +106,14 @@ def test_trace_phases_are_consistent(B, prec, method):
     plan.trace(True)
     plan.solve_bands(ks, 4)
     tr = plan.trace(False)
-    parts = sum(tr[k]["ms"] for k in ("pcg_fp32", "pcg_fp64", "residual_fp32", "residual_fp64",
+    parts = sum(tr[k]["ms"] for k in ("pcg_subspace", "pcg_lanczos", "residual_fp32", "residual_fp64",
                                       "lanczos_orth", "projection"))
     assert 0 < parts <= tr["gpu_span"]["ms"] * 1.001
     assert tr["gpu_span"]["ms"] <= tr["wall"]["ms"] * 1.001
     assert tr["gpu_span"]["count"] == 1 and tr["wall"]["count"] == 1
-    assert tr["pcg_fp32" if prec == 1 else "pcg_fp64"]["count"] > 0
+    assert (tr["pcg_lanczos"]["count"] > 0) == (method == 0)
     assert (tr["lanczos_orth"]["count"] > 0) == (method == 0)
+    assert tr["pcg_subspace"]["count"] > 0 or method == 0
     if prec == 0:
         assert tr["residual_fp64"]["count"] > 0 or method == 0
         assert tr["residual_fp32"]["count"] == 0
