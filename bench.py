@@ -29,12 +29,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0}   # algorithmic bytes per voxel, 5-pass chain
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the five passes) per system of the
-# FP32 fast-pass K-apply at 128^3, from one ncu capture of a 4-system launch (1845.7 MB read +
-# 1557.1 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
+# FP32 fast-pass K-apply at 128^3, from one ncu capture of a 4-system launch (1845.6 MB read +
+# 1562.1 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
 # to `sources_sha256` (fpasses.cuh, fft.cuh, common.cuh in that order); otherwise traffic is null.
 KAPPLY_TRAFFIC = {"grid": (128, 128, 128), "precision": 1, "fft_variant": 0,
-                  "bytes_per_system": 3402.8e6 / 4,
-                  "sources_sha256": "01a6c050ffe475c73b032ff292573d0ae0d32964dc736a42abf8b03806ace149"}
+                  "bytes_per_system": 3407.7e6 / 4,
+                  "sources_sha256": "6936885bf7a0de125b594791eddc73d59ed166e5b8ce26d9b3a219aaed132cff"}
 
 
 def parse():
