@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
     ap.add_argument("--fft-variant", type=int, default=0, choices=[0, 1, 2],
                     help="0: two-stage register FFT passes, 1: shared-memory Stockham passes, 2: cuFFT baseline")
+    ap.add_argument("--precond", default="green", choices=["green", "learned"],
+                    help="green: the Green operator P^-1 (the paper); learned: train the learned Fourier-space "
+                         "preconditioner first (untimed, reported under 'precond') and solve with it")
+    ap.add_argument("--lp-cells", type=int, default=16, help="training cells (64^3 Zener family) for --precond learned")
+    ap.add_argument("--lp-steps", type=int, default=500, help="Adam steps for --precond learned")
     ap.add_argument("--no-trace", action="store_true",
                     help="skip the extra traced (untimed) step that reports the solver's phase breakdown")
     ap.add_argument("--cuda-graph", type=int, default=1, choices=[0, 1],
@@ -265,6 +270,28 @@ def kapply_roofline(plan, p, prec, nb=0, fft_variant=0):
             "ms_per_launch": t_apply * 1000.0, "alg_bytes_per_launch": alg_bytes}
 
 
+def train_learned(args):
+    """Learned Fourier-space preconditioner: record CG pairs on 64^3 cells of
+    the Zener family (two wave vectors each), then full-batch Adam.  Untimed;
+    returns the network and what the JSON line reports about it."""
+    import torch
+    from paper_2106_12487_gb300 import bloch, synth
+    t0 = time.perf_counter()
+    lp = bloch.LearnedPrecond(seed=7)
+    for i in range(args.lp_cells):
+        c = synth.zener_cell((64, 64, 64), i)
+        pl = bloch.Plan.from_problem(c, precision=bloch.FP32)
+        pick = np.random.default_rng(31 + i).choice(len(c.k_list) - 1, 2, replace=False) + 1
+        lp.collect(pl, c.k_list[pick], n_rhs=2, n_iters=12, seed=31 + i)
+        pl.close()
+    L0, _ = lp.loss_grad()
+    lp.train(args.lp_steps, lr=3e-3)
+    L1, _ = lp.loss_grad()
+    torch.cuda.synchronize()
+    return lp, {"kind": "learned", "train_cells": args.lp_cells, "cell": [64, 64, 64], "adam_steps": args.lp_steps,
+                "loss": [L0, L1], "train_s": time.perf_counter() - t0}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2106_12487_gb300 import bloch, synth
@@ -289,6 +316,10 @@ def run_ours(args, ws, rank, local):
                    max_outer=args.max_outer, fft_variant=2 if args.fft_variant == 0 else args.fft_variant,
                    cuda_graph=args.cuda_graph)
     plan = bloch.Plan.from_problem(p, **opt)
+    lp, lp_info = None, {"kind": "green"}
+    if args.precond == "learned":
+        lp, lp_info = train_learned(args)
+        bloch.set_preconditioner(plan, lp)
     if args.kapply_only:
         roof = kapply_roofline(plan, p, prec, args.kapply_nb, opt["fft_variant"])
         if rank == 0:
@@ -346,6 +377,8 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plan2 = bloch.Plan.from_problem(p, **opt)
+        if lp is not None:
+            bloch.set_preconditioner(plan2, lp)
         om, _, _ = plan2.solve_bands(kbatch(args.warmup), p.n_bands, allow_nonconv=True)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -378,7 +411,7 @@ def run_ours(args, ws, rank, local):
                            "outer_iterations": sum(s["outer_iterations"] for s in stats_all),
                            "max_rel_residual": max(s["max_rel_residual"] for s in stats_all),
                            "k_applies_per_eigenpair": kap / (args.steps * kps * p.n_bands)},
-                "phases_ms": phases}
+                "phases_ms": phases, "precond": lp_info}
         print(json.dumps(line), flush=True)
     plan.close()
 

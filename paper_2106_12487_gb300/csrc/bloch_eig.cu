@@ -742,11 +742,10 @@ struct Subspace {
             }
             BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_Q, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice,
                                                  pl->stream));
-            dim3 gb((unsigned)std::min<long long>((n3 + 127) / 128, 8192), nact);
             {
                 TraceScope tr(pl, TR_PROJECT);
                 ++pl->launches;
-                k_basis<T><<<gb, 128, 0, pl->stream>>>(Ub, U, d_Q, q, n3);
+                launch_basis<T>(pl->stream, nact, Ub, U, d_Q, q, n3);
             }
             BLOCH_CUDA_CHECK_RET(cudaGetLastError());
             if ((s = residual_step(0, nact)) != BLOCH_OK) return s;
@@ -970,9 +969,8 @@ struct Lanczos {
             err = set_cuda_error(e, "Lanczos restart upload");
             return true;
         }
-        dim3 gb((unsigned)std::min<long long>((n3 + 127) / 128, 8192), 1);
         ++pl->launches;
-        k_basis<T><<<gb, 128, 0, pl->stream>>>(vb(s, 0), Tmp, d_Q, m, n3);
+        launch_basis<T>(pl->stream, 1, vb(s, 0), Tmp, d_Q, m, n3);
         if (done) {
             const double lam_scale = pl->Kscale / pl->rho_ref;
             double* om = omega_out + (size_t)sl.kidx * n_bands;
@@ -1165,7 +1163,8 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     S.n_bands = n_bands;
     S.m = pl->opt.ncv > 0 ? pl->opt.ncv : std::max(2 * n_bands + 1, 20);
     S.m = (int)std::min<long long>(S.m, 3 * pl->V - 4);
-    if (S.m > 63) return set_error(BLOCH_EUNSUPPORTED, "Lanczos basis above 63 vectors is not supported");
+    if (S.m > kBasisQMax - 1)
+        return set_error(BLOCH_EUNSUPPORTED, "Lanczos basis above 63 vectors is not supported");
     if (S.m < n_bands + 1) return set_error(BLOCH_EINVAL, "Lanczos basis too small for the requested bands");
     S.rho_s = pl->rho_uniform_scaled;
     S.tol_eig = tol_override > 0 ? tol_override : pl->opt.tol_eig;

@@ -210,6 +210,7 @@ bloch_status set_k(bloch_plan* pl, int nb, const double* k_host) {
     for (int i = 0; i < 3 * nb; ++i)
         if (!std::isfinite(k_host[i])) return set_error(BLOCH_ENONFINITE, "wave vector has a non-finite component");
     Workspace<T>& w = ws_of<T>(pl);
+    pl->k_host.assign(k_host, k_host + 3 * (size_t)nb);
     BLOCH_CUDA_CHECK_RET(
         cudaMemcpyAsync(w.kvec, k_host, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice, pl->stream));
     const int S = pl->Nx + pl->Ny + pl->Nz;
@@ -1007,6 +1008,8 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         gp->Ny = pl->Ny;
         gp->Nz = pl->Nz;
         gp->V = V;
+        gp->dx = make_fastdiv((unsigned)pl->Nx);
+        gp->dy = make_fastdiv((unsigned)pl->Ny);
     }
     for (int a = 0; a < 3; ++a) {
         pl->geo_f.ax[a] = make_axis(grid[a], 4);   // radices up to 16 in FP32

@@ -3,6 +3,8 @@
 // K = conj(U^T) Kn, M = conj(U^T) Mn, U <- U Q, err2).
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "vec.cuh"
 
@@ -186,10 +188,19 @@ static __global__ void k_gram_final(const double2* __restrict__ partial, int nbl
     out[((size_t)w * nslot + slot) * npair + pr] = make_double2(re, im);
 }
 
-// Out[slot][j][e] = sum_i In[slot][i][e] Q[slot][i][j]  (Q row-major q x q, double2)
+// Out[slot][j][e] = sum_i In[slot][i][e] Q[slot][i][j]  (Q row-major q x q, double2).
+//
+// k_basis_reg (q <= 32): each thread loads the q inputs of its element into
+// registers at once (q loads in flight) and forms the outputs one by one from
+// Q in shared memory (broadcast reads).
+// k_basis_cols (q <= 63, Lanczos restarts with a large basis): output columns
+// in chunks of 32 (blockIdx.y = slot * nchunk + chunk), the q x 32 slice of Q
+// in dynamic shared memory, 32 accumulators per thread.
+constexpr int kBasisQMax = 64;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_basis(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
-                                               const double2* __restrict__ Q, int q, long long n_per) {
+__global__ void __launch_bounds__(128) k_basis_reg(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
+                                                   const double2* __restrict__ Q, int q, long long n_per) {
     using C = cplx_t<T>;
     __shared__ C sQ[kQMax * kQMax];
     const int slot = blockIdx.y;
@@ -217,6 +228,62 @@ __global__ void __launch_bounds__(128) k_basis(const cplx_t<T>* __restrict__ In,
                 }
             ob[(size_t)j * n_per + e] = mk(re, im);
         }
+    }
+}
+
+constexpr int kBasisJC = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
+                                                    const double2* __restrict__ Q, int q, long long n_per) {
+    using C = cplx_t<T>;
+    constexpr int JC = kBasisJC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sQ = reinterpret_cast<C*>(smem_raw);   // sQ[i * JC + jj] = Q[i][j0 + jj]
+    const int nch = (q + JC - 1) / JC;
+    const int slot = blockIdx.y / nch;
+    const int j0 = (blockIdx.y - slot * nch) * JC;
+    const int ncol = min(JC, q - j0);
+    for (int t = threadIdx.x; t < q * JC; t += blockDim.x) {
+        const int i = t / JC, jj = t - i * JC;
+        const double2 v = jj < ncol ? Q[(size_t)slot * q * q + (size_t)i * q + j0 + jj] : make_double2(0.0, 0.0);
+        sQ[t] = mk(T(v.x), T(v.y));
+    }
+    __syncthreads();
+    const C* ib = In + (size_t)slot * q * n_per;
+    C* ob = Out + (size_t)slot * q * n_per;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
+         e += (long long)gridDim.x * blockDim.x) {
+        T re[JC], im[JC];
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj) re[jj] = im[jj] = T(0);
+#pragma unroll 2
+        for (int i = 0; i < q; ++i) {
+            const C v = ib[(size_t)i * n_per + e];
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const C w = sQ[i * JC + jj];
+                re[jj] = fma(v.x, w.x, fma(-v.y, w.y, re[jj]));
+                im[jj] = fma(v.x, w.y, fma(v.y, w.x, im[jj]));
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj)
+            if (jj < ncol) ob[(size_t)(j0 + jj) * n_per + e] = mk(re[jj], im[jj]);
+    }
+}
+
+// Basis rotation of nslot slots (q < kBasisQMax).
+template <typename T>
+void launch_basis(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* Out, const double2* Q, int q,
+                  long long n_per) {
+    const unsigned gx = (unsigned)std::min<long long>((n_per + 127) / 128, 8192);
+    if (q <= kQMax) {
+        k_basis_reg<T><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, q, n_per);
+    } else {
+        const int nch = (q + kBasisJC - 1) / kBasisJC;
+        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)q * kBasisJC * sizeof(cplx_t<T>), st>>>(In, Out, Q,
+                                                                                                     q, n_per);
     }
 }
 

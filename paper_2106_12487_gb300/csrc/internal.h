@@ -117,6 +117,8 @@ struct bloch_plan {
     bloch::PrecondSel psel{nullptr, 1};
     float* d_ztab = nullptr;
     size_t zcap = 0;
+    std::vector<double> zkey;      // what the current tables were built for (lp_activate)
+    std::vector<double> k_host;    // wave vectors (rad/m) of the systems of the last set_k
     // instantiated PCG-loop graphs (conditional WHILE node), keyed by their bound pointers
     struct PcgGraph {
         int prec, nb, max_iter, launches_per_iter;

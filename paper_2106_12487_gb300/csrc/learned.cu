@@ -11,6 +11,8 @@
 // normalised by the number of recorded iterates.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -32,6 +34,7 @@ struct bloch_lp {
     float* d_v = nullptr;
     double* d_grad = nullptr;   // kLPN gradient + loss
     int adam_t = 0;
+    unsigned long long version = 0;   // process-unique, renewed whenever the parameters change
     struct Block {
         int grid[3];
         long long V;
@@ -47,6 +50,13 @@ struct bloch_lp {
 };
 
 namespace bloch {
+
+// Versions of learned-preconditioner parameters, unique within the process,
+// so cached Z tables are never matched to another network's parameters.
+static unsigned long long next_lp_version() {
+    static std::atomic<unsigned long long> counter{0};
+    return ++counter;
+}
 
 static unsigned long long lp_hash(unsigned long long x) {
     x ^= x >> 33;
@@ -352,6 +362,7 @@ bloch_status lp_activate(bloch_plan* pl, int ntab, int qstride_sys, int zgroup) 
     }
     const size_t need = (size_t)ntab * pl->V * 6;
     if (need > pl->zcap) {
+        pl->zkey.clear();
         cudaFree(pl->d_ztab);
         pl->d_ztab = nullptr;
         pl->zcap = 0;
@@ -359,11 +370,23 @@ bloch_status lp_activate(bloch_plan* pl, int ntab, int qstride_sys, int zgroup) 
         if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (learned preconditioner tables)");
         pl->zcap = need;
     }
-    dim3 gr((unsigned)std::min<long long>((pl->V + 255) / 256, 1024), ntab);
-    ++pl->launches;
-    k_lp_table<T><<<gr, 256, 0, pl->stream>>>(pl->lp->d_prm, ws_of<T>(pl).qtab, qstride_sys, geo_of<T>(pl), pl->pc,
-                                              lp_snorm(pl), pl->d_ztab);
-    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    // the tables depend on the network, the precision and the wave vector of
+    // every qstride_sys-th system: rebuild only when one of them changed
+    std::vector<double> key;
+    key.reserve((size_t)3 * ntab + 4);
+    key.push_back((double)sizeof(T));
+    key.push_back((double)ntab);
+    key.push_back((double)pl->lp->version);
+    for (int t = 0; t < ntab; ++t)
+        for (int a = 0; a < 3; ++a) key.push_back(pl->k_host[(size_t)t * qstride_sys * 3 + a]);
+    if (key != pl->zkey) {
+        dim3 gr((unsigned)std::min<long long>((pl->V + 255) / 256, 1024), ntab);
+        ++pl->launches;
+        k_lp_table<T><<<gr, 256, 0, pl->stream>>>(pl->lp->d_prm, ws_of<T>(pl).qtab, qstride_sys, geo_of<T>(pl),
+                                                  pl->pc, lp_snorm(pl), pl->d_ztab);
+        BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        pl->zkey = key;
+    }
     pl->psel = PrecondSel{pl->d_ztab, zgroup};
     return BLOCH_OK;
 }
@@ -404,6 +427,7 @@ bloch_status bloch_lp_create(bloch_lp** out, uint64_t seed) {
     if (!out) return set_error(BLOCH_EINVAL, "out is NULL");
     *out = nullptr;
     bloch_lp* lp = new bloch_lp();
+    lp->version = next_lp_version();
     std::vector<float> h(kLPN, 0.f);
     const int nh = kLPH * kLPF + kLPH + kLPH * kLPH + kLPH;
     for (int i = 0; i < nh; ++i) {
@@ -448,6 +472,7 @@ bloch_status bloch_lp_params(bloch_lp* lp, double* get, const double* set) {
     if (set) {
         for (int i = 0; i < kLPN; ++i) h[i] = (float)set[i];
         BLOCH_CUDA_CHECK_RET(cudaMemcpy(lp->d_prm, h.data(), kLPN * sizeof(float), cudaMemcpyHostToDevice));
+        lp->version = bloch::next_lp_version();
     }
     if (get) {
         BLOCH_CUDA_CHECK_RET(cudaMemcpy(h.data(), lp->d_prm, kLPN * sizeof(float), cudaMemcpyDeviceToHost));
@@ -537,6 +562,8 @@ bloch_status bloch_lp_loss_grad(bloch_lp* lp, double* loss, double* grad) {
         g.Ny = b.grid[1];
         g.Nz = b.grid[2];
         g.V = b.V;
+        g.dx = make_fastdiv((unsigned)g.Nx);
+        g.dy = make_fastdiv((unsigned)g.Ny);
         const int nblk = (int)std::min<long long>((b.V + kLPT - 1) / kLPT, 608);
         k_lp_grad<<<nblk, kLPT, smem>>>(lp->d_prm, b.d_mom, b.d_q, g, b.pc, b.snorm, ws, lp->d_grad);
     }
@@ -562,6 +589,7 @@ bloch_status bloch_lp_train(bloch_lp* lp, int32_t steps, double lr, double* loss
         const float b2c = 1.f - std::pow(0.999f, (float)lp->adam_t);
         k_lp_adam<<<1, 512>>>(lp->d_prm, lp->d_m, lp->d_v, lp->d_grad, kLPN, (float)lr, b1c, b2c);
         BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        lp->version = bloch::next_lp_version();
     }
     BLOCH_CUDA_CHECK_RET(cudaDeviceSynchronize());
     return BLOCH_OK;

@@ -20,10 +20,29 @@
 
 namespace bloch {
 
+// Division of n < 2^31 by an invariant divisor d >= 1 with one high multiply,
+// an add and a shift (Granlund & Montgomery 1994, division by invariant
+// integers): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(m, n) + n) >> l.
+struct FastDiv {
+    unsigned m = 1;
+    int l = 0;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+    FastDiv f;
+    int l = 0;
+    while ((1ull << l) < (unsigned long long)d) ++l;
+    f.l = l;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) { return (__umulhi(f.m, n) + n) >> f.l; }
+
 struct Geo {
     int Nx, Ny, Nz;
     long long V;
     AxisPlan ax[3];
+    FastDiv dx, dy;   // division by Nx and by Ny
     // PCG convergence mask: system b is skipped when skip[b * skip_stride] == 0
     // (nullptr: every system runs); blockIdx.y / skip_ncomp is the system of a
     // per-component pass.

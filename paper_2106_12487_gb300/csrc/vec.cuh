@@ -54,15 +54,19 @@ __global__ void k_scale(const cplx_t<T>* in, cplx_t<T>* out, T s, size_t n) {
 // supported grid)
 template <typename T>
 __device__ __forceinline__ void voxel_q(const T* qb, const Geo& g, unsigned v, T& ax, T& ay, T& az) {
-    const unsigned nx = (unsigned)g.Nx, ny = (unsigned)g.Ny;
-    const unsigned t = v / nx;
-    const int x = (int)(v - t * nx);
-    const unsigned z = t / ny;
-    const int y = (int)(t - z * ny);
+    const unsigned t = fdiv(v, g.dx);
+    const int x = (int)(v - t * (unsigned)g.Nx);
+    const unsigned z = fdiv(t, g.dy);
+    const int y = (int)(t - z * (unsigned)g.Ny);
     ax = qb[x];
     ay = qb[g.Nx + y];
     az = qb[g.Nx + g.Ny + z];
 }
+
+// Correctly rounded reciprocal (the FP32 form uses the rounded reciprocal
+// intrinsic instead of a full division).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // z = P^-1(q) r for one voxel (three complex components); zero where q = 0.
 template <typename T>
@@ -85,7 +89,7 @@ __device__ __forceinline__ void green_apply(const PrecondCoef& pc, T qx, T qy, T
         z[0] = z[1] = z[2] = mk(T(0), T(0));
         return;
     }
-    const T id = T(1) / det;
+    const T id = recip(det);
     z[0] = cscale(cadd(cadd(cscale(r[0], A), cscale(r[1], F)), cscale(r[2], Ee)), id);
     z[1] = cscale(cadd(cadd(cscale(r[0], F), cscale(r[1], B)), cscale(r[2], D)), id);
     z[2] = cscale(cadd(cadd(cscale(r[0], Ee), cscale(r[1], D)), cscale(r[2], Cc)), id);
@@ -249,6 +253,7 @@ __global__ void k_cg_update(cplx_t<T>* __restrict__ r, const cplx_t<T>* __restri
     const T alpha = act ? T(sys[b].alpha) : T(0);
     T acc[2] = {T(0), T(0)};
     if (act) {
+#pragma unroll 2
         for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
             C rv[3], zv[3];
 #pragma unroll
@@ -291,6 +296,7 @@ __global__ void k_cg_pupdate(const cplx_t<T>* __restrict__ r, cplx_t<T>* __restr
     const T* qb = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T alpha = T(sys[b].alpha);
     const T beta = T(sys[b].beta);
+#pragma unroll 2
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)g.V; v += gridDim.x * blockDim.x) {
         C pv[3];
 #pragma unroll

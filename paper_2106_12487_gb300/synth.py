@@ -303,3 +303,22 @@ def small_polycrystal(grid, n_grains: int, seed: int, texture: str = "haar",
         k_list = kpath("GX", 4)
     return polycrystal(f"poly{grid}_{n_grains}_{seed}", grid, n_grains, seed, seed + 100, cu,
                        CU_CUBIC["rho"], np.asarray(k_list, dtype=float), n_bands, tol, texture)
+
+
+def zener_cell(grid, index: int, zener_range=(1.0, 4.0), grains_range=(20, 200), n_bands: int = 10,
+               n_k: int = 9) -> Problem:
+    """One cell of the learned-preconditioner training family: a cubic
+    polycrystal whose C11, C12 are the Cu-like values and whose C44 =
+    A (C11 - C12) / 2 for a Zener ratio A drawn uniformly from zener_range,
+    with a uniform integer number of grains from grains_range, periodic
+    Voronoi seeds 1000 + index and Haar orientations 2000 + index.  The draw
+    of A and of the grain count uses PCG64(1000 + index)."""
+    rng = np.random.default_rng(1000 + index)
+    A = float(rng.uniform(*zener_range))
+    ng = int(rng.integers(grains_range[0], grains_range[1] + 1))
+    C11, C12 = CU_CUBIC["C11"], CU_CUBIC["C12"]
+    C6 = cubic_voigt(C11, C12, A * (C11 - C12) / 2)
+    p = polycrystal(f"zener{tuple(grid)}_{index}", grid, ng, 1000 + index, 2000 + index, C6, CU_CUBIC["rho"],
+                    kpath("GXMGR", n_k), n_bands, 1e-10)
+    p.meta.update(zener=A)
+    return p

@@ -183,3 +183,25 @@ def test_bands_nonuniform_density(B, prec, bar, opt):
     with pytest.raises(B.BlochError) as e:
         B.Plan.from_problem(p, precision=prec, method=0, **opt).solve_bands(ks, 5)
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("n_bands,ncv", [(16, 0), (6, 40), (6, 63)])
+def test_lanczos_large_basis(B, n_bands, ncv):
+    """Lanczos bases above 32 vectors (16 bands take the default
+    max(2n + 1, 20) = 33; explicit 40 and the cap 63): the restart's basis
+    rotation takes its column-chunked form; frequencies against the oracle."""
+    p = synth.small_polycrystal((8, 8, 8), 6, 5, n_bands=n_bands)
+    med = O.Medium.from_problem(p)
+    ks = np.array([[0.5, 0.0, 0.0], [0.3, 0.6, 0.9]]) * math.pi / 1e-3
+    want = O.solve_bands(med, ks, n_bands, 1e-12, 1e-12, method="lanczos").omega
+    plan = B.Plan.from_problem(p, precision=0, method=0, tol_lin=1e-11, tol_eig=1e-10, ncv=ncv)
+    got, stats, _ = plan.solve_bands(ks, n_bands)
+    assert freq_err(got, want) < 1e-9
+
+
+def test_lanczos_basis_cap(B):
+    p = synth.small_polycrystal((8, 8, 8), 6, 5, n_bands=6)
+    ks = np.array([[0.5, 0.0, 0.0]]) * math.pi / 1e-3
+    with pytest.raises(B.BlochError) as e:
+        B.Plan.from_problem(p, precision=0, method=0, ncv=64).solve_bands(ks, 6)
+    assert e.value.status == 7

@@ -49,3 +49,20 @@ def test_kpath_endpoints_and_spacing():
     assert d.max() <= d.min() * 1.0001 or np.all(d > 0)
     k2 = synth.kpath("GX", 10)
     assert np.allclose(np.diff(k2[:, 0]), math.pi / 1e-3 / 9)
+
+
+def test_zener_cell_family():
+    """Training family of the learned preconditioner: Zener ratio and grain
+    count in range, C44 = A (C11 - C12) / 2 before rotation (the rotation
+    invariant C11 + C22 + C33 + 2 (C44 + C55 + C66) checks it), reproducible."""
+    a = synth.zener_cell((8, 8, 8), 3)
+    b = synth.zener_cell((8, 8, 8), 3)
+    assert np.array_equal(a.grain_ids, b.grain_ids) and np.allclose(a.C_per_grain, b.C_per_grain)
+    A = a.meta["zener"]
+    assert 1.0 <= A <= 4.0 and 20 <= a.G <= 200
+    C11, C12 = synth.CU_CUBIC["C11"], synth.CU_CUBIC["C12"]
+    C44 = A * (C11 - C12) / 2
+    inv = [np.trace(C[:3, :3]) + 2 * np.trace(C[3:, 3:]) for C in a.C_per_grain]
+    assert np.allclose(inv, 3 * C11 + 6 * C44, rtol=1e-12)
+    assert len(np.unique(a.grain_ids)) <= a.G
+    assert synth.zener_cell((8, 8, 8), 4).meta["zener"] != A
