@@ -303,8 +303,11 @@ def run_ours(args, ws, rank, local):
     prec = bloch.FP64 if args.form == "plain" else bloch.FP32
     if args.form == "chosen":
         # FP32 fields and PCG: FP32 shift-invert Lanczos, then Algorithm 1 refinement
-        # sweeps with the FP64 residual check
-        opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-5, tol_eig=1e-5, max_cg=500,
+        # sweeps with the FP64 residual check.  The refinement (residual-correction
+        # form) fixes the final accuracy, so the inner PCG tolerance of both stages
+        # only trades PCG iterations against sweeps: 1e-2 was fastest at equal
+        # frequencies (relative change <= 1e-10 against 1e-5 inner solves)
+        opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500,
                    max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph)
     elif args.form == "chosen-subspace":
         # FP32 fields and PCG, subspace iteration with warm starts, FP64 residual check

@@ -12,7 +12,7 @@ from paper_2106_12487_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-CHOSEN = dict(precision=1, method=0, tol_lin=1e-5, tol_eig=1e-5, max_cg=500, max_outer=100)
+CHOSEN = dict(precision=1, method=0, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, max_outer=100)   # the bench's
 
 
 @pytest.fixture(scope="module")
