@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--lp-steps", type=int, default=500, help="Adam steps for --precond learned")
     ap.add_argument("--no-trace", action="store_true",
                     help="skip the extra traced (untimed) step that reports the solver's phase breakdown")
+    ap.add_argument("--tensor-gram", type=int, default=0, choices=[0, 1],
+                    help="1: Algorithm 1 projections of FP32 blocks on the tensor cores (tcgen05)")
     ap.add_argument("--cuda-graph", type=int, default=1, choices=[0, 1],
                     help="1: PCG loop as one CUDA graph with a device-side while node; 0: host-driven loop "
                          "(same kernels; used for per-launch profiling)")
@@ -308,11 +310,13 @@ def run_ours(args, ws, rank, local):
         # only trades PCG iterations against sweeps: 1e-2 was fastest at equal
         # frequencies (relative change <= 1e-10 against 1e-5 inner solves)
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500,
-                   max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph)
+                   max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph,
+                   tensor_gram=args.tensor_gram)
     elif args.form == "chosen-subspace":
         # FP32 fields and PCG, subspace iteration with warm starts, FP64 residual check
         opt = dict(precision=prec, method=bloch.SUBSPACE, tol_lin=1e-3, tol_eig=1e-6, max_cg=500,
-                   max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph)
+                   max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph,
+                   tensor_gram=args.tensor_gram)
     else:
         # the paper's plain form: FP64, shift-invert Lanczos, cuFFT operator
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-10, tol_eig=1e-10, max_cg=2000,
@@ -406,7 +410,8 @@ def run_ours(args, ws, rank, local):
                 "config": {"workload": args.workload, "grid": list(p.grid), "grains": int(p.G),
                            "n_bands": p.n_bands, "n_k_path": int(nk), "k_per_step": kps,
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
-                           "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"], "method": "subspace" if opt["method"] else "lanczos",
+                           "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"],
+                           "tensor_gram": opt.get("tensor_gram", 0), "method": "subspace" if opt["method"] else "lanczos",
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,

@@ -104,6 +104,11 @@ typedef struct {
                             passes; x passes use half of it), one of 4, 8, 16, 32; each
                             pass lowers it further to fit its shared-memory budget.
                             0 = 32.  Default 0.                                         */
+    int32_t tensor_gram; /* Algorithm 1 projections of FP32 blocks: 1 = on the tensor cores
+                            (tcgen05, TF32 inputs split hi + lo so products keep FP32
+                            accuracy, FP32 accumulation per CTA, FP64 across CTAs);
+                            0 = on the CUDA cores.  FP64 blocks always use the CUDA
+                            cores.  Default 0.                                          */
 } bloch_options;
 
 /* Outcome of bloch_plan_autotune. */

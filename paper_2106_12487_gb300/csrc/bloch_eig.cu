@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "eig_kernels.cuh"
+#include "gram_tc.cuh"
 #include "internal.h"
 
 namespace bloch {
@@ -288,6 +289,11 @@ struct Subspace {
     double2 *U64 = nullptr, *KU64 = nullptr, *MU64 = nullptr;
     int gblk = 0, dblk = 0;
     size_t gsmem = 0;
+    // tensor-core Gram (FP32 blocks, options.tensor_gram)
+    bool use_tc = false;
+    int gblk_tc = 0;
+    size_t tcsmem = 0;
+    int* d_gerr = nullptr;
 
     struct Slot {
         int kidx = -1;
@@ -339,8 +345,23 @@ struct Subspace {
         if (cudaFuncSetAttribute(k_gram_km<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem) !=
             cudaSuccess)
             return set_error(BLOCH_ECUDA, "cudaFuncSetAttribute (Gram kernel)");
+        if constexpr (std::is_same<T, float>::value) {
+            use_tc = pl->opt.tensor_gram != 0 && q <= kQMaxTC;
+            if (use_tc) {
+                // about 16 CTAs per SM-slot of work, so each CTA's FP32 accumulator
+                // sums a few thousand element pairs before the FP64 reduction
+                gblk_tc = (int)std::max(1LL, std::min<long long>((n3 + kTCElems - 1) / kTCElems,
+                                                                 std::max(1, 2432 / B)));
+                tcsmem = tc_smem_bytes(q);
+                if (allow_max_dyn_smem(k_gram_tc) != cudaSuccess)
+                    return set_error(BLOCH_ECUDA, "cudaFuncSetAttribute (tensor-core Gram kernel)");
+                if ((s = alloc(&d_gerr, 1))) return s;
+                BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(d_gerr, 0, sizeof(int), pl->stream));
+            }
+        }
+        const int gpart_blk = std::max(gblk, gblk_tc);
         if ((s = alloc(&d_part, (size_t)B * q * dblk * 3)) || (s = alloc(&d_scal, (size_t)B * q * 2)) ||
-            (s = alloc(&d_gpart, (size_t)B * gblk * 2 * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
+            (s = alloc(&d_gpart, (size_t)B * gpart_blk * 2 * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
             (s = alloc(&d_Q, (size_t)B * q * q)) || (s = alloc(&d_idx, (size_t)3 * q)) ||
             (s = alloc(&d_val, (size_t)3 * q)))
             return s;
@@ -715,16 +736,34 @@ struct Subspace {
             // projections K = Ub^H Kn, M = Ub^H Mn in one pass over the block
             dim3 gg(gblk, nact);
             const int npair = q * q;
-            ++pl->launches;
-            k_gram_km<T><<<gg, kGKThreads, gsmem, pl->stream>>>(Ub, KU, uniform ? nullptr : MUb, q, n3, d_gpart);
-            ++pl->launches;
-            k_gram_final<<<dim3((2 * npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair, nact,
-                                                                                       d_G);
+            if constexpr (std::is_same<T, float>::value) {
+                if (use_tc) {
+                    ++pl->launches;
+                    k_gram_tc<<<dim3(gblk_tc, nact), kTCThreads, tcsmem, pl->stream>>>(
+                        Ub, KU, uniform ? nullptr : MUb, q, n3, d_gpart, d_gerr);
+                    ++pl->launches;
+                    k_gram_final<<<dim3((2 * npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk_tc,
+                                                                                               npair, nact, d_G);
+                }
+            }
+            if (!use_tc) {
+                ++pl->launches;
+                k_gram_km<T><<<gg, kGKThreads, gsmem, pl->stream>>>(Ub, KU, uniform ? nullptr : MUb, q, n3,
+                                                                    d_gpart);
+                ++pl->launches;
+                k_gram_final<<<dim3((2 * npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair,
+                                                                                           nact, d_G);
+            }
             trace_end(pl, tr_proj);
             std::vector<double2> G((size_t)2 * nact * npair);
             BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(G.data(), d_G, sizeof(double2) * G.size(), cudaMemcpyDeviceToHost,
                                                  pl->stream));
+            int gerr = 0;
+            if (use_tc)
+                BLOCH_CUDA_CHECK_RET(
+                    cudaMemcpyAsync(&gerr, d_gerr, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
             BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+            if (gerr) return set_error(BLOCH_ECUDA, "tensor-core Gram: a wait for the MMAs timed out");
             std::vector<double2> Qh((size_t)nact * npair);
             for (int i = 0; i < nact; ++i) {
                 std::vector<cd> Km(npair), Mm(npair), Qm;

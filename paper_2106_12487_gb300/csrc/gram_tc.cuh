@@ -1,0 +1,308 @@
+// Tensor-core (tcgen05) form of the Algorithm 1 projections for FP32 blocks:
+//   K[i][j] = sum_e conj(A_i(e)) Bk_j(e),   M[i][j] = sum_e conj(A_i(e)) C_j(e)
+// with C = Bm, or C = A for a uniform density.
+//
+// Real form.  A complex vector x of n elements is the real vector of its 2n
+// interleaved (re, im) floats; rot(x) = (im, -re) element by element.  Then
+//   Re conj(a).b = <a, b>,   Im conj(a).b = <a, rot(b)> = -<rot(a), b>.
+// One MMA chain D = P Q^T over the 2n floats of a chunk range gives both
+// matrices: P (M side, 128 rows) holds Bk_0..Bk_{q-1}, C_0..C_{q-1};
+// Q (N side, Npad rows) holds A_0..A_{q-1}, rot(A_0)..rot(A_{q-1}); so
+//   Re K[j][r] = D[r][j],       Im K[j][r] = -D[r][q + j],
+//   Re M[j][r] = D[q + r][j],   Im M[j][r] = -D[q + r][q + j].
+// FP32 accuracy from TF32 inputs: x = hi + lo with hi = x rounded to TF32 and
+// lo = x - hi (exact); D += Ph Qh^T + Ph Ql^T + Pl Qh^T (the dropped Pl Ql^T
+// term is below 2^-22 of each product).
+//
+// Data flow per CTA (one slot, a strided range of chunks of kTCElems complex
+// elements): 256 threads load the chunk's rows from HBM (each warp 8 rows x 4
+// elements: full 32-byte sectors), split them into hi/lo (and rot) and store
+// them in the K-major, unswizzled core-matrix layout (8 rows x 16 bytes per
+// 128-byte core matrix; core matrices adjacent in K 128 bytes apart, 8-row
+// groups SBO bytes apart) of one of two stages; one thread then issues the
+// stage's MMAs (M = 128, N = Npad, K = 8 floats each) into an FP32 accumulator
+// in tensor memory and commits them to the stage's mbarrier, which the
+// threads wait on before they refill that stage.  Rows of P beyond 2q are
+// never written: the 128-row operand reads whatever follows in shared memory
+// there, which only reaches accumulator rows that are discarded.  At the end
+// warps 0-3 read the accumulator (warp w owns lanes 32w..32w+31 = rows of D)
+// and write the CTA's partial K and M in FP64, in the layout k_gram_final
+// sums.  Every wait is bounded: on a timeout the kernel raises *err and
+// returns after releasing its tensor memory.
+#pragma once
+
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace bloch {
+
+constexpr int kTCThreads = 256;
+constexpr int kQMaxTC = 32;                  // block size limit (as the CUDA-core Gram)
+constexpr int kTCElems = 32;                 // complex elements of a chunk
+constexpr int kTCK = 2 * kTCElems;           // floats of a chunk (K extent of a stage)
+constexpr int kTCSBO = (kTCK / 4) * 128;     // bytes between 8-row groups of a tile
+constexpr int kTCLBO = 128;                  // bytes between core matrices adjacent in K
+constexpr long long kTCSpin = 1ll << 24;     // bound on mbarrier polls
+
+__host__ __device__ constexpr int tc_npad(int q) { return ((2 * q + 15) / 16) * 16; }
+__host__ __device__ constexpr int tc_pgroups(int q) { return (2 * q + 7) / 8; }
+__host__ __device__ constexpr int tc_stage_bytes(int q) {
+    return (2 * tc_pgroups(q) + 2 * (tc_npad(q) / 8)) * kTCSBO;
+}
+// shared memory of k_gram_tc: two stages, plus room for the 128-row reads of
+// the last stage's P tiles
+inline size_t tc_smem_bytes(int q) {
+    const size_t stage = (size_t)tc_stage_bytes(q);
+    const size_t pl1 = stage + (size_t)tc_pgroups(q) * kTCSBO;   // Pl of stage 1
+    const size_t need_read = pl1 + 16 * (size_t)kTCSBO;
+    return std::max(2 * stage, need_read);
+}
+__host__ __device__ constexpr int tc_tmem_cols(int q) { return tc_npad(q) <= 32 ? 32 : 64; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < kTCSpin; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// shared memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kTCLBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kTCSBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+// byte offset of element (row, k) of a K-major unswizzled tile
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+    return (uint32_t)((row >> 3) * kTCSBO + (k >> 2) * kTCLBO + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, int row, int k, float x, float y) {
+    const float hx = to_tf32(x), hy = to_tf32(y);
+    const uint32_t o = tc_off(row, k);
+    *reinterpret_cast<float2*>(hi + o) = make_float2(hx, hy);
+    *reinterpret_cast<float2*>(lo + o) = make_float2(x - hx, y - hy);
+}
+
+__global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict__ A, const float2* __restrict__ Bk,
+                                                        const float2* __restrict__ Bm, int q, long long n_per,
+                                                        double2* __restrict__ partial, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int wait_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool has_m = Bm != nullptr;
+    const int npad = tc_npad(q), pg = tc_pgroups(q), ncols = tc_tmem_cols(q);
+    const int stage = tc_stage_bytes(q);
+    const int nsrc = has_m ? 3 * q : 2 * q;   // source rows: Bk, A, (Bm)
+    const int slot = blockIdx.y;
+    const size_t sbase = (size_t)slot * q * n_per;
+    const long long nchunk = (n_per + kTCElems - 1) / kTCElems;
+    auto tile = [&](int s, int which) -> unsigned char* {   // 0 Ph, 1 Pl, 2 Qh, 3 Ql
+        const int off = which == 0 ? 0 : which == 1 ? pg : which == 2 ? 2 * pg : 2 * pg + npad / 8;
+        return sm + (size_t)s * stage + (size_t)off * kTCSBO;
+    };
+    // zero the padding rows of every tile once (P rows 2q.. 8pg, Q rows 2q..npad)
+    for (int s = 0; s < 2; ++s)
+        for (int w = 0; w < 4; ++w) {
+            const int r0 = 2 * q, r1 = w < 2 ? 8 * pg : npad;
+            for (int t = tid; t < (r1 - r0) * kTCK; t += kTCThreads) {
+                const int row = r0 + t / kTCK, k = t % kTCK;
+                *reinterpret_cast<float*>(tile(s, w) + tc_off(row, k)) = 0.f;
+            }
+        }
+    if (tid == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t dtm = tmem_base;
+    const uint32_t idesc = tc_idesc(npad);
+    // warp task t: source rows 8 * (t / 8) .. +7, elements 4 * (t % 8) .. +3 of the chunk;
+    // lane: row 8 * (t / 8) + lane / 4, element 4 * (t % 8) + lane % 4
+    const int ntask = ((nsrc + 7) / 8) * (kTCElems / 4);
+    constexpr int kMaxT = (3 * kQMaxTC / 8) * (kTCElems / 4) / (kTCThreads / 32);   // warp tasks per warp
+    float2 cur[kMaxT], nxt[kMaxT];
+    auto load = [&](long long ch, float2 (&v)[kMaxT]) {
+#pragma unroll
+        for (int i = 0; i < kMaxT; ++i) {
+            const int t = warp + i * (kTCThreads / 32);
+            v[i] = make_float2(0.f, 0.f);
+            if (t < ntask && ch < nchunk) {
+                const int s = 8 * (t / (kTCElems / 4)) + lane / 4;
+                const long long e = ch * kTCElems + 4 * (t % (kTCElems / 4)) + (lane & 3);
+                if (s < nsrc && e < n_per) {
+                    const float2* src = s < q ? Bk + sbase + (size_t)s * n_per
+                                              : (s < 2 * q ? A + sbase + (size_t)(s - q) * n_per
+                                                           : Bm + sbase + (size_t)(s - 2 * q) * n_per);
+                    v[i] = __ldg(src + e);
+                }
+            }
+        }
+    };
+    bool ok = true;
+    long long it = 0;
+    long long ch = blockIdx.x;
+    if (ch < nchunk) load(ch, cur);
+    for (; ch < nchunk; ch += gridDim.x, ++it) {
+        const int s = (int)(it & 1);
+        load(ch + gridDim.x, nxt);   // next chunk in flight while this one is staged
+        if (it >= 2) {   // the MMAs of iteration it - 2 have read this stage
+            if (tid == 0) wait_ok = mbar_wait(smem_u32(&bars[s]), (uint32_t)(((it - 2) >> 1) & 1)) ? 1 : 0;
+            __syncthreads();
+            if (!wait_ok) {   // uniform across the block
+                ok = false;
+                break;
+            }
+        }
+        unsigned char* ph = tile(s, 0);
+        unsigned char* pl = tile(s, 1);
+        unsigned char* qh = tile(s, 2);
+        unsigned char* ql = tile(s, 3);
+#pragma unroll
+        for (int i = 0; i < kMaxT; ++i) {
+            const int t = warp + i * (kTCThreads / 32);
+            if (t >= ntask) continue;
+            const int src = 8 * (t / (kTCElems / 4)) + lane / 4;
+            if (src >= nsrc) continue;
+            const int k = 2 * (4 * (t % (kTCElems / 4)) + (lane & 3));
+            const float2 v = cur[i];
+            if (src < q) {
+                tc_put(ph, pl, src, k, v.x, v.y);                       // Bk_r -> P row r
+            } else if (src < 2 * q) {
+                const int j = src - q;
+                tc_put(qh, ql, j, k, v.x, v.y);                         // A_j -> Q row j
+                tc_put(qh, ql, q + j, k, v.y, -v.x);                    // rot(A_j) -> Q row q + j
+                if (!has_m) tc_put(ph, pl, q + j, k, v.x, v.y);         // C_j = A_j -> P row q + j
+            } else {
+                tc_put(ph, pl, q + (src - 2 * q), k, v.x, v.y);         // C_j = Bm_j -> P row q + j
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t bph = smem_u32(ph), bpl = smem_u32(pl), bqh = smem_u32(qh), bql = smem_u32(ql);
+#pragma unroll
+            for (int ks = 0; ks < kTCK / 8; ++ks) {
+                const uint32_t o = (uint32_t)(ks * 2 * kTCLBO);
+                const int acc0 = (it > 0 || ks > 0) ? 1 : 0;
+                tc_mma(dtm, tc_desc(bph + o), tc_desc(bqh + o), idesc, acc0);
+                tc_mma(dtm, tc_desc(bph + o), tc_desc(bql + o), idesc, 1);
+                tc_mma(dtm, tc_desc(bpl + o), tc_desc(bqh + o), idesc, 1);
+            }
+            tc_commit(smem_u32(&bars[s]));
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxT; ++i) cur[i] = nxt[i];
+    }
+    // drain: the last one or two stages still in flight
+    if (tid == 0) {
+        bool d = ok;
+        if (d && it >= 1) d = mbar_wait(smem_u32(&bars[(it - 1) & 1]), (uint32_t)(((it - 1) >> 1) & 1));
+        if (d && it >= 2) d = mbar_wait(smem_u32(&bars[(it - 2) & 1]), (uint32_t)(((it - 2) >> 1) & 1));
+        wait_ok = d ? 1 : 0;
+        if (!d) atomicExch(err, 1);
+    }
+    __syncthreads();
+    ok = wait_ok != 0;
+    tc_fence_after();
+    const int npair = q * q;
+    double2* out = partial + ((size_t)slot * gridDim.x + blockIdx.x) * 2 * npair;
+    if (warp < 4) {
+        const int r = 32 * warp + lane;   // row of D held by this thread
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+            uint32_t v[16];
+            if (it > 0 && ok) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(dtm + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0u;   // no chunk reached this CTA (or a timeout)
+            }
+            if (r < 2 * q) {
+                const int w = r < q ? 0 : 1;
+                const int rr = r < q ? r : r - q;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    if (c >= 2 * q) continue;
+                    const double d = (double)__uint_as_float(v[i]);
+                    double* e = reinterpret_cast<double*>(out + (size_t)w * npair);
+                    if (c < q) e[2 * ((size_t)c * q + rr)] = d;             // Re X[c][rr]
+                    else e[2 * ((size_t)(c - q) * q + rr) + 1] = -d;        // Im X[c - q][rr]
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(dtm), "r"(ncols) : "memory");
+    }
+}
+
+}  // namespace bloch

@@ -62,7 +62,8 @@ def test_default_options_and_errors_without_gpu(libb):
     st = libb.bloch_plan_create(ctypes.byref(h), grid, L, ids, 1, C, rho0, None, None)
     assert st == 1 and b"density" in libb.bloch_last_error()
     assert libb.bloch_apply_K(None, 1, None, 0, None, None) == 1
-    for field, bad, msg in (("tile_pmax", 5, b"tile_pmax"), ("fft_variant", 3, b"fft_variant")):
+    for field, bad, msg in (("tile_pmax", 5, b"tile_pmax"), ("fft_variant", 3, b"fft_variant"),
+                            ("tensor_gram", 2, b"tensor_gram")):
         ob = bloch.default_options(**{field: bad})
         st = libb.bloch_plan_create(ctypes.byref(h), grid, L, ids, 1, C, rho, ctypes.byref(ob), None)
         assert st == 1 and not h.value and msg in libb.bloch_last_error()

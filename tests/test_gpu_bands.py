@@ -205,3 +205,28 @@ def test_lanczos_basis_cap(B):
     with pytest.raises(B.BlochError) as e:
         B.Plan.from_problem(p, precision=0, method=0, ncv=64).solve_bands(ks, 6)
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("uniform", [True, False])
+@pytest.mark.parametrize("method", [1, 0])
+def test_tensor_gram_bands(B, uniform, method):
+    """FP32 solves with the Algorithm 1 projections on the tensor cores
+    (tensor_gram = 1): the same frequencies as the oracle (to the FP32 bar)
+    and as the CUDA-core projections; uniform and non-uniform density (the
+    mass Gram is then a full product), subspace iteration and the Lanczos ->
+    refinement form.  Block sizes 12 (6 bands) and 18 (10 bands)."""
+    import dataclasses
+    if not uniform and method == 0:
+        pytest.skip("the Lanczos solver needs a uniform density")
+    for n_bands in (6, 10):
+        p = synth.small_polycrystal((12, 10, 8), 6, 9, n_bands=n_bands)
+        if not uniform:
+            p = dataclasses.replace(p, rho=np.random.default_rng(4).uniform(2000.0, 9000.0, p.G))
+        med = O.Medium.from_problem(p)
+        ks = np.array([[0.5, 0.0, 0.0], [0.3, 0.6, 0.9]]) * math.pi / 1e-3
+        want = O.solve_bands(med, ks, n_bands, 1e-12, 1e-12, method="lanczos").omega
+        opt = dict(precision=1, method=method, tol_lin=1e-3, tol_eig=1e-6)
+        got_tc, st_tc, _ = B.Plan.from_problem(p, tensor_gram=1, **opt).solve_bands(ks, n_bands)
+        got_cc, _, _ = B.Plan.from_problem(p, tensor_gram=0, **opt).solve_bands(ks, n_bands)
+        assert freq_err(got_tc, want) < 1e-6
+        assert np.max(np.abs(got_tc / got_cc - 1)) < 1e-6
