@@ -4,31 +4,34 @@
 //
 // Real form.  A complex vector x of n elements is the real vector of its 2n
 // interleaved (re, im) floats; rot(x) = (im, -re) element by element.  Then
-//   Re conj(a).b = <a, b>,   Im conj(a).b = <a, rot(b)> = -<rot(a), b>.
-// One MMA chain D = P Q^T over the 2n floats of a chunk range gives both
-// matrices: P (M side, 128 rows) holds Bk_0..Bk_{q-1}, C_0..C_{q-1};
-// Q (N side, Npad rows) holds A_0..A_{q-1}, rot(A_0)..rot(A_{q-1}); so
-//   Re K[j][r] = D[r][j],       Im K[j][r] = -D[r][q + j],
-//   Re M[j][r] = D[q + r][j],   Im M[j][r] = -D[q + r][q + j].
+//   Re conj(a).b = <a, b>,   Im conj(a).b = -<rot(a), b>.
+// With the 2q "P" rows p_r = Bk_r (r < q), C_{r-q} (q <= r < 2q) and the 2q
+// "Q" rows q_j = A_j (j < q), rot(A_{j-q}) (q <= j < 2q):
+//   Re K[j][r] = <p_r, q_j>,     Im K[j][r] = -<p_r, q_{q+j}>,
+//   Re M[j][r] = <p_{q+r}, q_j>, Im M[j][r] = -<p_{q+r}, q_{q+j}>.
 // FP32 accuracy from TF32 inputs: x = hi + lo with hi = x rounded to TF32 and
-// lo = x - hi (exact); D += Ph Qh^T + Ph Ql^T + Pl Qh^T (the dropped Pl Ql^T
-// term is below 2^-22 of each product).
+// lo = x - hi (exact), <p, q> = <ph, qh> + <ph, ql> + <pl, qh> up to the
+// dropped <pl, ql> (below 2^-22 of each product).  The split is stacked into
+// the operands: the MMA's 128-row A operand holds ph (rows 0..2q-1) and pl
+// (rows 2q..4q-1), its B operand qh (rows 0..2q-1) and ql (rows 2q..4q-1), so
+// ONE MMA chain D = [ph; pl] [qh; ql]^T forms all four products at once, and
+//   <p_r, q_j> = D[r][j] + D[r][2q + j] + D[2q + r][j].
 //
 // Data flow per CTA (one slot, a strided range of chunks of kTCElems complex
 // elements): 256 threads load the chunk's rows from HBM (each warp 8 rows x 4
 // elements: full 32-byte sectors), split them into hi/lo (and rot) and store
 // them in the K-major, unswizzled core-matrix layout (8 rows x 16 bytes per
 // 128-byte core matrix; core matrices adjacent in K 128 bytes apart, 8-row
-// groups SBO bytes apart) of one of two stages; one thread then issues the
-// stage's MMAs (M = 128, N = Npad, K = 8 floats each) into an FP32 accumulator
-// in tensor memory and commits them to the stage's mbarrier, which the
-// threads wait on before they refill that stage.  Rows of P beyond 2q are
+// groups kTCSBO bytes apart) of one of two stages; one thread then issues the
+// stage's MMAs (M = 128, N = Npad >= 4q, K = 8 floats each) into an FP32
+// accumulator in tensor memory and commits them to the stage's mbarrier, which
+// the threads wait on before they refill that stage.  Rows of A beyond 4q are
 // never written: the 128-row operand reads whatever follows in shared memory
 // there, which only reaches accumulator rows that are discarded.  At the end
-// warps 0-3 read the accumulator (warp w owns lanes 32w..32w+31 = rows of D)
-// and write the CTA's partial K and M in FP64, in the layout k_gram_final
-// sums.  Every wait is bounded: on a timeout the kernel raises *err and
-// returns after releasing its tensor memory.
+// warps 0-3 copy the accumulator (warp w owns lanes 32w..32w+31 = rows of D)
+// to shared memory, and all threads combine it into the CTA's partial K and M
+// in FP64, in the layout k_gram_final sums.  Every wait is bounded: on a
+// timeout the kernel raises *err and returns after releasing its tensor memory.
 #pragma once
 
 #include <stdint.h>
@@ -40,27 +43,25 @@
 namespace bloch {
 
 constexpr int kTCThreads = 256;
-constexpr int kQMaxTC = 32;                  // block size limit (as the CUDA-core Gram)
+constexpr int kQMaxTC = 32;                  // block size limit (4q rows fill M = 128)
 constexpr int kTCElems = 32;                 // complex elements of a chunk
 constexpr int kTCK = 2 * kTCElems;           // floats of a chunk (K extent of a stage)
 constexpr int kTCSBO = (kTCK / 4) * 128;     // bytes between 8-row groups of a tile
 constexpr int kTCLBO = 128;                  // bytes between core matrices adjacent in K
 constexpr long long kTCSpin = 1ll << 24;     // bound on mbarrier polls
 
-__host__ __device__ constexpr int tc_npad(int q) { return ((2 * q + 15) / 16) * 16; }
-__host__ __device__ constexpr int tc_pgroups(int q) { return (2 * q + 7) / 8; }
-__host__ __device__ constexpr int tc_stage_bytes(int q) {
-    return (2 * tc_pgroups(q) + 2 * (tc_npad(q) / 8)) * kTCSBO;
-}
-// shared memory of k_gram_tc: two stages, plus room for the 128-row reads of
-// the last stage's P tiles
+__host__ __device__ constexpr int tc_npad(int q) { return ((4 * q + 15) / 16) * 16; }
+__host__ __device__ constexpr int tc_agroups(int q) { return (4 * q + 7) / 8; }
+__host__ __device__ constexpr int tc_stage_bytes(int q) { return (tc_agroups(q) + tc_npad(q) / 8) * kTCSBO; }
+__host__ __device__ constexpr int tc_tmem_cols(int q) { return tc_npad(q) <= 32 ? 32 : (tc_npad(q) <= 64 ? 64 : 128); }
+// shared memory of k_gram_tc: two stages, room for the 128-row reads of the
+// last stage's A tile, and the accumulator copy of the epilogue
 inline size_t tc_smem_bytes(int q) {
     const size_t stage = (size_t)tc_stage_bytes(q);
-    const size_t pl1 = stage + (size_t)tc_pgroups(q) * kTCSBO;   // Pl of stage 1
-    const size_t need_read = pl1 + 16 * (size_t)kTCSBO;
-    return std::max(2 * stage, need_read);
+    const size_t need_read = stage + 16 * (size_t)kTCSBO;
+    const size_t dcopy = (size_t)128 * tc_npad(q) * sizeof(float);
+    return std::max(std::max(2 * stage, need_read), dcopy);
 }
-__host__ __device__ constexpr int tc_tmem_cols(int q) { return tc_npad(q) <= 32 ? 32 : 64; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -122,11 +123,11 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k) {
     return (uint32_t)((row >> 3) * kTCSBO + (k >> 2) * kTCLBO + (row & 7) * 16 + (k & 3) * 4);
 }
 
-__device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, int row, int k, float x, float y) {
+// hi part at row rh, lo part at row rh + lo_off of the same tile
+__device__ __forceinline__ void tc_put(unsigned char* tile, int rh, int lo_off, int k, float x, float y) {
     const float hx = to_tf32(x), hy = to_tf32(y);
-    const uint32_t o = tc_off(row, k);
-    *reinterpret_cast<float2*>(hi + o) = make_float2(hx, hy);
-    *reinterpret_cast<float2*>(lo + o) = make_float2(x - hx, y - hy);
+    *reinterpret_cast<float2*>(tile + tc_off(rh, k)) = make_float2(hx, hy);
+    *reinterpret_cast<float2*>(tile + tc_off(rh + lo_off, k)) = make_float2(x - hx, y - hy);
 }
 
 __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict__ A, const float2* __restrict__ Bk,
@@ -138,24 +139,22 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
     __shared__ int wait_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool has_m = Bm != nullptr;
-    const int npad = tc_npad(q), pg = tc_pgroups(q), ncols = tc_tmem_cols(q);
+    const int npad = tc_npad(q), ag = tc_agroups(q), ncols = tc_tmem_cols(q);
     const int stage = tc_stage_bytes(q);
+    const int q2 = 2 * q;                     // rows of one split half
     const int nsrc = has_m ? 3 * q : 2 * q;   // source rows: Bk, A, (Bm)
     const int slot = blockIdx.y;
     const size_t sbase = (size_t)slot * q * n_per;
     const long long nchunk = (n_per + kTCElems - 1) / kTCElems;
-    auto tile = [&](int s, int which) -> unsigned char* {   // 0 Ph, 1 Pl, 2 Qh, 3 Ql
-        const int off = which == 0 ? 0 : which == 1 ? pg : which == 2 ? 2 * pg : 2 * pg + npad / 8;
-        return sm + (size_t)s * stage + (size_t)off * kTCSBO;
-    };
-    // zero the padding rows of every tile once (P rows 2q.. 8pg, Q rows 2q..npad)
+    auto atile = [&](int s) -> unsigned char* { return sm + (size_t)s * stage; };
+    auto btile = [&](int s) -> unsigned char* { return sm + (size_t)s * stage + (size_t)ag * kTCSBO; };
+    // zero the padding rows once: A rows 4q .. 8ag, B rows 4q .. npad
     for (int s = 0; s < 2; ++s)
-        for (int w = 0; w < 4; ++w) {
-            const int r0 = 2 * q, r1 = w < 2 ? 8 * pg : npad;
-            for (int t = tid; t < (r1 - r0) * kTCK; t += kTCThreads) {
-                const int row = r0 + t / kTCK, k = t % kTCK;
-                *reinterpret_cast<float*>(tile(s, w) + tc_off(row, k)) = 0.f;
-            }
+        for (int w = 0; w < 2; ++w) {
+            const int r0 = 2 * q2, r1 = w == 0 ? 8 * ag : npad;
+            unsigned char* t0 = w == 0 ? atile(s) : btile(s);
+            for (int t = tid; t < (r1 - r0) * kTCK; t += kTCThreads)
+                *reinterpret_cast<float*>(t0 + tc_off(r0 + t / kTCK, t % kTCK)) = 0.f;
         }
     if (tid == 0) {
         mbar_init(smem_u32(&bars[0]), 1);
@@ -173,8 +172,8 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
     tc_fence_after();
     const uint32_t dtm = tmem_base;
     const uint32_t idesc = tc_idesc(npad);
-    // warp task t: source rows 8 * (t / 8) .. +7, elements 4 * (t % 8) .. +3 of the chunk;
-    // lane: row 8 * (t / 8) + lane / 4, element 4 * (t % 8) + lane % 4
+    // warp task t: source rows 8 (t / 8) .. +7, elements 4 (t % 8) .. +3 of the chunk;
+    // lane: row 8 (t / 8) + lane / 4, element 4 (t % 8) + lane % 4
     const int ntask = ((nsrc + 7) / 8) * (kTCElems / 4);
     constexpr int kMaxT = (3 * kQMaxTC / 8) * (kTCElems / 4) / (kTCThreads / 32);   // warp tasks per warp
     float2 cur[kMaxT], nxt[kMaxT];
@@ -210,10 +209,8 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
                 break;
             }
         }
-        unsigned char* ph = tile(s, 0);
-        unsigned char* pl = tile(s, 1);
-        unsigned char* qh = tile(s, 2);
-        unsigned char* ql = tile(s, 3);
+        unsigned char* at = atile(s);
+        unsigned char* bt = btile(s);
 #pragma unroll
         for (int i = 0; i < kMaxT; ++i) {
             const int t = warp + i * (kTCThreads / 32);
@@ -223,14 +220,14 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
             const int k = 2 * (4 * (t % (kTCElems / 4)) + (lane & 3));
             const float2 v = cur[i];
             if (src < q) {
-                tc_put(ph, pl, src, k, v.x, v.y);                       // Bk_r -> P row r
+                tc_put(at, src, q2, k, v.x, v.y);                     // Bk_r -> p_r
             } else if (src < 2 * q) {
                 const int j = src - q;
-                tc_put(qh, ql, j, k, v.x, v.y);                         // A_j -> Q row j
-                tc_put(qh, ql, q + j, k, v.y, -v.x);                    // rot(A_j) -> Q row q + j
-                if (!has_m) tc_put(ph, pl, q + j, k, v.x, v.y);         // C_j = A_j -> P row q + j
+                tc_put(bt, j, q2, k, v.x, v.y);                       // A_j -> q_j
+                tc_put(bt, q + j, q2, k, v.y, -v.x);                  // rot(A_j) -> q_{q+j}
+                if (!has_m) tc_put(at, q + j, q2, k, v.x, v.y);       // C_j = A_j -> p_{q+j}
             } else {
-                tc_put(ph, pl, q + (src - 2 * q), k, v.x, v.y);         // C_j = Bm_j -> P row q + j
+                tc_put(at, q + (src - 2 * q), q2, k, v.x, v.y);       // C_j = Bm_j -> p_{q+j}
             }
         }
         fence_async_smem();
@@ -238,14 +235,11 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t bph = smem_u32(ph), bpl = smem_u32(pl), bqh = smem_u32(qh), bql = smem_u32(ql);
+            const uint32_t ba = smem_u32(at), bb = smem_u32(bt);
 #pragma unroll
             for (int ks = 0; ks < kTCK / 8; ++ks) {
                 const uint32_t o = (uint32_t)(ks * 2 * kTCLBO);
-                const int acc0 = (it > 0 || ks > 0) ? 1 : 0;
-                tc_mma(dtm, tc_desc(bph + o), tc_desc(bqh + o), idesc, acc0);
-                tc_mma(dtm, tc_desc(bph + o), tc_desc(bql + o), idesc, 1);
-                tc_mma(dtm, tc_desc(bpl + o), tc_desc(bqh + o), idesc, 1);
+                tc_mma(dtm, tc_desc(ba + o), tc_desc(bb + o), idesc, (it > 0 || ks > 0) ? 1 : 0);
             }
             tc_commit(smem_u32(&bars[s]));
         }
@@ -263,10 +257,10 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
     __syncthreads();
     ok = wait_ok != 0;
     tc_fence_after();
-    const int npair = q * q;
-    double2* out = partial + ((size_t)slot * gridDim.x + blockIdx.x) * 2 * npair;
+    // accumulator -> shared memory (the stages are free now): dsm[row][col]
+    float* dsm = reinterpret_cast<float*>(sm);
     if (warp < 4) {
-        const int r = 32 * warp + lane;   // row of D held by this thread
+        const int r = 32 * warp + lane;
         for (int c0 = 0; c0 < npad; c0 += 16) {
             uint32_t v[16];
             if (it > 0 && ok) {
@@ -282,22 +276,25 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = 0u;   // no chunk reached this CTA (or a timeout)
             }
-            if (r < 2 * q) {
-                const int w = r < q ? 0 : 1;
-                const int rr = r < q ? r : r - q;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = c0 + i;
-                    if (c >= 2 * q) continue;
-                    const double d = (double)__uint_as_float(v[i]);
-                    double* e = reinterpret_cast<double*>(out + (size_t)w * npair);
-                    if (c < q) e[2 * ((size_t)c * q + rr)] = d;             // Re X[c][rr]
-                    else e[2 * ((size_t)(c - q) * q + rr) + 1] = -d;        // Im X[c - q][rr]
-                }
-            }
+            for (int i = 0; i < 16; ++i) dsm[(size_t)r * npad + c0 + i] = __uint_as_float(v[i]);
         }
     }
     tc_fence_before();
+    __syncthreads();
+    // <p_r, q_j> = D[r][j] + D[r][2q + j] + D[2q + r][j]
+    auto dot = [&](int r, int j) -> double {
+        return (double)dsm[(size_t)r * npad + j] + (double)dsm[(size_t)r * npad + q2 + j] +
+               (double)dsm[(size_t)(q2 + r) * npad + j];
+    };
+    const int npair = q * q;
+    double2* out = partial + ((size_t)slot * gridDim.x + blockIdx.x) * 2 * npair;
+    for (int t = tid; t < 2 * npair; t += kTCThreads) {
+        const int w = t / npair, pr = t - w * npair;   // w 0: K, 1: M; entry X[j][r]
+        const int j = pr / q, r = pr - j * q;
+        const int pr_row = w * q + r;
+        out[t] = make_double2(dot(pr_row, j), -dot(pr_row, q + j));
+    }
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
