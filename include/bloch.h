@@ -109,6 +109,10 @@ typedef struct {
                             accuracy, FP32 accumulation per CTA, FP64 across CTAs);
                             0 = on the CUDA cores.  FP64 blocks always use the CUDA
                             cores.  Default 0.                                          */
+    double hybrid_tol;   /* FP32 with BLOCH_LANCZOS: the Lanczos stage stops once its Ritz
+                            estimates reach this relative accuracy and hands its block to
+                            the Algorithm 1 refinement, which alone decides convergence
+                            (tol_eig).  0 = max(1e-5, 10 tol_eig).  Default 0.          */
 } bloch_options;
 
 /* Outcome of bloch_plan_autotune. */

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("tol_eig", ctypes.c_double), ("max_cg", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("k_batch", ctypes.c_int32), ("ncv", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("cuda_graph", ctypes.c_int32), ("fft_variant", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("tile_pmax", ctypes.c_int32), ("tensor_gram", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("tile_pmax", ctypes.c_int32), ("tensor_gram", ctypes.c_int32),
+                ("hybrid_tol", ctypes.c_double)]
 
 
 class Trace(ctypes.Structure):

@@ -1259,7 +1259,7 @@ static bloch_status run_hybrid(bloch_plan* pl, const std::vector<std::array<doub
     std::vector<double> om_tmp;
     bloch_status s = BLOCH_OK;
     bool unconverged = false;
-    const double tol_l = std::max(1e-5, 10.0 * pl->opt.tol_eig);
+    const double tol_l = pl->opt.hybrid_tol > 0 ? pl->opt.hybrid_tol : std::max(1e-5, 10.0 * pl->opt.tol_eig);
     for (size_t c0 = 0; c0 < ks.size() && s == BLOCH_OK; c0 += chunk) {
         std::vector<std::array<double, 3>> sub(ks.begin() + c0, ks.begin() + std::min(ks.size(), c0 + chunk));
         om_tmp.assign(sub.size() * n_bands, 0.0);

@@ -875,6 +875,10 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         delete pl;
         return set_error(BLOCH_EINVAL, "tile_pmax must be 0, 4, 8, 16 or 32");
     }
+    if (!(pl->opt.hybrid_tol >= 0.0) || !(pl->opt.hybrid_tol < 1.0)) {
+        delete pl;
+        return set_error(BLOCH_EINVAL, "hybrid_tol must be in [0, 1)");
+    }
     if (pl->opt.tensor_gram != 0 && pl->opt.tensor_gram != 1) {
         delete pl;
         return set_error(BLOCH_EINVAL, "tensor_gram must be 0 or 1");

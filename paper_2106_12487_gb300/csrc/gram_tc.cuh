@@ -59,7 +59,7 @@ __host__ __device__ constexpr int tc_tmem_cols(int q) { return tc_npad(q) <= 32 
 inline size_t tc_smem_bytes(int q) {
     const size_t stage = (size_t)tc_stage_bytes(q);
     const size_t need_read = stage + 16 * (size_t)kTCSBO;
-    const size_t dcopy = (size_t)128 * tc_npad(q) * sizeof(float);
+    const size_t dcopy = (size_t)128 * (tc_npad(q) + 1) * sizeof(float);
     return std::max(std::max(2 * stage, need_read), dcopy);
 }
 
@@ -257,8 +257,10 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
     __syncthreads();
     ok = wait_ok != 0;
     tc_fence_after();
-    // accumulator -> shared memory (the stages are free now): dsm[row][col]
+    // accumulator -> shared memory (the stages are free now): dsm[row][col],
+    // rows padded by one float so a warp's 32 rows fall in different banks
     float* dsm = reinterpret_cast<float*>(sm);
+    const int ld = npad + 1;
     if (warp < 4) {
         const int r = 32 * warp + lane;
         for (int c0 = 0; c0 < npad; c0 += 16) {
@@ -277,15 +279,15 @@ __global__ void __launch_bounds__(kTCThreads) k_gram_tc(const float2* __restrict
                 for (int i = 0; i < 16; ++i) v[i] = 0u;   // no chunk reached this CTA (or a timeout)
             }
 #pragma unroll
-            for (int i = 0; i < 16; ++i) dsm[(size_t)r * npad + c0 + i] = __uint_as_float(v[i]);
+            for (int i = 0; i < 16; ++i) dsm[(size_t)r * ld + c0 + i] = __uint_as_float(v[i]);
         }
     }
     tc_fence_before();
     __syncthreads();
     // <p_r, q_j> = D[r][j] + D[r][2q + j] + D[2q + r][j]
     auto dot = [&](int r, int j) -> double {
-        return (double)dsm[(size_t)r * npad + j] + (double)dsm[(size_t)r * npad + q2 + j] +
-               (double)dsm[(size_t)(q2 + r) * npad + j];
+        return (double)dsm[(size_t)r * ld + j] + (double)dsm[(size_t)r * ld + q2 + j] +
+               (double)dsm[(size_t)(q2 + r) * ld + j];
     };
     const int npair = q * q;
     double2* out = partial + ((size_t)slot * gridDim.x + blockIdx.x) * 2 * npair;
