@@ -13,6 +13,7 @@ from paper_2106_12487_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 CHOSEN = dict(precision=1, method=0, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, max_outer=100)   # the bench's
+# (the bench also sets block = n_bands + 2)
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +32,7 @@ def test_rve128_chosen_form_frequencies(B):
     p = synth.workload("rve128_g200")
     idx = [1, 37]              # the first wave vector after Gamma, one on M-Gamma
     ks = p.k_list[idx]
-    plan = B.Plan.from_problem(p, **CHOSEN)
+    plan = B.Plan.from_problem(p, block=p.n_bands + 2, **CHOSEN)
     vecs = torch.zeros(len(idx) * p.n_bands * 3 * plan.V, dtype=torch.complex64, device="cuda")
     got, stats, _ = plan.solve_bands(ks, p.n_bands, vecs_out=vecs)
     ref_plan = B.Plan.from_problem(p, precision=0, method=0, tol_lin=1e-10, tol_eig=1e-10, max_cg=2000)
@@ -76,7 +77,7 @@ def test_rve256_chosen_form_eigenpairs(B, rve256):
     import torch
     p, med = rve256
     ks = p.k_list[[9]]
-    plan = B.Plan.from_problem(p, **CHOSEN)
+    plan = B.Plan.from_problem(p, block=p.n_bands + 2, **CHOSEN)
     vecs = torch.zeros(p.n_bands * 3 * plan.V, dtype=torch.complex64, device="cuda")
     got, stats, _ = plan.solve_bands(ks, p.n_bands, vecs_out=vecs)
     assert np.all(np.diff(got[0]) >= 0) and got[0, 0] > 0
