@@ -1119,7 +1119,7 @@ struct Lanczos {
                 ++pl->launches;
                 k_vdots<T><<<gd, 256, 0, pl->stream>>>(Vb, (long long)(m + 1) * n3, Xc, n3, d_nv, n3, maxnv, d_part);
                 ++pl->launches;
-                k_vdots_final<<<nact, 64, 0, pl->stream>>>(d_part, nblk, maxnv, rho_s, d_h);
+                k_vdots_final<<<dim3(maxnv, nact), 256, 0, pl->stream>>>(d_part, nblk, maxnv, rho_s, d_h);
                 dim3 ga(nblk, nact);
                 ++pl->launches;
                 k_vaxpy<T><<<ga, 256, 0, pl->stream>>>(Vb, (long long)(m + 1) * n3, Xc, n3, d_h, d_nv, n3, maxnv);

@@ -423,19 +423,19 @@ __global__ void k_vdots(const cplx_t<T>* __restrict__ V, long long vstride, cons
         partial[((size_t)slot * gridDim.x + blockIdx.x) * maxnv + i] = make_double2(acc[0], acc[1]);
 }
 
-// h[slot][i] = scale * sum_blk partial
+// h[slot][i] = scale * sum_blk partial; one block per (i, slot): blockIdx.x = i,
+// blockIdx.y = slot (a strided sum per thread, then the block tree: fixed order)
 static __global__ void k_vdots_final(const double2* __restrict__ partial, int nblk, int maxnv, double scale,
                                      double2* __restrict__ h) {
-    const int slot = blockIdx.x;
-    for (int i = threadIdx.x; i < maxnv; i += blockDim.x) {
-        double re = 0, im = 0;
-        for (int b = 0; b < nblk; ++b) {
-            const double2 v = partial[((size_t)slot * nblk + b) * maxnv + i];
-            re += v.x;
-            im += v.y;
-        }
-        h[(size_t)slot * maxnv + i] = make_double2(scale * re, scale * im);
+    const int i = blockIdx.x, slot = blockIdx.y;
+    double acc[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const double2 v = partial[((size_t)slot * nblk + b) * maxnv + i];
+        acc[0] += v.x;
+        acc[1] += v.y;
     }
+    block_sum<double, 2>(acc);
+    if (threadIdx.x == 0) h[(size_t)slot * maxnv + i] = make_double2(scale * acc[0], scale * acc[1]);
 }
 
 // W[slot] -= sum_{i < nv[slot]} V[slot][i] h[slot][i]
