@@ -250,8 +250,9 @@ void configure_passes(bloch_plan* pl, int variant, int pmax) {
 int fast_z_blocks(const bloch_plan* pl) {
     if (!pl->fast || !fast_x(pl->Nz)) return 0;
     const int RA = pl->Nz == 16 ? 4 : (pl->Nz == 128 ? 16 : 8);
+    const int P = kFastZThreads / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
-    return (int)((npen + 128 / RA - 1) / (128 / RA));
+    return (int)((npen + P - 1) / P);
 }
 
 bool has_fast_pass(const bloch_plan* pl, int precision) {
@@ -277,8 +278,8 @@ static void set_fast_attrs_n() {
     fast_attr(k_fpass_y<T, +1, RA, RB, PT>);
     fast_attr(k_fpass_y<T, -1, RA, RB, PT>);
     if constexpr (Z) {
-        fast_attr(k_fpass_z_strain<T, RA, RB>);
-        fast_attr(k_fpass_z_div<T, RA, RB>);
+        fast_attr(k_fpass_z_strain<T, RA, RB, kFastZThreads>);
+        fast_attr(k_fpass_z_div<T, RA, RB, kFastZThreads>);
         if constexpr (RB <= 8) fast_attr(k_fpass_x_stress<T, RA, RB>);
     }
 }
@@ -320,26 +321,28 @@ template <typename T, int RA, int RB>
 static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
-    constexpr int P = 128 / RA;
+    constexpr int NT = kFastZThreads;
+    constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     const size_t smem = (size_t)(N + 4 * N * P) * sizeof(cplx_t<T>);
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
-    k_fpass_z_strain<T, RA, RB><<<gr, 128, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
-                                                                 tw_of<T>(pl, 2), g);
+    k_fpass_z_strain<T, RA, RB, NT><<<gr, NT, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
+                                                                   tw_of<T>(pl, 2), g);
 }
 
 template <typename T, int RA, int RB>
 static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale, const cplx_t<T>* dotp, double2* dpart) {
     const Geo& g = geo_of<T>(pl);
     constexpr int N = RA * RB;
-    constexpr int P = 128 / RA;
+    constexpr int NT = kFastZThreads;
+    constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     const size_t smem = (size_t)(N + 3 * N * P) * sizeof(cplx_t<T>);
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
-    k_fpass_z_div<T, RA, RB><<<gr, 128, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
-                                                              tw_of<T>(pl, 2), g, out_scale, dotp, dpart);
+    k_fpass_z_div<T, RA, RB, NT><<<gr, NT, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
+                                                                tw_of<T>(pl, 2), g, out_scale, dotp, dpart);
 }
 
 template <typename T, int RA, int RB>

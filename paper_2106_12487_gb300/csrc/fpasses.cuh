@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_fpass_y(const cplx_t<T>* in, cplx_t<T>*
 }
 
 // --------------------------------------------------- pass 1: strain + inverse z
-// One thread per stage-2 task (blockDim.x == P * RA, P = 128 / RA).  The z
+// One thread per stage-2 task (blockDim.x == NT == P * RA, P = NT / RA).  The z
 // transform of q_z U_k cannot be formed from that of U_k (q_z varies along
 // the pencil), but q_x, q_y are constant on a z pencil, so with
 // a_k = F_z^-1(U_k) and b_k = F_z^-1(q_z U_k) the six Voigt strains are
@@ -103,13 +103,15 @@ __global__ void __launch_bounds__(256) k_fpass_y(const cplx_t<T>* in, cplx_t<T>*
 // and a_x are carried between them); the next component's pencils stream
 // into shared memory (cp.async, double buffered) while the current one is
 // transformed.
-template <typename T, int RA, int RB>
-__global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
+// NT = 256 gives 16-32 neighbouring pencils per CTA, so each z row of the
+// tile is 128-256 contiguous bytes in HBM.
+template <typename T, int RA, int RB, int NT = 128>
+__global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
                                                            const T* __restrict__ qtab,
                                                            const cplx_t<T>* __restrict__ twz, Geo g) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
-    constexpr int P = 128 / RA;
+    constexpr int P = NT / RA;
     constexpr int NP = N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
     auto prefetch = [&](int k, C* dstb) {
         const C* src = Ub + (size_t)k * g.V;
 #pragma unroll
-        for (int e = tid; e < NP; e += 128) {
+        for (int e = tid; e < NP; e += NT) {
             const int n = e / P, p = e % P;
             const bool ok = p < np;
             cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
     };
     prefetch(2, stg);
     prefetch(0, stg + NP);
-    for (int i = tid; i < N; i += 128) tw[i] = twz[i];
+    for (int i = tid; i < N; i += NT) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
     const unsigned pi = pi0 + (p2 < np ? p2 : 0);
     const T qx = qxt[pi % (unsigned)g.Nx], qy = qyt[pi / (unsigned)g.Nx];
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
 }
 
 // --------------------------------------------------- pass 5: forward z + divergence
-// One thread per stage-2 task (blockDim.x == P * RA); the three output
+// One thread per stage-2 task (blockDim.x == NT == P * RA); the three output
 // components of its RB elements are accumulated in registers:
 //   out_x = q_x S11 + q_y S12 + q_z S13, out_y = q_x S12 + q_y S22 + q_z S23,
 //   out_z = q_x S13 + q_y S23 + q_z S33   (S = forward z transform of sigma).
@@ -220,14 +222,14 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_strain(const cplx_t<T>* __re
 // With dotp != nullptr the CTA also forms sum conj(dotp) * out over its
 // pencils (the (p, A p) product of the PCG iteration, Algorithm 2) and writes
 // it to dpart[b * gridDim.x + blockIdx.x].
-template <typename T, int RA, int RB>
-__global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restrict__ E, cplx_t<T>* __restrict__ out,
+template <typename T, int RA, int RB, int NT = 128>
+__global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* __restrict__ E, cplx_t<T>* __restrict__ out,
                                                         const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
                                                         Geo g, T out_scale, const cplx_t<T>* __restrict__ dotp,
                                                         double2* __restrict__ dpart) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
-    constexpr int P = 128 / RA;
+    constexpr int P = NT / RA;
     constexpr int NP = N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restr
     auto prefetch = [&](int c, C* dstb) {
         const C* src = Eb + (size_t)c * g.V;
 #pragma unroll
-        for (int e = tid; e < NP; e += 128) {
+        for (int e = tid; e < NP; e += NT) {
             const int n = e / P, p = e % P;
             const bool ok = p < np;
             cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restr
     };
     prefetch(0, stg);
     prefetch(1, stg + NP);
-    for (int i = tid; i < N; i += 128) tw[i] = twz[i];
+    for (int i = tid; i < N; i += NT) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
     const unsigned pi = pi0 + (p2 < np ? p2 : 0);
     const T qv[2] = {qxt[pi % (unsigned)g.Nx], qyt[pi / (unsigned)g.Nx]};
@@ -320,22 +322,27 @@ __global__ void __launch_bounds__(128, 4) k_fpass_z_div(const cplx_t<T>* __restr
             }
         }
     }
-    if (dotp) {   // block reduction (4 warps); deterministic order
+    if (dotp) {   // block reduction (NT / 32 warps); deterministic order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dre += __shfl_xor_sync(0xffffffffu, dre, o);
             dim += __shfl_xor_sync(0xffffffffu, dim, o);
         }
-        __shared__ T red[2][4];
+        __shared__ T red[2][NT / 32];
         if ((tid & 31) == 0) {
             red[0][tid >> 5] = dre;
             red[1][tid >> 5] = dim;
         }
         __syncthreads();
-        if (tid == 0)
-            dpart[(size_t)b * gridDim.x + blockIdx.x] =
-                make_double2((double)red[0][0] + red[0][1] + red[0][2] + red[0][3],
-                             (double)red[1][0] + red[1][1] + red[1][2] + red[1][3]);
+        if (tid == 0) {
+            double sr = 0.0, si = 0.0;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) {
+                sr += (double)red[0][w];
+                si += (double)red[1][w];
+            }
+            dpart[(size_t)b * gridDim.x + blockIdx.x] = make_double2(sr, si);
+        }
     }
 }
 

@@ -38,6 +38,8 @@ struct Workspace {
 };
 
 constexpr int kDefaultPmax = 32;
+// threads per CTA of the fast z passes (P = kFastZThreads / RA neighbouring pencils)
+constexpr int kFastZThreads = 256;
 
 // Phases of a band solve timed by the tracer (bloch_plan_trace).
 enum TracePhase { TR_PCG_SUB = 0, TR_PCG_LZ, TR_RES32, TR_RES64, TR_ORTHO, TR_PROJECT, TR_SPAN, TR_WALL, TR_NPHASE };
