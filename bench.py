@@ -30,11 +30,11 @@ FALLBACK_HBM = 6800.0
 KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0}   # algorithmic bytes per voxel, 5-pass chain
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the five passes) per system of the
 # FP32 fast-pass K-apply at 128^3, from one ncu capture of a 4-system launch (1845.6 MB read +
-# 1562.1 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
+# 1550.9 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
 # to `sources_sha256` (fpasses.cuh, fft.cuh, common.cuh in that order); otherwise traffic is null.
 KAPPLY_TRAFFIC = {"grid": (128, 128, 128), "precision": 1, "fft_variant": 0,
-                  "bytes_per_system": 3407.7e6 / 4,
-                  "sources_sha256": "6936885bf7a0de125b594791eddc73d59ed166e5b8ce26d9b3a219aaed132cff"}
+                  "bytes_per_system": 3396.5e6 / 4,
+                  "sources_sha256": "9455e1d962ad0ae4dbb7acd9413840e5605b0182f8136f654b9ceb46b4397061"}
 
 
 def parse():
