@@ -924,6 +924,7 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
                 double c = pl->C0V[vi[i][j] * 6 + vi[k][l]];
                 if (j != l) c += pl->C0V[vi[i][l] * 6 + vi[k][j]];
                 pl->pc.a[a][m] = c / pl->Cref;
+                pl->pc.af[a][m] = (float)pl->pc.a[a][m];
             }
         }
     }

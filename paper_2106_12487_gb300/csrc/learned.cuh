@@ -70,7 +70,7 @@ __device__ __forceinline__ void acoustic3(const PrecondCoef& pc, T qx, T qy, T q
     for (int i = 0; i < 6; ++i) {
         T s = 0;
 #pragma unroll
-        for (int j = 0; j < 6; ++j) s = fma(T(pc.a[i][j]), m[j], s);
+        for (int j = 0; j < 6; ++j) s = fma(pcoef<T>(pc, i, j), m[j], s);
         p6[i] = s;
     }
     P[0][0] = p6[0];

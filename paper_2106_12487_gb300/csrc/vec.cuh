@@ -14,7 +14,12 @@ namespace bloch {
 // monomials (qx^2, qy^2, qz^2, qy qz, qx qz, qx qy), from the scaled C0.
 struct PrecondCoef {
     double a[6][6];
+    float af[6][6];   // the same coefficients rounded once to FP32 (FP32 kernels read these:
+                      // no FP64 -> FP32 conversion per voxel)
 };
+template <typename T> __device__ __forceinline__ T pcoef(const PrecondCoef& pc, int i, int j);
+template <> __device__ __forceinline__ float pcoef<float>(const PrecondCoef& pc, int i, int j) { return pc.af[i][j]; }
+template <> __device__ __forceinline__ double pcoef<double>(const PrecondCoef& pc, int i, int j) { return pc.a[i][j]; }
 
 // Per-system CG scalars (device resident).
 struct CGSys {
@@ -78,7 +83,7 @@ __device__ __forceinline__ void green_apply(const PrecondCoef& pc, T qx, T qy, T
     for (int i = 0; i < 6; ++i) {
         T s = 0;
 #pragma unroll
-        for (int j = 0; j < 6; ++j) s = fma(T(pc.a[i][j]), m[j], s);
+        for (int j = 0; j < 6; ++j) s = fma(pcoef<T>(pc, i, j), m[j], s);
         P[i] = s;
     }
     const T a = P[0], bq = P[1], c = P[2], d = P[3], e = P[4], f = P[5];
