@@ -180,6 +180,23 @@ bloch_status bloch_apply_K(bloch_plan* plan, int32_t nb, const double* k, int32_
                            const void* u, void* Ku);
 
 /*
+ * Stiffness operator in the real-space basis: Ku = F^-1 A_k F u, the
+ * sequence of Section 3.2 spelled out on grid values of the periodic part of
+ * the Bloch displacement -- forward 3D FFT of the three components, Eq.
+ * (hatA) in Fourier space, inverse 3D FFT.  F is the unnormalised DFT
+ * (exp(-i xi.x) over the voxel centres' grid) and F^-1 carries 1/V, so
+ * bloch_apply_K(F u) = F bloch_apply_K_real(u).
+ *   k, precision  as bloch_apply_K
+ *   u             device, nb x 3 x V complex, real-space grid values; not modified
+ *   Ku            device, nb x 3 x V complex; may not alias u
+ * Enqueued on the plan's stream.  Scratch: the operator workspace of
+ * bloch_apply_K plus 9 x V complex per vector of solver workspace, held by
+ * the plan and grown on demand.  Errors as bloch_apply_K.
+ */
+bloch_status bloch_apply_K_real(bloch_plan* plan, int32_t nb, const double* k, int32_t precision,
+                                const void* u, void* Ku);
+
+/*
  * Mass operator, Eq. (hatM): Mu = F{rho(x) F^-1 u} on nb Fourier-space vectors.
  * With a uniform density this is exactly rho*u (F F^-1 = I) and costs one
  * scaling; otherwise three inverse and three forward 3D FFTs per vector.

@@ -28,7 +28,7 @@ EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", 
             "bloch_apply_K_noalloc", "bloch_lp_num_params", "bloch_lp_create", "bloch_lp_destroy", "bloch_lp_params",
             "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train", "bloch_lp_num_blocks", "bloch_lp_export_block",
             "bloch_plan_set_preconditioner", "bloch_plan_autotune",
-            "bloch_plan_trace"]
+            "bloch_plan_trace", "bloch_apply_K_real"]
 
 
 class BlochError(RuntimeError):
@@ -94,6 +94,7 @@ def lib():
     L.bloch_plan_destroy.argtypes = [VP]
     L.bloch_plan_destroy.restype = None
     L.bloch_apply_K.argtypes = [VP, I32, P(D), I32, VP, VP]
+    L.bloch_apply_K_real.argtypes = [VP, I32, P(D), I32, VP, VP]
     L.bloch_apply_M.argtypes = [VP, I32, I32, VP, VP]
     L.bloch_apply_K_noalloc.argtypes = [VP, I32, P(D), VP, VP]
     L.bloch_apply_precond.argtypes = [VP, I32, P(D), I32, VP, VP]
@@ -126,7 +127,8 @@ def lib():
               "bloch_lp_export_block", "bloch_plan_set_preconditioner"]:
         getattr(L, f).restype = ctypes.c_int
     for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
-              "bloch_solve_bands", "bloch_host_gen_eig", "bloch_plan_autotune", "bloch_plan_trace"]:
+              "bloch_solve_bands", "bloch_host_gen_eig", "bloch_plan_autotune", "bloch_plan_trace",
+              "bloch_apply_K_real"]:
         getattr(L, f).restype = ctypes.c_int
     _LIB = L
     return L
@@ -241,6 +243,15 @@ class Plan:
         kv = self._kv(k, nb)
         _check(lib().bloch_apply_K(self.handle, nb, _dptr(kv, ctypes.c_double), prec,
                                    _tensor_ptr(u, prec, nb * 3 * self.V), _tensor_ptr(out, prec, nb * 3 * self.V)))
+        return out
+
+    def apply_K_real(self, k, u, out, precision: int | None = None):
+        """bloch_apply_K_real: the stiffness operator on real-space grid values."""
+        prec = self.precision if precision is None else precision
+        nb = u.numel() // (3 * self.V)
+        kv = self._kv(k, nb)
+        _check(lib().bloch_apply_K_real(self.handle, nb, _dptr(kv, ctypes.c_double), prec,
+                                        _tensor_ptr(u, prec, nb * 3 * self.V), _tensor_ptr(out, prec, nb * 3 * self.V)))
         return out
 
     def apply_K_noalloc(self, k, u, out):

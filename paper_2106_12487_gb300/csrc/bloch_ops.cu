@@ -123,6 +123,8 @@ static cudaError_t set_smem_attrs() {
     SETA(k_pass_x_stress<T>);
     SETA(k_pass_z_div<T>);
     SETA(k_pass_x_rho<T>);
+    SETA((k_pass_x<T, +1>));
+    SETA((k_pass_x<T, -1>));
 #undef SETA
     return cudaSuccess;
 }
@@ -478,6 +480,23 @@ void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out
     k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5, out_scale);
 }
 
+// In-place 3D FFT of nb three-component fields (DIR -1 forward, +1 inverse;
+// unnormalised), times out_scale: shared-memory passes along z, y and x.
+template <typename T, int DIR>
+static void launch_fft3(bloch_plan* pl, int nb, cplx_t<T>* W, T out_scale) {
+    const Geo& g = geo_of<T>(pl);
+    const TileCfg& t = tile_of<T>(pl);
+    const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,
+                    pyz = (long long)pl->Ny * pl->Nz;
+    dim3 gz((unsigned)((pxy + t.Pz2 - 1) / t.Pz2), nb * 3);
+    dim3 gy((unsigned)((pxz + t.Py2 - 1) / t.Py2), nb * 3);
+    dim3 gx((unsigned)((pyz + t.Px4 - 1) / t.Px4), nb);
+    pl->launches += 3;
+    k_pass_axis<T, DIR, 2><<<gz, 256, t.smem_z2, pl->stream>>>(W, W, tw_of<T>(pl, 2), g, t.Pz2, T(1));
+    k_pass_axis<T, DIR, 1><<<gy, 256, t.smem_y2, pl->stream>>>(W, W, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    k_pass_x<T, DIR><<<gx, 256, t.smem_x4, pl->stream>>>(W, tw_of<T>(pl, 0), g, t.Px4, out_scale);
+}
+
 template <typename T>
 void launch_M(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale) {
     const long long n = (long long)nb * 3 * pl->V;
@@ -742,6 +761,20 @@ INST(double)
 using namespace bloch;
 
 // ============================================================== C ABI
+template <typename T>
+static bloch_status apply_K_real_impl(bloch_plan* pl, int nb, const double* k, const cplx_t<T>* u, cplx_t<T>* Ku) {
+    bloch_status st = ensure_cg<T>(pl, nb);
+    if (st != BLOCH_OK) return st;
+    if ((st = set_k<T>(pl, nb, k)) != BLOCH_OK) return st;
+    Workspace<T>& w = ws_of<T>(pl);
+    BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(w.Ap, u, sizeof(cplx_t<T>) * (size_t)nb * 3 * pl->V,
+                                         cudaMemcpyDeviceToDevice, pl->stream));
+    launch_fft3<T, -1>(pl, nb, w.Ap, T(1));                       // u^ = F u
+    launch_K<T>(pl, nb, w.Ap, Ku, T(pl->Kscale));                 // A_k u^
+    launch_fft3<T, +1>(pl, nb, Ku, T(1.0 / (double)pl->V));       // F^-1
+    return BLOCH_OK;
+}
+
 extern "C" {
 
 void bloch_default_options(bloch_options* opt) {
@@ -1056,6 +1089,26 @@ bloch_status bloch_apply_K(bloch_plan* pl, int32_t nb, const double* k, int32_t 
         if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
         launch_K<double>(pl, nb, (const double2*)u, (double2*)Ku, pl->Kscale);
     }
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    if (pl->pending != BLOCH_OK) {
+        const bloch_status p = pl->pending;
+        pl->pending = BLOCH_OK;
+        return p;
+    }
+    return BLOCH_OK;
+}
+
+bloch_status bloch_apply_K_real(bloch_plan* pl, int32_t nb, const double* k, int32_t precision, const void* u,
+                                void* Ku) {
+    bloch_status st = check_common(pl, nb, precision);
+    if (st != BLOCH_OK) return st;
+    if (!k || !u || !Ku) return set_error(BLOCH_EINVAL, "NULL argument");
+    if (u == Ku) return set_error(BLOCH_EINVAL, "Ku may not alias u");
+    if (precision == BLOCH_FP32)
+        st = apply_K_real_impl<float>(pl, nb, k, (const float2*)u, (float2*)Ku);
+    else
+        st = apply_K_real_impl<double>(pl, nb, k, (const double2*)u, (double2*)Ku);
+    if (st != BLOCH_OK) return st;
     BLOCH_CUDA_CHECK_RET(cudaGetLastError());
     if (pl->pending != BLOCH_OK) {
         const bloch_status p = pl->pending;

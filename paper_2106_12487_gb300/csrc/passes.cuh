@@ -59,7 +59,7 @@ __device__ __forceinline__ int pad_even(int n) { return (n + 1) & ~1; }
 
 // ---------------------------------------------------------------- pass 1
 template <typename T>
-__global__ void __launch_bounds__(256) k_pass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
+__global__ void __launch_bounds__(256, (sizeof(T) == 8) ? 2 : 1) k_pass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
                                                        const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
                                                        Geo g, int P) {
     using C = cplx_t<T>;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) k_pass_axis(const cplx_t<T>* in, cplx_t<T
 // ---------------------------------------------------------------- pass 3
 // Rows along x; all six strain components of P rows in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
+__global__ void __launch_bounds__(256, (sizeof(T) == 8) ? 2 : 1) k_pass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
                                                        const T* __restrict__ Ctab,
                                                        const cplx_t<T>* __restrict__ twx, Geo g, int P) {
     using C = cplx_t<T>;
@@ -359,6 +359,49 @@ __global__ void __launch_bounds__(256) k_pass_x_rho(cplx_t<T>* W, const int32_t*
     for (int e = tid; e < 3 * NP; e += nthr) {
         const int c = e / NP, r = e - c * NP, p = r / N, n = r - p * N;
         if (p < nr) Wb[(size_t)c * g.V + (size_t)(r0 + p) * N + n] = buf[c][r];
+    }
+}
+
+// ------------------------------------------- plain transform along x
+// 1D FFT (DIR -1 forward, +1 inverse, unnormalised) of the three components
+// of nb systems along x, in place, times out_scale; rows are contiguous, P
+// rows per CTA, blockIdx.y = system.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) k_pass_x(cplx_t<T>* W, const cplx_t<T>* __restrict__ twx, Geo g, int P,
+                                                T out_scale) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int N = g.Nx;
+    const int NP = N * P;
+    C* tw = sm;
+    C* s0 = tw + pad_even(N);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int b = blockIdx.y;
+    const long long rows = (long long)g.Ny * g.Nz;
+    const long long r0 = (long long)blockIdx.x * P;
+    const int nr = (int)min((long long)P, rows - r0);
+    C* Wb = W + (size_t)b * 3 * g.V;
+    const C zero = mk(T(0), T(0));
+    for (int i = tid; i < N; i += nthr) tw[i] = twx[i];
+    for (int e = tid; e < 3 * NP; e += nthr) {
+        const int c = e / NP, r = e - c * NP, p = r / N, n = r - p * N;
+        s0[e] = (p < nr) ? Wb[(size_t)c * g.V + (size_t)(r0 + p) * N + n] : zero;
+    }
+    __syncthreads();
+    C* buf[3];
+    C* wk = s0 + 3 * NP;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        C* a = s0 + c * NP;
+        C* res = fft_tile<DIR, false>(a, wk, g.ax[0], P, N, tw, tid, nthr);
+        if (res == wk) wk = a;
+        buf[c] = res;
+    }
+    __syncthreads();
+    for (int e = tid; e < 3 * NP; e += nthr) {
+        const int c = e / NP, r = e - c * NP, p = r / N, n = r - p * N;
+        if (p < nr) Wb[(size_t)c * g.V + (size_t)(r0 + p) * N + n] = cscale(buf[c][r], out_scale);
     }
 }
 

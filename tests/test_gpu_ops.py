@@ -197,3 +197,22 @@ def test_invalid_arguments_on_device(B):
     assert e.value.status == 6
     with pytest.raises(TypeError):
         plan.apply_K([0, 0, 0], u.to(torch.complex64), torch.zeros_like(u))
+
+
+@pytest.mark.parametrize("grid", [(16, 16, 16), (24, 20, 15), (32, 16, 64), (1, 1, 1)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_K_real_basis(B, grid, prec):
+    """Real-space basis: F^-1 A_k F u against the oracle's Fourier-space
+    operator wrapped in numpy's forward / inverse FFT (same conventions)."""
+    p = synth.small_polycrystal(grid, 5, 13)
+    med = O.Medium.from_problem(p)
+    plan = B.Plan.from_problem(p, precision=prec)
+    ks = np.array([[0.3, -0.2, 0.7], [0.0, 0.9, 0.1]]) * math.pi / 1e-3
+    u = synth.random_field(grid, 19, batch=2)
+    out = to_dev(np.zeros_like(u), prec)
+    plan.apply_K_real(ks, to_dev(u, prec), out)
+    got = out.cpu().numpy()
+    ax = (-3, -2, -1)
+    for b in range(2):
+        want = np.fft.ifftn(O.apply_K(med, ks[b], np.fft.fftn(u[b], axes=ax)), axes=ax)
+        assert rel(got[b], want) < TOL[prec]
