@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--max-outer", type=int, default=100, help="sweep cap (profiling runs bound it)")
     ap.add_argument("--kapply-only", action="store_true", help="time only the K-apply chain")
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
+    ap.add_argument("--kapply-prec", default="form", choices=["form", "fp32", "fp64"],
+                    help="with --kapply-only: precision of the timed chain (form = the form's), with --fft-variant "
+                         "taken as given")
     ap.add_argument("--fft-variant", type=int, default=0, choices=[0, 1, 2],
                     help="0: two-stage register FFT passes, 1: shared-memory Stockham passes, 2: cuFFT baseline")
     ap.add_argument("--precond", default="green", choices=["green", "learned"],
@@ -330,6 +333,11 @@ def run_ours(args, ws, rank, local):
         lp, lp_info = train_learned(args)
         bloch.set_preconditioner(plan, lp)
     if args.kapply_only:
+        if args.kapply_prec != "form":
+            plan.close()
+            prec = bloch.FP64 if args.kapply_prec == "fp64" else bloch.FP32
+            opt = dict(opt, precision=prec, fft_variant=args.fft_variant)
+            plan = bloch.Plan.from_problem(p, **opt)
         roof = kapply_roofline(plan, p, prec, args.kapply_nb, opt["fft_variant"])
         if rank == 0:
             print(json.dumps({"kapply": roof}), flush=True)
