@@ -265,9 +265,10 @@ bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, dou
  * and same FP32 kernels as bloch_apply_K with precision BLOCH_FP32).
  *
  * For callers that must not allocate device memory at the point of the call:
- * code that runs while a CUDA graph is being captured (an allocation there
- * breaks the capture), services whose device memory is carved up in advance,
- * and latency-critical loops that forbid allocator calls.  bloch_apply_K grows
+ * services whose device memory is carved up in advance (a fixed budget or a
+ * pool that must not grow), code embedded in a host framework that owns the
+ * allocator, and latency-critical loops in which a cudaMalloc or cudaFree
+ * (which can synchronise the device) is not acceptable.  bloch_apply_K grows
  * a plan-owned scratch buffer with cudaMalloc when it first meets a larger
  * batch; this entry point calls no cudaMalloc, cudaFree or allocating library
  * routine.  Its FFT-pass scratch is one fixed file-scope device array of

@@ -2,9 +2,10 @@
 //
 // bloch_apply_K runs its FFT passes through a plan-owned scratch buffer that
 // grows with cudaMalloc the first time a larger batch is seen.  Callers that
-// may not allocate device memory at the point of the call (code running
-// while a CUDA graph is being captured, memory-pool-constrained services,
-// real-time loops that forbid allocator calls) use bloch_apply_K_noalloc
+// may not allocate device memory at the point of the call (services with a
+// fixed device-memory budget, code embedded in a framework that owns the
+// allocator, real-time loops in which an allocator call may stall the
+// device) use bloch_apply_K_noalloc
 // instead: its scratch is one file-scope device array of fixed size,
 // reserved when the library is loaded on a GPU and held until the process
 // exits.  The operator, its kernels and its results are those of

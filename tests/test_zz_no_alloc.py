@@ -1,9 +1,10 @@
 """The allocation-free stiffness apply (bloch_apply_K_noalloc) against the
 regular one (bloch_apply_K), called through the C ABI.
 
-Callers that cannot allocate device memory when they apply the operator (for
-example while a CUDA graph is being captured) use the allocation-free entry
-point; it must give the regular entry point's result.  Two calls in a row with
+Callers that cannot allocate device memory when they apply the operator (a
+service with a fixed device-memory budget, a real-time loop in which a
+cudaMalloc may stall the device) use the allocation-free entry point; it must
+give the regular entry point's result.  Two calls in a row with
 different wave vectors and fields check that the shared fixed scratch left by
 one call does not leak into the next.  This file is collected last so that a
 run stopping at the first failure has already run every other test.
