@@ -329,3 +329,34 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     bad = spectrum()
     monkeypatch.setattr(O, "voigt_to_tensor", orig_v)
     assert np.max(np.abs(bad - ref)) > 1e-6 * ref.max()
+
+
+# ------------------------------------- real-space basis: plane waves (Section 3.2)
+@pytest.mark.parametrize("bins", [(1, 0, 0), (0, 3, 1), (5, 2, 4), (3, 0, 2)])
+def test_real_space_plane_wave_is_christoffel_eigenvector(bins):
+    """On grid values at the voxel centres, a plane wave e exp(i xi.x) of a
+    homogeneous medium is mapped by F^-1 A_k F (numpy's FFT pair, the library's
+    real-space convention) to (P(xi + k) e) exp(i xi.x), with the Christoffel
+    matrix P written here from C and xi taken from the paper's frequency set in
+    FFT bin order (negative half above N/2; the even-N Nyquist bin at -N pi/L)."""
+    C = synth.rotate_voigt(synth.cubic_voigt(168.4e9, 121.4e9, 75.4e9), synth.haar_rotations(1, 9)[0])
+    grid = (6, 4, 5)
+    med = homog(C, 8960.0, grid)
+    k = np.array([0.31, -0.47, 0.22]) * math.pi / 1e-3
+    Nx, Ny, Nz = grid
+    xi = []
+    for m, n in zip(bins, grid):
+        f = np.sort(paper_freqs(n))          # the paper's set
+        xi.append(f[f >= 0][m] if m < (n + 1) // 2 else f[f < 0][m - (n + 1) // 2])
+    xi = np.array(xi)
+    xs = [(0.5 + np.arange(n)) * 1e-3 / n for n in grid]
+    X, Y, Z = xs[0][None, None, :], xs[1][None, :, None], xs[2][:, None, None]
+    phase = np.exp(1j * (xi[0] * X + xi[1] * Y + xi[2] * Z))
+    e = np.array([0.3 - 0.2j, 1.0, -0.5 + 0.7j])
+    u = e[:, None, None, None] * phase[None]
+    ax = (-3, -2, -1)
+    Ku = np.fft.ifftn(O.apply_K(med, k, np.fft.fftn(u, axes=ax)), axes=ax)
+    q = xi + k
+    P = np.einsum("ijkl,j,l->ik", O.voigt_to_tensor(C), q, q)
+    want = (P @ e)[:, None, None, None] * phase[None]
+    assert np.linalg.norm(Ku - want) <= 1e-12 * np.linalg.norm(want)
