@@ -96,3 +96,31 @@ def test_host_gen_eig_degenerate_cluster(libb):
     lam, Q = bloch.host_gen_eig(K, np.eye(n))
     assert np.allclose(lam, [1, 1, 1, 2, 2, 5, 5, 5, 5], atol=1e-13)
     assert np.allclose(Q.conj().T @ Q, np.eye(n), atol=1e-13)
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """The ctypes mirrors of the header's structs (options, stats, tune
+    report, trace) have the C compiler's sizes and field offsets."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2106_12487_gb300 import bloch
+    structs = {"bloch_options": bloch.Options, "bloch_stats": bloch.Stats,
+               "bloch_tune_report": bloch.TuneReport, "bloch_trace": bloch.Trace}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bloch.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
