@@ -297,13 +297,6 @@ static void set_fast_attrs() {
     set_fast_attrs_n<T, 16, 16, false>();
 }
 
-// P for the fast y/z passes: 32 pencils (256 B rows in FP32), fewer if the axis has fewer
-static int fast_P(long long npen, int pmax) {
-    int P = pmax;
-    while (P > 1 && (long long)(P / 2) >= npen) P >>= 1;
-    return P;
-}
-
 template <typename T, int RA, int RB>
 static void fast_y(bloch_plan* pl, int DIR, int nb, cplx_t<T>* E) {
     const Geo& g = geo_of<T>(pl);
