@@ -45,9 +45,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rve128_g200")
     ap.add_argument("--form", default="chosen", choices=["chosen", "chosen-subspace", "plain"])
-    ap.add_argument("--k-per-step", type=int, default=4)
+    ap.add_argument("--k-per-step", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-path", action="store_true",
+                    help="skip the leg that solves the whole 64-point path in one bloch_solve_bands call")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the leg that times the plain FP64 cuFFT form on two 4-point batches")
     ap.add_argument("--max-outer", type=int, default=100, help="sweep cap (profiling runs bound it)")
     ap.add_argument("--kapply-only", action="store_true", help="time only the K-apply chain")
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
@@ -191,6 +195,92 @@ def oracle_applies_per_eigenpair():
     return float(g["oracle_cg_iters"]) / float(g["eigenpairs"]), "rve16_g8 oracle Lanczos"
 
 
+def _oracle_k_solve(task):
+    """Worker of the oracle baseline (spawned process): the oracle's band solve
+    (shift-invert Lanczos through ARPACK, Algorithm 2 PCG) of one wave vector
+    of a workload.  Returns (omega, wall s, process CPU s)."""
+    name, i, tol = task
+    from oracle import bloch_oracle as O
+    from paper_2106_12487_gb300 import synth
+    p = synth.workload(name)
+    med = O.Medium.from_problem(p)
+    t0, c0 = time.perf_counter(), time.process_time()
+    res = O.solve_bands(med, p.k_list[i:i + 1], p.n_bands, tol, tol, method="lanczos")
+    return res.omega[0].tolist(), time.perf_counter() - t0, time.process_time() - c0
+
+
+def _noop(_):
+    return 0
+
+
+def oracle_band_baseline(name="rve16_g8", tol=1e-10, one_core_k=5):
+    """The FP64 oracle as it stands, measured (not extrapolated) on a whole
+    small workload: every wave vector of `name` solved in a spawned process
+    pool over the host cores (one wave vector per process, one thread each),
+    plus one wave vector alone on one core.  Returns the two rates in
+    eigenpairs/s, the cores kept busy and the oracle's frequencies."""
+    import multiprocessing as mp
+    from paper_2106_12487_gb300 import synth
+    p = synth.workload(name)
+    nk = int(p.k_list.shape[0])
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    try:
+        nproc = max(1, min(nk, os.cpu_count() or 1))
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(nproc) as pool:
+            pool.map(_noop, range(nproc))          # interpreters started before the clock
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_k_solve, [(name, i, tol) for i in range(nk)], chunksize=1)
+            wall = time.perf_counter() - t0
+            one = pool.apply(_oracle_k_solve, ((name, one_core_k, tol),))
+    finally:
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    cpu = sum(r[2] for r in res)
+    omega = np.array([r[0] for r in res])
+    return {"workload": name, "grid": list(p.grid), "n_k": nk, "n_bands": int(p.n_bands), "tol": tol,
+            "all_cores": {"value": nk * p.n_bands / wall, "wall_s": wall, "processes": nproc,
+                          "cores": max(1, int(round(cpu / max(wall, 1e-9))))},
+            "one_core": {"value": p.n_bands / one[1], "wall_s": one[1], "k_index": one_core_k, "cores": 1},
+            "omega": omega}
+
+
+def gpu_band_same_config(name, omega_ref):
+    """Our band solve on the oracle-baseline workload, all its wave vectors in
+    one bloch_solve_bands call per form (FP64 plain form with our passes at the
+    oracle's tolerance; FP32 chosen form), CUDA events after one warm-up call;
+    max relative frequency difference to the oracle's."""
+    import torch
+    from paper_2106_12487_gb300 import bloch, synth
+    p = synth.workload(name)
+    out = {}
+    forms = {"fp64_plain": dict(precision=bloch.FP64, method=bloch.LANCZOS, tol_lin=1e-10, tol_eig=1e-10),
+             "chosen": dict(precision=bloch.FP32, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5,
+                            block=p.n_bands + 2, max_cg=500)}
+    stream = torch.cuda.current_stream()
+    for form, opt in forms.items():
+        plan = bloch.Plan.from_problem(p, **opt)
+        plan.solve_bands(p.k_list, p.n_bands, allow_nonconv=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        om, st, status = plan.solve_bands(p.k_list, p.n_bands, allow_nonconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1000.0
+        nz = omega_ref > 0
+        out[form] = {"value": p.k_list.shape[0] * p.n_bands / dt, "status": int(status),
+                     "max_rel_freq_diff_vs_oracle": float(np.max(np.abs(om[nz] / omega_ref[nz] - 1.0)))}
+        plan.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle (FP64 numpy) on the host cores, same workload and metric."""
     if rank != 0:
@@ -209,9 +299,9 @@ def run_reference(args, ws, rank):
     wall = time.perf_counter() - t0
     ta = float(np.mean(t_apply))
     value = 1.0 / (ta * a_per_pair)
-    sample = (f"{args.steps} x (1 PCG iteration + residual check) of the FP64 oracle at {p.grid} "
-              f"({ta:.2f} s per A_k apply); eigenpairs/s = 1/(s per apply x {a_per_pair:.1f} applies per "
-              f"eigenpair, {src})")
+    sample = (f"estimate, not a measured band solve: {args.steps} x (1 PCG iteration + residual check) of the "
+              f"FP64 oracle at {p.grid} ({ta:.2f} s per A_k apply, measured); eigenpairs/s = 1/(s per apply x "
+              f"{a_per_pair:.1f} applies per eigenpair, {src}); a 128^3 band solve of the oracle takes hours")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -357,12 +447,13 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    stats_all = []
+    stats_all, status_all = [], []
     launches0 = plan.kernel_launches
     ev0.record(stream)
     for s in range(args.steps):
-        _, st, _ = plan.solve_bands(kbatch(args.warmup + s), p.n_bands, allow_nonconv=True)
+        _, st, status = plan.solve_bands(kbatch(args.warmup + s), p.n_bands, allow_nonconv=True)
         stats_all.append(st)
+        status_all.append(int(status))
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -374,6 +465,8 @@ def run_ours(args, ws, rank, local):
     value = pairs / t
     cg = sum(s["cg_iterations"] for s in stats_all)
     kap = sum(s["k_applies"] for s in stats_all)
+    k_unconv = int(sum(s["k_unconverged"] for s in stats_all))
+    covered = sorted({i for s in range(args.steps) for i in k_indices(args.warmup + s, rank, ws, kps, nk)})
 
     roof = kapply_roofline(plan, p, prec, args.kapply_nb, opt["fft_variant"])
 
@@ -385,8 +478,61 @@ def run_ours(args, ws, rank, local):
         tr = plan.trace(False)
         phases = {k: round(v["ms"], 3) for k, v in tr.items()}
 
+    # config 3 as written: the whole path in one bloch_solve_bands call (warm plan)
+    path = None
+    if not args.no_path and ws == 1:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        om_path, st_path, status_path = plan.solve_bands(p.k_list, p.n_bands, allow_nonconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / 1000.0
+        path = {"n_k": int(nk), "value": nk * p.n_bands / tp, "ms": tp * 1000.0, "status": int(status_path),
+                "k_unconverged": int(st_path["k_unconverged"]),
+                "k_applies_per_eigenpair": st_path["k_applies"] / (nk * p.n_bands)}
+
+    # the plain FP64 form (the paper's method: shift-invert Lanczos, PCG 1e-10,
+    # cuFFT operator) on a near-Gamma and a mid-path batch, the chosen form on
+    # the same batches, and the largest frequency difference between the two
+    plain = None
+    if not args.no_plain and ws == 1 and args.form == "chosen":
+        batches = [[1, 2, 3, 4], [20, 21, 22, 23]]
+        popt = dict(precision=bloch.FP64, method=bloch.LANCZOS, tol_lin=1e-10, tol_eig=1e-10, max_cg=2000,
+                    max_outer=args.max_outer, fft_variant=2, cuda_graph=1)
+        pplan = bloch.Plan.from_problem(p, **popt)
+        tp = tc = 0.0
+        diff = 0.0
+        statuses = []
+        for bt in batches:
+            kb = p.k_list[bt]
+            for which, pl_ in (("plain", pplan), ("chosen", plan)):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                om, _, stt = pl_.solve_bands(kb, p.n_bands, allow_nonconv=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dt = e0.elapsed_time(e1) / 1000.0
+                statuses.append(int(stt))
+                if which == "plain":
+                    tp += dt
+                    om_plain = om
+                else:
+                    tc += dt
+                    diff = max(diff, float(np.max(np.abs(om / om_plain - 1.0))))
+        pplan.close()
+        npairs = sum(len(b) for b in batches) * p.n_bands
+        plain = {"form": "FP64, shift-invert Lanczos, PCG 1e-10, cuFFT operator (fft_variant 2)",
+                 "k_indices": batches, "value": npairs / tp, "chosen_same_batches": npairs / tc,
+                 "chosen_over_plain": tp / tc, "max_rel_freq_diff": diff, "statuses": statuses,
+                 "unit": "eigenpairs/s"}
+
     # end to end through the public API with host buffers: plan upload from
-    # host arrays, band solve, frequencies back to host
+    # host arrays, then the same k batches as the timed region (host k lists
+    # in, host frequencies out)
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
@@ -394,39 +540,60 @@ def run_ours(args, ws, rank, local):
         plan2 = bloch.Plan.from_problem(p, **opt)
         if lp is not None:
             bloch.set_preconditioner(plan2, lp)
-        om, _, _ = plan2.solve_bands(kbatch(args.warmup), p.n_bands, allow_nonconv=True)
+        d2h = 0
+        for s in range(args.steps):
+            om, _, _ = plan2.solve_bands(kbatch(args.warmup + s), p.n_bands, allow_nonconv=True)
+            d2h += om.nbytes
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
+        te = max_over_ranks(ws, te)
         plan2.close()
-        h2d = p.grain_ids.nbytes + p.C_per_grain.nbytes + p.rho.nbytes + kps * 3 * 8
-        e2e = {"value": kps * p.n_bands / te, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(om.nbytes)}
+        h2d = p.grain_ids.nbytes + p.C_per_grain.nbytes + p.rho.nbytes + args.steps * kps * 3 * 8
+        e2e = {"value": pairs / te, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d // args.steps),
+               "d2h_bytes_per_step": int(d2h // args.steps),
+               "note": "plan creation from host arrays once, then the timed region's k batches"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        ta, threads = oracle_sample(p, 2)
-        a_per_pair, src = oracle_applies_per_eigenpair()
-        cpu = {"value": 1.0 / (ta * a_per_pair), "unit": "eigenpairs/s", "cores": threads, "kind": "oracle",
-               "sample": f"2 PCG iterations + residual of the FP64 oracle at {p.grid} ({ta:.2f} s per A_k apply), "
-                         f"scaled by {a_per_pair:.1f} oracle applies per eigenpair ({src})"}
+        ob = oracle_band_baseline()
+        same = gpu_band_same_config(ob["workload"], ob["omega"])
+        ta, threads = oracle_sample(p, 1)
+        a_per_pair = kap / (args.steps * kps * p.n_bands)
+        cpu = {"value": ob["all_cores"]["value"], "unit": "eigenpairs/s", "cores": ob["all_cores"]["cores"],
+               "kind": "oracle",
+               "sample": (f"measured, not extrapolated: the FP64 oracle's whole band solve of {ob['workload']} "
+                          f"({ob['n_k']} k x {ob['n_bands']} bands, grid {ob['grid']}, tol {ob['tol']}), one wave "
+                          f"vector per spawned process on {ob['all_cores']['processes']} processes, "
+                          f"{ob['all_cores']['wall_s']:.1f} s wall; that config differs from the GPU's 128^3 "
+                          f"workload (see same_config_gpu for ours on it)"),
+               "one_core": ob["one_core"], "same_config_gpu": same,
+               "workload_128_estimate": {
+                   "value": 1.0 / (ta * a_per_pair), "s_per_apply": ta,
+                   "note": "estimate, not a measurement: oracle seconds per A_k apply at 128^3 times the "
+                           "K-applies per eigenpair of the timed GPU form"}}
 
     if rank == 0:
+        valid = k_unconv == 0 and all(st == 0 for st in status_all)
         line = {"metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == bloch.FP32 else "f64",
-                "data": "synthetic",
+                "data": "synthetic", "valid": valid,
                 "config": {"workload": args.workload, "grid": list(p.grid), "grains": int(p.G),
                            "n_bands": p.n_bands, "n_k_path": int(nk), "k_per_step": kps,
+                           "k_covered": len(covered),
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
                            "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"],
-                           "tensor_gram": opt.get("tensor_gram", 0), "block": opt.get("block", 0), "method": "subspace" if opt["method"] else "lanczos",
+                           "tensor_gram": opt.get("tensor_gram", 0), "block": opt.get("block", 0),
+                           "method": "subspace" if opt["method"] else "lanczos",
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+                "solve_status": {"per_step": status_all, "k_unconverged": k_unconv},
                 "solver": {"cg_iterations": cg, "k_applies": kap,
                            "outer_iterations": sum(s["outer_iterations"] for s in stats_all),
                            "max_rel_residual": max(s["max_rel_residual"] for s in stats_all),
                            "k_applies_per_eigenpair": kap / (args.steps * kps * p.n_bands)},
+                "path_one_call": path, "plain_baseline": plain,
                 "phases_ms": phases, "precond": lp_info}
         print(json.dumps(line), flush=True)
     plan.close()

@@ -138,6 +138,9 @@ typedef struct {
     int64_t outer_iterations;  /* subspace sweeps or Lanczos restarts                */
     double max_rel_residual;   /* max over bands of ||A u - lam M u|| / ||A u|| (FP64) */
     double seconds;            /* wall time of the call                              */
+    int64_t k_unconverged;     /* wave vectors that reached the sweep/restart cap
+                                  before the tolerance (their omega are the last
+                                  estimates; the call returns BLOCH_ENOTCONV_EIG) */
 } bloch_stats;
 
 /* Fill *opt with the defaults above. */
@@ -261,8 +264,9 @@ bloch_status bloch_solve_bands(bloch_plan* plan, int32_t n_k, const double* k_li
 bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, double* lam, double* Q);
 
 /*
- * Allocation-free stiffness apply (no counterpart in the paper; same operator
- * and same FP32 kernels as bloch_apply_K with precision BLOCH_FP32).
+ * Allocation-free stiffness apply (no counterpart in the paper; same operator,
+ * same FP32 pass kernels and launch shapes as bloch_apply_K with precision
+ * BLOCH_FP32 and fft_variant 0).
  *
  * For callers that must not allocate device memory at the point of the call:
  * services whose device memory is carved up in advance (a fixed budget or a
@@ -272,12 +276,18 @@ bloch_status bloch_host_gen_eig(int32_t n, const double* K, const double* M, dou
  * a plan-owned scratch buffer with cudaMalloc when it first meets a larger
  * batch; this entry point calls no cudaMalloc, cudaFree or allocating library
  * routine.  Its FFT-pass scratch is one fixed file-scope device array of
- * 97 MiB, reserved on every GPU that loads the library and held until the
- * process exits.
+ * 97 MiB.  The array is placed on a GPU when the library's module holding it
+ * is loaded there: with CUDA's default lazy module loading that happens at
+ * the first call of this entry point on the device, so that first call does
+ * take the 97 MiB (and can fail with BLOCH_ENOMEM / BLOCH_ECUDA if the device
+ * is full).  Make one warm-up call per device before fixing the process's
+ * device-memory budget; from then on the array stays until the process exits.
  *   plan   an existing plan (created beforehand; creation itself allocates)
- *   nb     systems, with nb * Nx*Ny*Nz <= 2097152 (one 128^3 system, eight
- *          64^3 systems) and (Nx+Ny+Nz+6) * nb <= 262144; larger requests
- *          return BLOCH_EINVAL with the limit in bloch_last_error()
+ *   nb     systems, 1 <= nb <= 10922, with nb * Nx*Ny*Nz <= 2097152 (one
+ *          128^3 system, eight 64^3 systems) and (Nx+Ny+Nz+6) * nb <= 262144;
+ *          larger requests return BLOCH_EINVAL with the limit in
+ *          bloch_last_error() and enqueue nothing
+ *   The plan must use fft_variant 0 (else BLOCH_EUNSUPPORTED, nothing enqueued).
  *   k      host, nb x 3 wave vectors (rad/m)
  *   u, Ku  device, nb x 3 x V float2 each, as in bloch_apply_K (Ku may not alias u)
  * The first call on a device does a one-time set-up on that device (looks up
@@ -327,6 +337,23 @@ bloch_status bloch_lp_params(bloch_lp* lp, double* get, const double* set);
  */
 bloch_status bloch_lp_collect(bloch_lp* lp, bloch_plan* plan, int32_t n_k, const double* k_list, int32_t n_rhs,
                               int32_t n_iters, uint64_t seed);
+
+/*
+ * Add one data block from caller-supplied pairs (the caller's own CG runs, or
+ * any residual/error pairs of the plan's operator): for each pair j the
+ * per-Fourier-voxel moments A = Re r_j r_j^H, B = sym Re r_j e_j^H (six
+ * entries each, order xx yy zz yz xz xy) and c = |e_j|^2, each weighted by
+ * 1/||r_j||_2^2 (pairs with r_j = 0 are skipped), are summed into a new block.
+ * The block's wave vector (the network's q features) is k.
+ *   k        host, 3 (rad/m)
+ *   n_pairs  1 <= n_pairs <= 10922
+ *   r, e     device, n_pairs x 3 x V float2 each, Fourier basis of the plan's grid
+ * Runs on the plan's stream and synchronises it; grows the plan's PCG
+ * workspace to n_pairs systems.  Errors: BLOCH_EINVAL, BLOCH_ENONFINITE (k),
+ * BLOCH_ENOMEM, BLOCH_ECUDA.
+ */
+bloch_status bloch_lp_add_pairs(bloch_lp* lp, bloch_plan* plan, const double* k, int32_t n_pairs, const void* r,
+                                const void* e);
 
 /* Loss (mean over recorded iterates) and its gradient (host, bloch_lp_num_params() values; may be NULL). */
 bloch_status bloch_lp_loss_grad(bloch_lp* lp, double* loss, double* grad);

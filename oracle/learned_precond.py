@@ -112,6 +112,31 @@ def sym6_to_mat(a: np.ndarray) -> np.ndarray:
     return M
 
 
+def moments(r: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """Per-Fourier-voxel moments of residual/error pairs, the sufficient
+    statistics of the loss above: for pairs j (r, e shaped (n, 3, Nz, Ny, Nx),
+    complex) with weights w_j = 1/||r_j||^2 (pairs with r_j = 0 skipped),
+        A = sum_j w_j Re(r_j r_j^H),  B = sum_j w_j sym Re(r_j e_j^H),  c = sum_j w_j |e_j|^2,
+    returned as (V, 13): A and B in the order (xx, yy, zz, yz, xz, xy), then c.
+    With Z real symmetric, ||Z r - e||^2 = tr(Z Z A) - 2 tr(Z B) + c per voxel."""
+    n = r.shape[0]
+    V = int(np.prod(r.shape[2:]))
+    rv = r.reshape(n, 3, V)
+    ev = e.reshape(n, 3, V)
+    out = np.zeros((V, 13))
+    pairs = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+    for j in range(n):
+        nr2 = float(np.vdot(rv[j], rv[j]).real)
+        if nr2 == 0.0:
+            continue
+        w = 1.0 / nr2
+        for t, (a, b) in enumerate(pairs):
+            out[:, t] += w * (rv[j, a] * np.conj(rv[j, b])).real
+            out[:, 6 + t] += w * 0.5 * ((rv[j, a] * np.conj(ev[j, b])).real + (rv[j, b] * np.conj(ev[j, a])).real)
+        out[:, 12] += w * np.sum(np.abs(ev[j]) ** 2, axis=0)
+    return out
+
+
 def loss(theta: np.ndarray, H: int, blocks) -> float:
     """blocks: iterable of dicts with q (n, 3), A (n, 6), B (n, 6), c (n,),
     C0 (3, 3, 3, 3) scaled, Nmax."""

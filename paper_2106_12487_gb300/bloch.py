@@ -28,7 +28,7 @@ EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", 
             "bloch_apply_K_noalloc", "bloch_lp_num_params", "bloch_lp_create", "bloch_lp_destroy", "bloch_lp_params",
             "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train", "bloch_lp_num_blocks", "bloch_lp_export_block",
             "bloch_plan_set_preconditioner", "bloch_plan_autotune",
-            "bloch_plan_trace", "bloch_apply_K_real"]
+            "bloch_plan_trace", "bloch_apply_K_real", "bloch_lp_add_pairs"]
 
 
 class BlochError(RuntimeError):
@@ -70,7 +70,8 @@ class TuneReport(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("cg_iterations", ctypes.c_int64), ("linear_solves", ctypes.c_int64),
                 ("k_applies", ctypes.c_int64), ("outer_iterations", ctypes.c_int64),
-                ("max_rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("max_rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("k_unconverged", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -115,6 +116,7 @@ def lib():
     L.bloch_lp_destroy.restype = None
     L.bloch_lp_params.argtypes = [VP, P(D), P(D)]
     L.bloch_lp_collect.argtypes = [VP, VP, I32, P(D), I32, I32, U64]
+    L.bloch_lp_add_pairs.argtypes = [VP, VP, P(D), I32, VP, VP]
     L.bloch_lp_loss_grad.argtypes = [VP, P(D), P(D)]
     L.bloch_lp_train.argtypes = [VP, I32, D, P(D)]
     L.bloch_lp_num_blocks.argtypes = [VP]
@@ -123,7 +125,8 @@ def lib():
     L.bloch_plan_set_preconditioner.argtypes = [VP, VP]
     L.bloch_plan_autotune.argtypes = [VP, I32, I32, P(TuneReport)]
     L.bloch_plan_trace.argtypes = [VP, I32, P(Trace)]
-    for f in ["bloch_lp_create", "bloch_lp_params", "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train",
+    for f in ["bloch_lp_create", "bloch_lp_params", "bloch_lp_collect", "bloch_lp_add_pairs", "bloch_lp_loss_grad",
+              "bloch_lp_train",
               "bloch_lp_export_block", "bloch_plan_set_preconditioner"]:
         getattr(L, f).restype = ctypes.c_int
     for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
@@ -352,6 +355,14 @@ class LearnedPrecond:
         kl = np.ascontiguousarray(np.asarray(k_list, dtype=np.float64).reshape(-1, 3))
         _check(lib().bloch_lp_collect(self.handle, plan.handle, kl.shape[0], _dptr(kl, ctypes.c_double),
                                       int(n_rhs), int(n_iters), int(seed)))
+
+    def add_pairs(self, plan: Plan, k, r, e):
+        """bloch_lp_add_pairs: one data block from caller-supplied (r_j, e_j) pairs
+        (complex64 CUDA tensors of n_pairs x 3 x V values, Fourier basis)."""
+        n = r.numel() // (3 * plan.V)
+        kv = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(3))
+        _check(lib().bloch_lp_add_pairs(self.handle, plan.handle, _dptr(kv, ctypes.c_double), n,
+                                        _tensor_ptr(r, FP32, n * 3 * plan.V), _tensor_ptr(e, FP32, n * 3 * plan.V)))
 
     def loss_grad(self):
         L = np.zeros(1)

@@ -34,6 +34,45 @@ namespace bloch {
 
 using cd = std::complex<double>;
 
+bloch_status plan_solver_buf(bloch_plan* pl, int pool, int idx, size_t bytes, void** out) {
+    auto& v = pl->solver_bufs[pool];
+    if ((int)v.size() <= idx) v.resize(idx + 1);
+    bloch_plan::SolverBuf& b = v[idx];
+    bytes = std::max<size_t>(bytes, 256);
+    if (b.bytes < bytes) {
+        cudaStreamSynchronize(pl->stream);   // an earlier solve may still use the old buffer
+        if (b.p) {
+            cudaFree(b.p);
+            pl->device_bytes -= b.bytes;
+        }
+        b.p = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            b.p = nullptr;
+            return set_cuda_error(e, "cudaMalloc (eigensolver block)");
+        }
+        b.bytes = bytes;
+        pl->device_bytes += bytes;
+    }
+    *out = b.p;
+    return BLOCH_OK;
+}
+
+size_t plan_solver_bytes(const bloch_plan* pl) {
+    size_t t = pl->handoff_bytes;
+    for (const auto& v : pl->solver_bufs)
+        for (const auto& b : v) t += b.bytes;
+    return t;
+}
+
+void plan_solver_release(bloch_plan* pl) {
+    for (auto& v : pl->solver_bufs) {
+        for (auto& b : v) cudaFree(b.p);
+        v.clear();
+    }
+}
+
 // ====================================================================
 // Small dense Hermitian eigenproblems (host, FP64)
 // ====================================================================
@@ -317,17 +356,10 @@ struct Subspace {
     // segments: slot s walks order[seg_next[s] .. seg_end[s]) when warm starting
     std::vector<size_t> seg_next, seg_end;
 
-    std::vector<void*> allocs;
-    ~Subspace() {
-        cudaStreamSynchronize(pl->stream);
-        for (void* p : allocs) cudaFree(p);
-    }
+    int nalloc = 0;   // buffers taken from the plan's pool 0
     template <typename X>
     bloch_status alloc(X** p, size_t n_el) {
-        cudaError_t e = cudaMalloc((void**)p, n_el * sizeof(X));
-        if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (eigensolver block)");
-        allocs.push_back(*p);
-        return BLOCH_OK;
+        return plan_solver_buf(pl, 0, nalloc++, n_el * sizeof(X), (void**)p);
     }
 
     C* vec(C* base, int slot, int i = 0) const { return base + ((size_t)slot * q + i) * n3; }
@@ -560,7 +592,10 @@ struct Subspace {
         for (int i = 0; i < sl.n_eff; ++i) om[b + i] = std::sqrt(std::max(sl.lam[i], 0.0) * lam_scale);
         st->outer_iterations += sl.sweeps;
         st->max_rel_residual = std::max(st->max_rel_residual, sl.err2);
-        if (!converged) any_unconverged = true;
+        if (!converged) {
+            any_unconverged = true;
+            st->k_unconverged += 1;
+        }
         if (vecs_out) {
             C* out = (C*)vecs_out + (size_t)sl.kidx * n_bands * n3;
             if (sl.gamma) {
@@ -834,6 +869,7 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     // slots: from the options or from free memory
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
+    freeb += plan_solver_bytes(pl);   // held by the plan from earlier solves, reused
     const size_t blk = (size_t)S.q * S.n3 * sizeof(cplx_t<T>);
     const size_t per_slot = blk * (S.uniform ? 9 : 11) + 64 * 1024;
     long long Bmax = std::max<long long>(1, (long long)(0.6 * (double)freeb / (double)per_slot));
@@ -900,17 +936,10 @@ struct Lanczos {
     };
     std::vector<Slot> slots;
     int nact = 0;
-    std::vector<void*> allocs;
-    ~Lanczos() {
-        cudaStreamSynchronize(pl->stream);
-        for (void* p : allocs) cudaFree(p);
-    }
+    int nalloc = 0;   // buffers taken from the plan's pool 1
     template <typename X>
     bloch_status alloc(X** p, size_t n_el) {
-        cudaError_t e = cudaMalloc((void**)p, n_el * sizeof(X));
-        if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (Lanczos basis)");
-        allocs.push_back(*p);
-        return BLOCH_OK;
+        return plan_solver_buf(pl, 1, nalloc++, n_el * sizeof(X), (void**)p);
     }
     C* vb(int s, int i) const { return Vb + ((size_t)s * (m + 1) + i) * n3; }
 
@@ -1028,7 +1057,10 @@ struct Lanczos {
                 mx = std::max(mx, beta * std::abs(Y[(size_t)(m - 1) * m + idx[i]]) / std::max(std::fabs(th), 1e-300));
             }
             st->max_rel_residual = std::max(st->max_rel_residual, mx);
-            if (!conv) any_unconverged = true;
+            if (!conv) {
+                any_unconverged = true;
+                if (!ritz_out) st->k_unconverged += 1;   // the hybrid's refinement decides for it
+            }
             if (ritz_out) {
                 size_t pos = 0;
                 while (pos < order.size() && order[pos] != sl.kidx) ++pos;
@@ -1229,6 +1261,7 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     if (S.order.empty()) return BLOCH_OK;
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
+    freeb += plan_solver_bytes(pl);   // held by the plan from earlier solves, reused
     const size_t per_slot = (size_t)(S.m + 1 + 2 + 5) * S.n3 * sizeof(cplx_t<T>);
     long long Bmax = std::max<long long>(1, (long long)(0.5 * (double)freeb / (double)per_slot));
     Bmax = std::min<long long>(Bmax, 64);
@@ -1253,9 +1286,19 @@ static bloch_status run_hybrid(bloch_plan* pl, const std::vector<std::array<doub
     const int q = pl->opt.block > 0 ? pl->opt.block : std::min(2 * n_bands, n_bands + 8);
     const long long n3 = 3 * pl->V;
     const int chunk = std::max(1, std::min<int>((int)ks.size(), pl->opt.k_batch > 0 ? pl->opt.k_batch : 8));
-    C* buf = nullptr;
-    cudaError_t e = cudaMalloc((void**)&buf, sizeof(C) * (size_t)chunk * q * n3);
-    if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (Lanczos hand-off)");
+    const size_t need = sizeof(C) * (size_t)chunk * q * n3;
+    if (need > pl->handoff_bytes) {
+        cudaStreamSynchronize(pl->stream);
+        if (pl->d_handoff) pl->device_bytes -= pl->handoff_bytes;
+        cudaFree(pl->d_handoff);
+        pl->d_handoff = nullptr;
+        pl->handoff_bytes = 0;
+        cudaError_t e = cudaMalloc(&pl->d_handoff, need);
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (Lanczos hand-off)");
+        pl->handoff_bytes = need;
+        pl->device_bytes += need;
+    }
+    C* buf = (C*)pl->d_handoff;
     std::vector<double> om_tmp;
     bloch_status s = BLOCH_OK;
     bool unconverged = false;
@@ -1279,7 +1322,6 @@ static bloch_status run_hybrid(bloch_plan* pl, const std::vector<std::array<doub
         }
     }
     cudaStreamSynchronize(pl->stream);
-    cudaFree(buf);
     if (s != BLOCH_OK) return s;
     if (unconverged) return set_error(BLOCH_ENOTCONV_EIG, "refinement reached its sweep cap");
     return BLOCH_OK;

@@ -6,9 +6,11 @@
 // fixed device-memory budget, code embedded in a framework that owns the
 // allocator, real-time loops in which an allocator call may stall the
 // device) use bloch_apply_K_noalloc
-// instead: its scratch is one file-scope device array of fixed size,
-// reserved when the library is loaded on a GPU and held until the process
-// exits.  The operator, its kernels and its results are those of
+// instead: its scratch is one file-scope device array of fixed size.  The
+// array is placed on a device when this file's module is loaded there --
+// with CUDA's lazy module loading, at the first call of the entry point on
+// that device -- and held until the process exits.  The operator, its kernels
+// (the same pass kernels and launch shapes) and its results are those of
 // bloch_apply_K in FP32.
 #include <cuda_runtime.h>
 
@@ -46,8 +48,8 @@ static cudaError_t attrs_n() {
     if ((e = smem_attr(k_fpass_y<float, +1, RA, RB, PT>)) != cudaSuccess) return e;
     if ((e = smem_attr(k_fpass_y<float, -1, RA, RB, PT>)) != cudaSuccess) return e;
     if constexpr (RB <= 8) {
-        if ((e = smem_attr(k_fpass_z_strain<float, RA, RB>)) != cudaSuccess) return e;
-        if ((e = smem_attr(k_fpass_z_div<float, RA, RB>)) != cudaSuccess) return e;
+        if ((e = smem_attr(k_fpass_z_strain<float, RA, RB, kFastZThreads>)) != cudaSuccess) return e;
+        if ((e = smem_attr(k_fpass_z_div<float, RA, RB, kFastZThreads>)) != cudaSuccess) return e;
         if ((e = smem_attr(k_fpass_x_stress<float, RA, RB>)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -106,13 +108,16 @@ static void y_pass(bloch_plan* pl, int DIR, int nb, float2* E) {
         k_fpass_y<float, -1, RA, RB, PT><<<gr, 256, smem, pl->stream>>>(E, E, pl->d_twf[1], pl->geo_f);
 }
 
+// z passes: kFastZThreads threads per CTA over P = kFastZThreads / RA
+// neighbouring pencils, the launch shape of bloch_apply_K
 template <int RA, int RB>
 static void z_strain(bloch_plan* pl, int nb, const float2* u, float2* E, const float* qtab) {
     constexpr int N = RA * RB;
-    constexpr int P = 128 / RA;
+    constexpr int NT = kFastZThreads;
+    constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
-    k_fpass_z_strain<float, RA, RB><<<gr, 128, (size_t)(N + 4 * N * P) * sizeof(float2), pl->stream>>>(
+    k_fpass_z_strain<float, RA, RB, NT><<<gr, NT, (size_t)(N + 4 * N * P) * sizeof(float2), pl->stream>>>(
         u, E, qtab, pl->d_twf[2], pl->geo_f);
 }
 
@@ -130,10 +135,11 @@ static void x_stress(bloch_plan* pl, int nb, float2* E) {
 template <int RA, int RB>
 static void z_div(bloch_plan* pl, int nb, const float2* E, float2* out, const float* qtab) {
     constexpr int N = RA * RB;
-    constexpr int P = 128 / RA;
+    constexpr int NT = kFastZThreads;
+    constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
-    k_fpass_z_div<float, RA, RB><<<gr, 128, (size_t)(N + 3 * N * P) * sizeof(float2), pl->stream>>>(
+    k_fpass_z_div<float, RA, RB, NT><<<gr, NT, (size_t)(N + 3 * N * P) * sizeof(float2), pl->stream>>>(
         E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale, nullptr, nullptr);
 }
 
@@ -153,7 +159,9 @@ extern "C" bloch_status bloch_apply_K_noalloc(bloch_plan* pl, int32_t nb, const 
     if (!pl) return set_error(BLOCH_EINVAL, "plan is NULL");
     if (!k || !u || !Ku) return set_error(BLOCH_EINVAL, "NULL argument");
     if (u == Ku) return set_error(BLOCH_EINVAL, "Ku may not alias u");
-    if (nb < 1) return set_error(BLOCH_EINVAL, "nb must be >= 1");
+    // the y passes launch 6 * nb CTA rows (gridDim.y <= 65535), as in bloch_apply_K
+    if (nb < 1 || nb > 65535 / 6) return set_error(BLOCH_EINVAL, "nb must be in [1, 10922]");
+    if (!pl->fast) return set_error(BLOCH_EUNSUPPORTED, "bloch_apply_K_noalloc runs the default FFT variant only");
     const size_t pass_bytes = (size_t)6 * (size_t)pl->V * (size_t)nb * sizeof(float2);
     if (pass_bytes > kNoAllocPassBytes)
         return set_error(BLOCH_EINVAL, "bloch_apply_K_noalloc: nb * V = " + std::to_string((long long)nb * pl->V) +
@@ -181,7 +189,6 @@ extern "C" bloch_status bloch_apply_K_noalloc(bloch_plan* pl, int32_t nb, const 
 
     // the five passes of the K-apply, the kernels of bloch_apply_K (two-stage
     // register passes on axes of 16..128, shared-memory Stockham passes otherwise)
-    if (!pl->fast) return set_error(BLOCH_EUNSUPPORTED, "bloch_apply_K_noalloc runs the default FFT variant only");
     const Geo& g = pl->geo_f;
     const TileCfg& t = pl->tile_f;
     const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,

@@ -834,6 +834,8 @@ void bloch_plan_destroy(bloch_plan* pl) {
     cudaFree(pl->d_nactive);
     cudaFreeHost(pl->h_nactive);
     cudaFree(pl->d_ztab);
+    cudaFree(pl->d_handoff);
+    plan_solver_release(pl);
     delete pl;
 }
 

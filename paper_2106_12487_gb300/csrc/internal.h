@@ -133,6 +133,19 @@ struct bloch_plan {
     int* d_iter = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
 
+    // hand-off block of the FP32 Lanczos -> Algorithm 1 form (chunk x q x 3V float2),
+    // kept by the plan and grown on demand
+    void* d_handoff = nullptr;
+    size_t handoff_bytes = 0;
+    // block buffers of the eigensolvers (pool 0: subspace iteration, 1: Lanczos),
+    // kept between bloch_solve_bands calls and grown on demand, so a solve
+    // allocates (and synchronises on a free) only when it needs more than before
+    struct SolverBuf {
+        void* p = nullptr;
+        size_t bytes = 0;
+    };
+    std::vector<SolverBuf> solver_bufs[2];
+
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;
     size_t device_bytes = 0;
@@ -214,6 +227,13 @@ template <typename T>
 bloch_status lp_activate(bloch_plan* pl, int ntab, int qstride_sys, int zgroup);
 void lp_deactivate(bloch_plan* pl);
 
+}  // namespace bloch
+
+namespace bloch {
+// eigensolver buffers kept by the plan (bloch_eig.cu): buffer idx of pool, at least bytes
+bloch_status plan_solver_buf(bloch_plan* pl, int pool, int idx, size_t bytes, void** out);
+size_t plan_solver_bytes(const bloch_plan* pl);
+void plan_solver_release(bloch_plan* pl);
 }  // namespace bloch
 
 // eigensolver entry (bloch_eig.cu)

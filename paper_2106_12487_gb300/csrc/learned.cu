@@ -47,6 +47,8 @@ struct bloch_lp {
     };
     std::vector<Block> blocks;
     long long total_samples = 0;
+    double* d_w = nullptr;      // per-pair weights of the moment kernel
+    int wcap = 0;
 };
 
 namespace bloch {
@@ -90,26 +92,46 @@ __global__ void k_lp_rhs(cplx_t<T>* b, const T* __restrict__ qtab, Geo g, unsign
     }
 }
 
-// mom[v] += sum over systems of the scaled moments of (r, e = xs - x)
+// Per-pair weights of the moments: 1/||r_j||^2, or 0 for a pair that is not
+// recorded.  From the CG scalars: pairs are recorded while ||r_j|| > 1e-4 ||b||
+// (below that the error e_j is dominated by the 1e-6 accuracy of x* itself).
+__global__ void k_lp_weights_cg(const CGSys* __restrict__ sys, int nsys, double* __restrict__ w) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsys) w[s] = (sys[s].rr > 1e-8 * sys[s].bb) ? 1.0 / sys[s].rr : 0.0;
+}
+
+// From the inner products (r_j, r_j) of caller-supplied pairs (0 for r_j = 0).
+__global__ void k_lp_weights_dot(const double2* __restrict__ rr, int n, double* __restrict__ w) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) w[s] = rr[s].x > 0.0 ? 1.0 / rr[s].x : 0.0;
+}
+
+// mom[v] += sum over pairs of w_j times the moments of (r_j, e_j) at voxel v:
+// A = Re r r^H, B = sym Re r e^H (xx yy zz yz xz xy), c = |e|^2, where
+// e_j = xs_j - x_j (CG iterates against the converged solution) or, with
+// xs == nullptr, e_j = x_j (errors given directly).
 __global__ void k_lp_moments(const float2* __restrict__ r, const float2* __restrict__ x,
-                             const float2* __restrict__ xs, const CGSys* __restrict__ sys, int nsys, long long V,
+                             const float2* __restrict__ xs, const double* __restrict__ w, int nsys, long long V,
                              float* __restrict__ mom) {
     for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < (unsigned)V; v += gridDim.x * blockDim.x) {
         float acc[kMom];
 #pragma unroll
         for (int i = 0; i < kMom; ++i) acc[i] = 0.f;
         for (int s = 0; s < nsys; ++s) {
-            // pairs are recorded while ||r_j|| > 1e-4 ||b||: below that the error
-            // e_j is dominated by the 1e-6 accuracy of x* itself
-            if (!(sys[s].rr > 1e-8 * sys[s].bb)) continue;
-            const float sc = (float)(1.0 / sys[s].rr);   // 1/||r||^2
+            const float sc = (float)w[s];
+            if (sc == 0.f) continue;
             float2 rv[3], ev[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const size_t i = ((size_t)s * 3 + c) * V + v;
                 rv[c] = r[i];
-                const float2 a = xs[i], b = x[i];
-                ev[c] = make_float2(a.x - b.x, a.y - b.y);
+                const float2 b = x[i];
+                if (xs) {
+                    const float2 a = xs[i];
+                    ev[c] = make_float2(a.x - b.x, a.y - b.y);
+                } else {
+                    ev[c] = b;
+                }
             }
             const int ii[6] = {0, 1, 2, 1, 0, 0}, jj[6] = {0, 1, 2, 2, 2, 1};
 #pragma unroll
@@ -396,11 +418,24 @@ template bloch_status lp_activate<double>(bloch_plan*, int, int, int);
 
 void lp_deactivate(bloch_plan* pl) { pl->psel = PrecondSel{nullptr, 1}; }
 
+static bloch_status lp_weights_cap(bloch_lp* lp, int n) {
+    if (n <= lp->wcap) return BLOCH_OK;
+    cudaDeviceSynchronize();
+    cudaFree(lp->d_w);
+    lp->d_w = nullptr;
+    lp->wcap = 0;
+    cudaError_t e = cudaMalloc((void**)&lp->d_w, (size_t)n * sizeof(double));
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (pair weights)");
+    lp->wcap = n;
+    return BLOCH_OK;
+}
+
 struct MomHook {
     bloch_plan* pl;
     const float2* x;
     const float2* xs;
     float* mom;
+    double* w;
     int nsys;
     int n_iters;
     int recorded = 0;
@@ -409,10 +444,36 @@ struct MomHook {
 static void mom_hook(void* ctx, int it) {
     MomHook* h = (MomHook*)ctx;
     if (it >= h->n_iters) return;
-    ++h->pl->launches;
+    h->pl->launches += 2;
+    k_lp_weights_cg<<<(h->nsys + 127) / 128, 128, 0, h->pl->stream>>>(h->pl->ws_f.sys, h->nsys, h->w);
     k_lp_moments<<<(unsigned)std::min<long long>((h->pl->V + 255) / 256, 2048), 256, 0, h->pl->stream>>>(
-        h->pl->ws_f.r, h->x, h->xs, h->pl->ws_f.sys, h->nsys, h->pl->V, h->mom);
+        h->pl->ws_f.r, h->x, h->xs, h->w, h->nsys, h->pl->V, h->mom);
     h->recorded += h->nsys;
+}
+
+// New empty data block for the plan's grid whose q table is that of the
+// plan's system 0 (set_k must have run).
+static bloch_status lp_new_block(bloch_plan* pl, bloch_lp::Block& blk) {
+    blk.grid[0] = pl->Nx;
+    blk.grid[1] = pl->Ny;
+    blk.grid[2] = pl->Nz;
+    blk.V = pl->V;
+    blk.pc = pl->pc;
+    for (int i = 0; i < 36; ++i) blk.C0V[i] = pl->C0V[i] / pl->Cref;
+    blk.snorm = lp_snorm(pl);
+    blk.samples = 0;
+    blk.d_mom = nullptr;
+    blk.d_q = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&blk.d_mom, (size_t)pl->V * kMom * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&blk.d_q, (size_t)(pl->Nx + pl->Ny + pl->Nz) * sizeof(float))) != cudaSuccess) {
+        cudaFree(blk.d_mom);
+        return set_cuda_error(e, "cudaMalloc (data block)");
+    }
+    BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(blk.d_mom, 0, (size_t)pl->V * kMom * sizeof(float), pl->stream));
+    BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(blk.d_q, pl->ws_f.qtab, (size_t)(pl->Nx + pl->Ny + pl->Nz) * sizeof(float),
+                                         cudaMemcpyDeviceToDevice, pl->stream));
+    return BLOCH_OK;
 }
 
 }  // namespace bloch
@@ -455,6 +516,7 @@ bloch_status bloch_lp_create(bloch_lp** out, uint64_t seed) {
 void bloch_lp_destroy(bloch_lp* lp) {
     if (!lp) return;
     cudaDeviceSynchronize();
+    cudaFree(lp->d_w);
     cudaFree(lp->d_prm);
     cudaFree(lp->d_m);
     cudaFree(lp->d_v);
@@ -513,22 +575,13 @@ bloch_status bloch_lp_collect(bloch_lp* lp, bloch_plan* pl, int32_t n_k, const d
         if (st == BLOCH_ENOTCONV_CG) st = BLOCH_OK;
         if (st != BLOCH_OK) break;
         bloch_lp::Block blk;
-        blk.grid[0] = pl->Nx;
-        blk.grid[1] = pl->Ny;
-        blk.grid[2] = pl->Nz;
-        blk.V = pl->V;
-        blk.pc = pl->pc;
-        for (int i = 0; i < 36; ++i) blk.C0V[i] = pl->C0V[i] / pl->Cref;
-        blk.snorm = lp_snorm(pl);
-        if ((e = cudaMalloc((void**)&blk.d_mom, (size_t)pl->V * kMom * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&blk.d_q, (size_t)(pl->Nx + pl->Ny + pl->Nz) * sizeof(float))) != cudaSuccess) {
-            st = set_cuda_error(e, "cudaMalloc (data block)");
+        if ((st = lp_new_block(pl, blk)) != BLOCH_OK) break;
+        if ((st = lp_weights_cap(lp, n_rhs)) != BLOCH_OK) {
+            cudaFree(blk.d_mom);
+            cudaFree(blk.d_q);
             break;
         }
-        cudaMemsetAsync(blk.d_mom, 0, (size_t)pl->V * kMom * sizeof(float), pl->stream);
-        cudaMemcpyAsync(blk.d_q, pl->ws_f.qtab, (size_t)(pl->Nx + pl->Ny + pl->Nz) * sizeof(float),
-                        cudaMemcpyDeviceToDevice, pl->stream);
-        MomHook h{pl, x, xs, blk.d_mom, n_rhs, n_iters + 1};
+        MomHook h{pl, x, xs, blk.d_mom, lp->d_w, n_rhs, n_iters + 1};
         st = pcg_run<float>(pl, n_rhs, b, x, 1.0, 1e-30, n_iters, false, nullptr, nullptr, nullptr, mom_hook, &h);
         if (st == BLOCH_ENOTCONV_CG) st = BLOCH_OK;
         cudaStreamSynchronize(pl->stream);
@@ -542,6 +595,40 @@ bloch_status bloch_lp_collect(bloch_lp* lp, bloch_plan* pl, int32_t n_k, const d
     cudaFree(x);
     pl->lp = saved;
     return st;
+}
+
+bloch_status bloch_lp_add_pairs(bloch_lp* lp, bloch_plan* pl, const double* k, int32_t n_pairs, const void* r,
+                                const void* e) {
+    if (!lp || !pl || !k || !r || !e) return set_error(BLOCH_EINVAL, "NULL argument");
+    if (n_pairs < 1 || n_pairs > 65535 / 6) return set_error(BLOCH_EINVAL, "n_pairs must be in [1, 10922]");
+    bloch_status st;
+    if ((st = set_k<float>(pl, 1, k)) != BLOCH_OK) return st;
+    if ((st = ensure_cg<float>(pl, n_pairs)) != BLOCH_OK) return st;
+    if ((st = lp_weights_cap(lp, n_pairs)) != BLOCH_OK) return st;
+    const float2* rr = (const float2*)r;
+    const float2* ee = (const float2*)e;
+    launch_dot<float>(pl, n_pairs, rr, rr, 3 * pl->V, pl->ws_f.dots, pl->ws_f.part2);
+    ++pl->launches;
+    k_lp_weights_dot<<<(n_pairs + 127) / 128, 128, 0, pl->stream>>>(pl->ws_f.dots, n_pairs, lp->d_w);
+    bloch_lp::Block blk;
+    if ((st = lp_new_block(pl, blk)) != BLOCH_OK) return st;
+    ++pl->launches;
+    k_lp_moments<<<(unsigned)std::min<long long>((pl->V + 255) / 256, 2048), 256, 0, pl->stream>>>(
+        rr, ee, nullptr, lp->d_w, n_pairs, pl->V, blk.d_mom);
+    std::vector<double> w(n_pairs);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(w.data(), lp->d_w, sizeof(double) * n_pairs, cudaMemcpyDeviceToHost, pl->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(pl->stream);
+    if (ce != cudaSuccess) {
+        cudaFree(blk.d_mom);
+        cudaFree(blk.d_q);
+        return set_cuda_error(ce, "bloch_lp_add_pairs");
+    }
+    for (double wi : w) blk.samples += wi > 0.0 ? 1 : 0;
+    lp->total_samples += blk.samples;
+    lp->blocks.push_back(blk);
+    return BLOCH_OK;
 }
 
 bloch_status bloch_lp_loss_grad(bloch_lp* lp, double* loss, double* grad) {

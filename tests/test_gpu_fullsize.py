@@ -1,7 +1,8 @@
 """Full-size parity at the measured workload (128^3, 200 grains, <001> fibre):
 the bench's FP32 chosen form against the FP64 plain form (Lanczos, tol 1e-10)
-on sampled wave vectors, and the FP64 oracle's Rayleigh quotients of the
-returned FP32 eigenvectors (computed one vector at a time)."""
+on every wave vector of the path, and the FP64 oracle's Rayleigh quotients and
+residuals of returned FP32 eigenvectors (Kato-Temple bounds, computed one
+vector at a time)."""
 import math
 
 import numpy as np
@@ -27,24 +28,51 @@ def B():
     return bloch
 
 
-def test_rve128_chosen_form_frequencies(B):
+@pytest.mark.slow
+def test_rve128_whole_path_against_fp64_and_oracle_bounds(B):
+    """All 64 wave vectors of the 128^3 workload: the bench's FP32 chosen form
+    (one bloch_solve_bands call over the whole path) against FP64 shift-invert
+    Lanczos (PCG 1e-10), max relative frequency difference <= 1e-6, every k
+    converged.  At three sampled wave vectors (first after Gamma, mid-path,
+    last = R) the FP64 oracle's Rayleigh quotient rho and residual eps of
+    returned vectors give the Kato-Temple bound |lambda - rho| <= eps^2 / gap
+    (gap to the nearest other eigenvalue of the FP64 run, halved for safety):
+    the returned lambda must lie inside it, so each is an eigenvalue of the
+    FP64 operator to that accuracy, not only consistent with its own vector."""
     import torch
     p = synth.workload("rve128_g200")
-    idx = [1, 37]              # the first wave vector after Gamma, one on M-Gamma
-    ks = p.k_list[idx]
-    plan = B.Plan.from_problem(p, block=p.n_bands + 2, **CHOSEN)
-    vecs = torch.zeros(len(idx) * p.n_bands * 3 * plan.V, dtype=torch.complex64, device="cuda")
-    got, stats, _ = plan.solve_bands(ks, p.n_bands, vecs_out=vecs)
+    nk, nb = p.k_list.shape[0], p.n_bands
+    plan = B.Plan.from_problem(p, block=nb + 2, **CHOSEN)
+    vecs = torch.zeros(nk * nb * 3 * plan.V, dtype=torch.complex64, device="cuda")
+    got, stats, status = plan.solve_bands(p.k_list, nb, vecs_out=vecs)
+    assert status == 0 and stats["k_unconverged"] == 0
+    plan.close()
     ref_plan = B.Plan.from_problem(p, precision=0, method=0, tol_lin=1e-10, tol_eig=1e-10, max_cg=2000)
-    ref, _, _ = ref_plan.solve_bands(ks, p.n_bands)
-    assert np.max(np.abs(got / ref - 1)) < 1e-6
-    # oracle Rayleigh quotients of three returned vectors (acoustic, mid, top band)
+    ref, rstats, rstatus = ref_plan.solve_bands(p.k_list, nb)
+    ref_plan.close()
+    assert rstatus == 0
+    gamma = np.all(p.k_list == 0.0, axis=1)
+    assert np.all(got[gamma, :3] == 0) and np.all(ref[gamma, :3] == 0)
+    nz = ref > 0
+    rel = np.abs(got[nz] / ref[nz] - 1)
+    print(f"\n128^3 whole path: max rel freq diff chosen vs FP64 {rel.max():.3e} over {nz.sum()} eigenpairs")
+    assert rel.max() <= 1e-6
     med = O.Medium.from_problem(p)
-    V = vecs.cpu().numpy().reshape(len(idx), p.n_bands, 3, *reversed(p.grid))
-    for i, b in [(0, 0), (0, 9), (1, 4)]:
-        u = V[i, b].astype(np.complex128)
-        lam, res = O.rayleigh_quotients(med, ks[i], u[None])
-        assert abs(math.sqrt(lam[0]) / got[i, b] - 1) < 1e-6
+    V = vecs.view(nk, nb, 3 * plan.V)
+    rho = med.rho_bar
+    for ki, bands in [(1, [0, 5, 9]), (32, [0, 9]), (nk - 1, [3])]:
+        lam_ref = np.sort(ref[ki] ** 2)
+        for b in bands:
+            u = V[ki, b].cpu().numpy().astype(np.complex128).reshape(3, *reversed(p.grid))
+            Ku = O.apply_K(med, p.k_list[ki], u)
+            Mu = O.apply_M(med, u)
+            rq = O.vdot(u, Ku).real / O.vdot(u, Mu).real
+            eps = O.norm(Ku - rq * Mu) / O.norm(Mu)   # uniform density: M = rho I
+            others = np.delete(lam_ref, np.argmin(np.abs(lam_ref - rq)))
+            gap = 0.5 * np.min(np.abs(others - rq))
+            lam_got = got[ki, b] ** 2
+            assert abs(lam_got - rq) <= eps ** 2 / gap + 1e-12 * rq, (ki, b, lam_got, rq, eps, gap)
+            assert abs(math.sqrt(rq) / got[ki, b] - 1) < 1e-6
 
 
 @pytest.fixture(scope="module")

@@ -159,3 +159,91 @@ def test_bands_independent_of_preconditioner(B):
         B.set_preconditioner(plan, lp)
         got, _, _ = plan.solve_bands(ks, 6)
         assert np.max(np.abs(got / want - 1)) < bar
+
+
+def _scaled_units(p):
+    """The library's internal units: q~ = q * L_max / (2 pi), C~ = C0 / C_ref with
+    C_ref the largest diagonal entry of C0; K~ = K / K_scale, K_scale = C_ref / qscale^2."""
+    med = O.Medium.from_problem(p)
+    qscale = max(p.L) / (2 * math.pi)
+    Cref = max(med.C0[0, 0, 0, 0], med.C0[1, 1, 1, 1], med.C0[2, 2, 2, 2])
+    return med, qscale, med.C0 / Cref, Cref / qscale ** 2
+
+
+@pytest.mark.parametrize("grid", [(9, 7, 5), (8, 6, 4), (16, 12, 10)])
+def test_trained_network_inference_matches_oracle(B, grid):
+    """Inference with non-trivial parameters (g far from 1, different per
+    branch): the library's Z tables applied by bloch_apply_precond against the
+    oracle's Z_of at every Fourier bin, odd and even grids (Nyquist bins), a
+    general wave vector and k = 0 (bin 0 maps to zero)."""
+    p = synth.small_polycrystal(grid, 5, 13)
+    plan = B.Plan.from_problem(p, precision=1)
+    lp = B.LearnedPrecond(seed=11)
+    theta = lp.params()
+    rng = np.random.default_rng(grid[0])
+    nh = H * 5 + H + H * H + H
+    theta[:nh] = rng.uniform(-0.9, 0.9, nh)
+    theta[nh:nh + H] = rng.uniform(-1.0, 1.0, H)
+    theta[-1] = 0.3
+    lp.params(set_to=theta)
+    theta = lp.params()          # the FP32 values in use
+    B.set_preconditioner(plan, lp)
+    ks = np.array([[0.31, -0.17, 0.42], [0.0, 0.0, 0.0]]) * math.pi / 1e-3
+    r = synth.random_field(p.grid, 8, batch=2)
+    z = to_dev(np.zeros_like(r))
+    plan.apply_precond(ks, to_dev(r), z)
+    got = z.cpu().numpy().astype(np.complex128)
+    r32 = r.astype(np.complex64).astype(np.complex128)
+    med, qscale, C0s, Kscale = _scaled_units(p)
+    Nmax = max(grid)
+    g_all = []
+    for b in range(2):
+        qv = np.stack([np.broadcast_to(med.q(ks[b])[j], med.shape[1:]) for j in range(3)], -1).reshape(-1, 3)
+        qv = qv * qscale
+        nz = np.einsum("nj,nj->n", qv, qv) > 0
+        Z = np.zeros((qv.shape[0], 3, 3))
+        Z[nz] = OL.Z_of(theta, H, qv[nz], C0s, Nmax)
+        rb = r32[b].reshape(3, -1).T
+        want = np.einsum("nij,nj->ni", Z, rb) / Kscale
+        gb = got[b].reshape(3, -1).T
+        assert np.all(gb[~nz] == 0)
+        # per voxel, relative to |Z| |r| at that voxel (small and large |q| alike)
+        scale = np.linalg.norm(Z, axis=(1, 2)) * np.linalg.norm(rb, axis=1) / Kscale
+        err = np.linalg.norm(gb - want, axis=1)
+        assert np.max(err[nz] / scale[nz]) < 1e-5
+        assert np.linalg.norm(gb - want) <= 2e-6 * np.linalg.norm(want)
+        # the network is far from the Green operator here
+        g_all.append(OL.g_of(theta, H, OL.features(qv[nz], np.linalg.eigvalsh(OL.acoustic(C0s, qv[nz])), Nmax)))
+    g_all = np.concatenate([g.ravel() for g in g_all])
+    assert g_all.min() < 0.8 and g_all.max() > 1.2
+
+
+def test_moment_kernel_matches_oracle(B):
+    """The moment kernel used by bloch_lp_collect, fed caller-supplied pairs
+    through bloch_lp_add_pairs, against the oracle's moments of the same
+    (FP32-rounded) pairs; a zero-residual pair is skipped."""
+    import torch
+    p = synth.small_polycrystal((9, 8, 6), 4, 21)
+    plan = B.Plan.from_problem(p, precision=1)
+    lp = B.LearnedPrecond(seed=2)
+    rng = np.random.default_rng(5)
+    shape = (3, 3) + tuple(reversed(p.grid))
+    r = (rng.normal(size=shape) + 1j * rng.normal(size=shape)) * np.array([1.0, 3e-2, 40.0])[:, None, None, None, None]
+    e = (rng.normal(size=shape) + 1j * rng.normal(size=shape)) * 0.7
+    r[1] = 0.0
+    r = r.astype(np.complex64)
+    e = e.astype(np.complex64)
+    k = np.array([0.2, -0.45, 0.1]) * math.pi / 1e-3
+    lp.add_pairs(plan, k, to_dev(r), to_dev(e))
+    torch.cuda.synchronize()
+    assert lp.num_blocks == 1
+    blk = lp.export_block(0)
+    assert blk["samples"] == 2
+    want = OL.moments(r.astype(np.complex128), e.astype(np.complex128))
+    got = blk["mom"]
+    colmax = np.max(np.abs(want), axis=0)
+    assert np.all(np.abs(got - want) <= 1e-5 * colmax[None, :])
+    # the block's q features are the scaled xi + k of the plan's grid
+    med, qscale, _, _ = _scaled_units(p)
+    qx = (med.xi[0].ravel() + k[0]) * qscale
+    assert np.allclose(blk["q"][:p.grid[0]], qx, rtol=1e-6, atol=1e-6)

@@ -67,3 +67,39 @@ def test_loss_vanishes_at_the_generating_parameters():
     assert OL.loss(ts + 0.05 * rng.normal(size=ts.size), H, blocks) > 1e-6 * c.sum()
     g = OL.fd_grad(ts, H, blocks, h=1e-6)
     assert np.linalg.norm(g) < 1e-5 * c.sum()
+
+
+def test_moments_reproduce_the_pairwise_loss():
+    """The moments function against the definition it serves: for any
+    symmetric Z per voxel, sum_voxels tr(Z Z A) - 2 tr(Z B) + c equals the
+    brute-force sum over pairs of ||Z r_j - e_j||^2 / ||r_j||^2 (complex
+    fields), and a zero residual pair is skipped."""
+    rng = np.random.default_rng(6)
+    shape = (3, 4, 3, 5)
+    n = 4
+    r = rng.normal(size=(n,) + shape) + 1j * rng.normal(size=(n,) + shape)
+    e = rng.normal(size=(n,) + shape) + 1j * rng.normal(size=(n,) + shape)
+    r[2] = 0.0                                   # skipped pair
+    V = 60
+    S = rng.normal(size=(V, 3, 3))
+    Z = S + np.transpose(S, (0, 2, 1))           # symmetric, indefinite is fine here
+    m = OL.moments(r, e)
+    A = OL.sym6_to_mat(m[:, :6])
+    Bm = OL.sym6_to_mat(m[:, 6:12])
+    via_moments = float(np.einsum("nij,njk,nki->", Z, Z, A) - 2.0 * np.einsum("nij,nji->", Z, Bm) + m[:, 12].sum())
+    brute = 0.0
+    for j in range(n):
+        rj = r[j].reshape(3, V).T
+        ej = e[j].reshape(3, V).T
+        nr2 = float(np.sum(np.abs(rj) ** 2))
+        if nr2 == 0.0:
+            continue
+        d = np.einsum("nij,nj->ni", Z, rj) - ej
+        brute += float(np.sum(np.abs(d) ** 2)) / nr2
+    assert abs(via_moments - brute) <= 1e-12 * abs(brute)
+    # a planted mistake (unsymmetrised B) changes the loss
+    m2 = m.copy()
+    m2[:, 6 + 3] *= 1.5
+    B2 = OL.sym6_to_mat(m2[:, 6:12])
+    bad = float(np.einsum("nij,njk,nki->", Z, Z, A) - 2.0 * np.einsum("nij,nji->", Z, B2) + m[:, 12].sum())
+    assert abs(bad - brute) > 1e-6 * abs(brute)
