@@ -463,6 +463,73 @@ def solve_bands(med: Medium, k_list, n: int, tol_lin: float = 1e-10, tol_eig: fl
 
 
 # ---------------------------------------------------------------------------
+# Group velocity (Section 5.1, Eq. c_group; wave speeds of Section 5.2)
+# ---------------------------------------------------------------------------
+def apply_dK(med: Medium, k, m: int, U: np.ndarray) -> np.ndarray:
+    """Derivative of the stiffness operator with respect to k_m, by the product
+    rule on the component form of Eq. (hatA) (q = xi + k, dq_j/dk_m = delta_jm):
+    dA_i{U}/dk_m = F{ C_imkl F^-1(q_l U_k) } + q_j F{ C_ijkm F^-1(U_k) }."""
+    q = med.q(k)
+    out = np.zeros(U.shape, dtype=complex)
+    w = [_Finv(U[kk]) for kk in range(3)]
+    for i in range(3):
+        s1 = np.zeros(U.shape[1:], dtype=complex)
+        for kk in range(3):
+            for ll in range(3):
+                s1 += med.C4g[:, i, m, kk, ll][med.grain_ids] * _Finv(q[ll] * U[kk])
+        out[i] += _F(s1)
+        for j in range(3):
+            s2 = np.zeros(U.shape[1:], dtype=complex)
+            for kk in range(3):
+                s2 += med.C4g[:, i, j, kk, m][med.grain_ids] * w[kk]
+            out[i] += q[j] * _F(s2)
+    return out
+
+
+def group_velocity_hf(med: Medium, k, U: np.ndarray):
+    """Group velocities d omega / d k of eigenvectors U (n, 3, Nz, Ny, Nx) of
+    A_k U = lambda M U by the Hellmann-Feynman identity (M does not depend on k):
+    d lambda / d k_m = u^H (dA/dk_m) u / u^H M u,  d omega/d k = (d lambda/d k) / (2 omega),
+    lambda the Rayleigh quotient of u.  Returns (omega (n,), c (n, 3))."""
+    n = U.shape[0]
+    om = np.empty(n)
+    c = np.empty((n, 3))
+    for p in range(n):
+        Mu = apply_M(med, U[p])
+        uMu = vdot(U[p], Mu).real
+        lam = vdot(U[p], apply_K(med, k, U[p])).real / uMu
+        om[p] = math.sqrt(max(lam, 0.0))
+        for m in range(3):
+            dl = vdot(U[p], apply_dK(med, k, m, U[p])).real / uMu
+            c[p, m] = dl / (2.0 * om[p])
+    return om, c
+
+
+def group_velocity_fd(med: Medium, k, n: int, h: float, solver=None):
+    """Group velocities of the n lowest bands by central finite differences of
+    the band frequencies along each axis, the derivative of Eq. (c_group) taken
+    as the paper takes it (differences of omega between neighbouring wave
+    vectors of a branch); valid where the bands are simple.  `solver(k, n)`
+    returns the n lowest omega (default: dense generalised eigensolve, tiny
+    grids only).  Returns c (n, 3)."""
+    if solver is None:
+        import scipy.linalg
+
+        Md = dense_M(med)
+
+        def solver(kk, nn):
+            lam = scipy.linalg.eigh(dense_K(med, kk), Md, eigvals_only=True, subset_by_index=(0, nn - 1))
+            return np.sqrt(np.maximum(lam, 0.0))
+    c = np.empty((n, 3))
+    k = np.asarray(k, float)
+    for m in range(3):
+        e = np.zeros(3)
+        e[m] = h
+        c[:, m] = (solver(k + e, n) - solver(k - e, n)) / (2.0 * h)
+    return c
+
+
+# ---------------------------------------------------------------------------
 # Dense matrices for tiny grids (tests only)
 # ---------------------------------------------------------------------------
 def dense_operator(apply, shape) -> np.ndarray:

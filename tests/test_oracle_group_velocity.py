@@ -1,0 +1,100 @@
+"""Pins of the oracle's group velocity (Section 5.1, Eq. c_group) on the CPU.
+
+* the derivative operator dA/dk_m (product rule on Eq. hatA) equals the central
+  difference of A_k in k, which is exact because A_k is quadratic in k;
+* a homogeneous isotropic medium has omega = c |xi + k| on every branch (the
+  closed form of Section 4.1), so the group velocity of a plane wave is
+  c (xi + k)/|xi + k| with c = c_L or c_T;
+* on a small polycrystal the Hellmann-Feynman velocities of the dense
+  eigenvectors equal central differences of the band frequencies (the way the
+  paper differentiates a branch) to O(h^2).
+"""
+import math
+
+import numpy as np
+import scipy.linalg
+
+from oracle import bloch_oracle as O
+from paper_2106_12487_gb300 import synth
+
+L3 = (1e-3, 1e-3, 1e-3)
+
+
+def homog(C6, rho, grid, L=L3):
+    Nx, Ny, Nz = grid
+    return O.Medium(grid, L, np.zeros((Nz, Ny, Nx), np.int32), np.asarray(C6)[None], np.array([rho]))
+
+
+def small_poly(grid=(4, 4, 3), ng=3, seed=9, rho_mix=False):
+    p = synth.small_polycrystal(grid, ng, seed)
+    rho = p.rho.copy()
+    if rho_mix:
+        rho = rho * (1.0 + 0.5 * np.arange(rho.size) / rho.size)
+    return O.Medium(tuple(p.grid), tuple(p.L), p.grain_ids, p.C_per_grain, rho)
+
+
+def test_derivative_operator_is_the_exact_central_difference():
+    med = small_poly()
+    rng = np.random.default_rng(3)
+    U = rng.normal(size=med.shape) + 1j * rng.normal(size=med.shape)
+    k = np.array([0.37, -0.21, 0.55]) * math.pi / 1e-3
+    h = 0.4 * math.pi / 1e-3          # large step: A_k is quadratic, the difference is exact
+    for m in range(3):
+        e = np.zeros(3)
+        e[m] = h
+        fd = (O.apply_K(med, k + e, U) - O.apply_K(med, k - e, U)) / (2 * h)
+        d = O.apply_dK(med, k, m, U)
+        assert np.linalg.norm(d - fd) <= 1e-12 * np.linalg.norm(fd)
+        # planted mistake: twice the first product-rule term in place of both
+        # terms (equal only in the inner product with U, not as operators)
+        q = med.q(k)
+        first = np.zeros(U.shape, dtype=complex)
+        for i in range(3):
+            s1 = np.zeros(U.shape[1:], dtype=complex)
+            for kk in range(3):
+                for ll in range(3):
+                    s1 += med.C4g[:, i, m, kk, ll][med.grain_ids] * np.fft.ifftn(q[ll] * U[kk])
+            first[i] = np.fft.fftn(s1)
+        assert np.linalg.norm(2 * first - fd) > 1e-3 * np.linalg.norm(fd)
+
+
+def test_homogeneous_isotropic_plane_waves():
+    lam_l, mu = 90e9, 40e9
+    rho = 5000.0
+    cL, cT = math.sqrt((lam_l + 2 * mu) / rho), math.sqrt(mu / rho)
+    grid = (5, 4, 6)
+    med = homog(synth.isotropic_voigt(lam_l, mu), rho, grid)
+    k = np.array([0.31, 0.12, -0.44]) * math.pi / 1e-3
+    for b in [(0, 0, 0), (1, 3, 2), (4, 1, 5)]:
+        q = np.array([med.xi[0].ravel()[b[0]], med.xi[1].ravel()[b[1]], med.xi[2].ravel()[b[2]]]) + k
+        qh = q / np.linalg.norm(q)
+        t1 = np.cross(qh, [0.3, 0.8, -0.5])
+        t1 /= np.linalg.norm(t1)
+        t2 = np.cross(qh, t1)
+        for pol, c in ((qh, cL), (t1, cT), (t2, cT)):
+            U = np.zeros((1,) + med.shape, dtype=complex)
+            U[0, :, b[2], b[1], b[0]] = pol
+            om, cg = O.group_velocity_hf(med, k, U)
+            assert abs(om[0] / (c * np.linalg.norm(q)) - 1) < 1e-12
+            assert np.allclose(cg[0], c * qh, rtol=0, atol=1e-10 * c)
+
+
+def test_hellmann_feynman_equals_branch_differences_polycrystal():
+    for rho_mix in (False, True):
+        med = small_poly(rho_mix=rho_mix)
+        k = np.array([0.41, 0.23, -0.17]) * math.pi / 1e-3
+        K = O.dense_K(med, k)
+        M = O.dense_M(med)
+        lam, W = scipy.linalg.eigh(K, M, subset_by_index=(0, 7))
+        simple = np.ones(8, bool)
+        rel_gap = np.diff(lam) / lam[1:]
+        simple[:-1] &= rel_gap > 1e-3
+        simple[1:] &= rel_gap > 1e-3
+        U = W.T.reshape((8,) + med.shape)
+        om, c_hf = O.group_velocity_hf(med, k, U)
+        assert np.allclose(om, np.sqrt(lam), rtol=1e-10)
+        h = 1e-4 * math.pi / 1e-3         # O(h^2) truncation ~1e-7, rounding ~1e-10 relative
+        c_fd = O.group_velocity_fd(med, k, 8, h)
+        scale = np.max(np.abs(c_hf))
+        assert simple.sum() >= 4
+        assert np.max(np.abs(c_fd[simple] - c_hf[simple])) <= 1e-6 * scale
