@@ -252,6 +252,50 @@ bloch_status bloch_solve_bands(bloch_plan* plan, int32_t n_k, const double* k_li
                                double* omega_out, void* vecs_out, bloch_stats* stats);
 
 /*
+ * Group velocity of eigenvectors, Section 5.1 Eq. (c_group): c = d omega / d k
+ * for each given vector u of A_k u = lambda M u, by the Hellmann-Feynman
+ * identity d lambda/d k_m = u^H (dA_k/dk_m) u / u^H M u (M does not depend on
+ * k), with u^H (dA_k/dk_m) u = 2 Re sum_xi conj(U_i) F{sigma_im} from the
+ * component form of Eq. (hatA), sigma = C(x) : F^-1(sym (xi+k) (x) U) the
+ * mode's stress, and d omega/d k = (d lambda/d k) / (2 omega).  lambda is the
+ * Rayleigh quotient of u, so u should be an eigenvector (as returned by
+ * bloch_solve_bands; any normalisation) of a simple eigenvalue -- within a
+ * degenerate eigenspace the result depends on the vector chosen.  The wave
+ * speeds of Section 5.2 are |c| of the acoustic branches at small k.
+ *   nb         vectors (1..10922)
+ *   k          host, nb x 3 (rad/m), the wave vector of each vector
+ *   precision  BLOCH_FP32 or BLOCH_FP64 (u's type; arithmetic in that type,
+ *              sums in FP64)
+ *   u          device, nb x 3 x V complex, Fourier basis
+ *   omega_out  host, nb (may be NULL): sqrt of the Rayleigh quotient (rad/s)
+ *   c_out      host, nb x 3 (m/s); 0 where omega = 0 (rigid translations at k = 0)
+ * Synchronises the plan's stream.  Errors: BLOCH_EINVAL (arguments, a zero
+ * vector), BLOCH_ENONFINITE (k), BLOCH_ENOMEM, BLOCH_ECUDA.
+ */
+bloch_status bloch_group_velocity(bloch_plan* plan, int32_t nb, const double* k, int32_t precision, const void* u,
+                                  double* omega_out, double* c_out);
+
+/*
+ * Real-space eigenvector fields, Section 5.2 Eq. (rotate_eigenvector):
+ * U(x) = e^{-i phi} F^-1(U^) with F^-1 normalised by 1/V.  The paper takes phi
+ * as the single phase of the field; here phi = arg(sum_x sum_i U_i(x)^2) / 2,
+ * which is that phase (mod pi) whenever the field has one, and otherwise the
+ * single phase maximising ||Re(e^{-i phi} F^-1(U^))||.  Optionally the strain
+ * of the same field, eps_ij = (dU_i/dx_j + dU_j/dx_i)/2 computed spectrally
+ * with d/dx_j = i xi_j (Section 5.2's epsilon_11 = dU_1/dx_1 is eps_xx).
+ *   nb         fields (1..10922)
+ *   precision  BLOCH_FP32 or BLOCH_FP64
+ *   u_hat      device, nb x 3 x V complex, Fourier basis (not modified)
+ *   u_real     device, nb x 3 x V complex: the phase-rotated real-space fields
+ *   strain     device, nb x 6 x V complex, tensor components (xx yy zz yz xz
+ *              xy), or NULL
+ *   phi_out    host, nb (may be NULL): phi (rad)
+ * Outputs may not alias u_hat.  Synchronises the plan's stream.
+ */
+bloch_status bloch_eigvec_real(bloch_plan* plan, int32_t nb, int32_t precision, const void* u_hat, void* u_real,
+                               void* strain, double* phi_out);
+
+/*
  * Host utility (no GPU): the dense generalised Hermitian eigenproblem
  * K Q = M Q diag(lam) solved for the projected matrices of Algorithm 1
  * (step EIG(K, M)), by Cholesky of M and cyclic complex Jacobi, in FP64.

@@ -530,6 +530,27 @@ def group_velocity_fd(med: Medium, k, n: int, h: float, solver=None):
 
 
 # ---------------------------------------------------------------------------
+# Real-space eigenvectors (Section 5.2, Eq. rotate_eigenvector)
+# ---------------------------------------------------------------------------
+def eigvec_real(med: Medium, U_hat: np.ndarray):
+    """U(x) = e^{-i phi} F^-1(U_hat) with phi the single phase of the field
+    (reading: phi = arg(sum_x U(x).U(x)) / 2, the field's phase mod pi when it
+    has one, else the least-squares best single phase), and the strain of the
+    same field eps_ij = (d_j U_i + d_i U_j) / 2 with d_j = i xi_j (the
+    epsilon_11 = dU_1/dx_1 of the section), components (xx, yy, zz, yz, xz, xy).
+    Returns (phi, U (3, Nz, Ny, Nx), eps (6, Nz, Ny, Nx))."""
+    w = _Finv(U_hat)
+    phi = 0.5 * math.atan2(float(np.sum(w * w).imag), float(np.sum(w * w).real))
+    rot = np.exp(-1j * phi)
+    U = rot * w
+    pairs = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+    eps = np.empty((6,) + U_hat.shape[1:], dtype=complex)
+    for c, (i, j) in enumerate(pairs):
+        eps[c] = rot * _Finv(0.5j * (med.xi[j] * U_hat[i] + med.xi[i] * U_hat[j]))
+    return phi, U, eps
+
+
+# ---------------------------------------------------------------------------
 # Dense matrices for tiny grids (tests only)
 # ---------------------------------------------------------------------------
 def dense_operator(apply, shape) -> np.ndarray:

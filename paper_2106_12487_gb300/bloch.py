@@ -28,7 +28,8 @@ EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", 
             "bloch_apply_K_noalloc", "bloch_lp_num_params", "bloch_lp_create", "bloch_lp_destroy", "bloch_lp_params",
             "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train", "bloch_lp_num_blocks", "bloch_lp_export_block",
             "bloch_plan_set_preconditioner", "bloch_plan_autotune",
-            "bloch_plan_trace", "bloch_apply_K_real", "bloch_lp_add_pairs"]
+            "bloch_plan_trace", "bloch_apply_K_real", "bloch_lp_add_pairs", "bloch_group_velocity",
+            "bloch_eigvec_real"]
 
 
 class BlochError(RuntimeError):
@@ -102,6 +103,8 @@ def lib():
     L.bloch_pcg.argtypes = [VP, I32, P(D), I32, VP, VP, D, I32, I32, P(I32), P(D)]
     L.bloch_solve_bands.argtypes = [VP, I32, P(D), I32, P(D), VP, P(Stats)]
     L.bloch_host_gen_eig.argtypes = [I32, P(D), P(D), P(D), P(D)]
+    L.bloch_group_velocity.argtypes = [VP, I32, P(D), I32, VP, P(D), P(D)]
+    L.bloch_eigvec_real.argtypes = [VP, I32, I32, VP, VP, VP, P(D)]
     L.bloch_last_error.argtypes = []
     L.bloch_last_error.restype = ctypes.c_char_p
     L.bloch_plan_device_bytes.argtypes = [VP]
@@ -131,7 +134,7 @@ def lib():
         getattr(L, f).restype = ctypes.c_int
     for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
               "bloch_solve_bands", "bloch_host_gen_eig", "bloch_plan_autotune", "bloch_plan_trace",
-              "bloch_apply_K_real"]:
+              "bloch_apply_K_real", "bloch_group_velocity", "bloch_eigvec_real"]:
         getattr(L, f).restype = ctypes.c_int
     _LIB = L
     return L
@@ -294,6 +297,30 @@ class Plan:
                              _dptr(rel, ctypes.c_double))
         _check(st, allow=(4,) if allow_nonconv else ())
         return iters, rel, st
+
+    def group_velocity(self, k, u, precision: int | None = None):
+        """bloch_group_velocity: (omega (nb,), c (nb, 3)) of the vectors u
+        (nb x 3 x V, Fourier basis) at wave vectors k (nb x 3 or 3)."""
+        prec = self.precision if precision is None else precision
+        nb = u.numel() // (3 * self.V)
+        kv = self._kv(k, nb)
+        om = np.zeros(nb)
+        c = np.zeros((nb, 3))
+        _check(lib().bloch_group_velocity(self.handle, nb, _dptr(kv, ctypes.c_double), prec,
+                                          _tensor_ptr(u, prec, nb * 3 * self.V), _dptr(om, ctypes.c_double),
+                                          _dptr(c, ctypes.c_double)))
+        return om, c
+
+    def eigvec_real(self, u_hat, u_real, strain=None, precision: int | None = None):
+        """bloch_eigvec_real: phase-rotated real-space fields (and strain) of
+        Fourier-basis vectors; returns the phases phi."""
+        prec = self.precision if precision is None else precision
+        nb = u_hat.numel() // (3 * self.V)
+        phi = np.zeros(nb)
+        sp = None if strain is None else _tensor_ptr(strain, prec, nb * 6 * self.V)
+        _check(lib().bloch_eigvec_real(self.handle, nb, prec, _tensor_ptr(u_hat, prec, nb * 3 * self.V),
+                                       _tensor_ptr(u_real, prec, nb * 3 * self.V), sp, _dptr(phi, ctypes.c_double)))
+        return phi
 
     def solve_bands(self, k_list, n_bands, vecs_out=None, allow_nonconv=False):
         kl = np.ascontiguousarray(np.asarray(k_list, dtype=np.float64).reshape(-1, 3))

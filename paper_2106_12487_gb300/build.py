@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbloch.so")
 
-SOURCES = ["bloch_ops.cu", "bloch_eig.cu", "bloch_noalloc.cu", "bloch_cufft.cu", "learned.cu", "autotune.cu", "trace.cu"]
+SOURCES = ["bloch_ops.cu", "bloch_eig.cu", "bloch_noalloc.cu", "bloch_cufft.cu", "learned.cu", "autotune.cu", "trace.cu",
+           "bloch_props.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

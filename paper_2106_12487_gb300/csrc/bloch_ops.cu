@@ -473,10 +473,34 @@ void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out
     k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5, out_scale);
 }
 
+// Fourier-space stress of nb systems whose q tables are set, into the
+// operator workspace E (6 components per system, Voigt order xx yy zz yz xz
+// xy): S = F{ C~(x) : F^-1(sym q (x) u) }, i.e. the K-apply's passes 1-4 and a
+// forward z transform of the six stress components in place of its
+// divergence.  Shared-memory passes (any grid, both precisions).
+template <typename T>
+void launch_K_stress(bloch_plan* pl, int nb, const cplx_t<T>* u) {
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    const TileCfg& t = tile_of<T>(pl);
+    const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,
+                    pyz = (long long)pl->Ny * pl->Nz;
+    dim3 g1((unsigned)((pxy + t.Pz5 - 1) / t.Pz5), nb);
+    dim3 g2((unsigned)((pxz + t.Py2 - 1) / t.Py2), nb * 6);
+    dim3 g3((unsigned)((pyz + t.Px7 - 1) / t.Px7), nb);
+    dim3 gz((unsigned)((pxy + t.Pz2 - 1) / t.Pz2), nb * 6);
+    pl->launches += 5;
+    k_pass_z_strain<T><<<g1, 256, t.smem_z5, pl->stream>>>(u, w.E, w.qtab, tw_of<T>(pl, 2), g, t.Pz5);
+    k_pass_axis<T, +1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    k_pass_x_stress<T><<<g3, 256, t.smem_x7, pl->stream>>>(w.E, pl->d_ids, ctab_of<T>(pl), tw_of<T>(pl, 0), g, t.Px7);
+    k_pass_axis<T, -1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
+    k_pass_axis<T, -1, 2><<<gz, 256, t.smem_z2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 2), g, t.Pz2, T(1));
+}
+
 // In-place 3D FFT of nb three-component fields (DIR -1 forward, +1 inverse;
 // unnormalised), times out_scale: shared-memory passes along z, y and x.
 template <typename T, int DIR>
-static void launch_fft3(bloch_plan* pl, int nb, cplx_t<T>* W, T out_scale) {
+void launch_fft3(bloch_plan* pl, int nb, cplx_t<T>* W, T out_scale) {
     const Geo& g = geo_of<T>(pl);
     const TileCfg& t = tile_of<T>(pl);
     const long long pxy = (long long)pl->Nx * pl->Ny, pxz = (long long)pl->Nx * pl->Nz,
@@ -740,6 +764,9 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     template bloch_status set_k<T>(bloch_plan*, int, const double*);                                     \
     template int launch_K<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T, const cplx_t<T>*, double2*); \
     template void launch_M<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                        \
+    template void launch_K_stress<T>(bloch_plan*, int, const cplx_t<T>*);                                 \
+    template void launch_fft3<T, -1>(bloch_plan*, int, cplx_t<T>*, T);                                   \
+    template void launch_fft3<T, +1>(bloch_plan*, int, cplx_t<T>*, T);                                   \
     template void launch_precond<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, T);                  \
     template void launch_dot<T>(bloch_plan*, int, const cplx_t<T>*, const cplx_t<T>*, long long,         \
                                 double2*, double2*);                                                     \

@@ -137,14 +137,15 @@ struct bloch_plan {
     // kept by the plan and grown on demand
     void* d_handoff = nullptr;
     size_t handoff_bytes = 0;
-    // block buffers of the eigensolvers (pool 0: subspace iteration, 1: Lanczos),
+    // block buffers of the eigensolvers (pool 0: subspace iteration, 1: Lanczos,
+    // 2: band properties),
     // kept between bloch_solve_bands calls and grown on demand, so a solve
     // allocates (and synchronises on a free) only when it needs more than before
     struct SolverBuf {
         void* p = nullptr;
         size_t bytes = 0;
     };
-    std::vector<SolverBuf> solver_bufs[2];
+    std::vector<SolverBuf> solver_bufs[3];   // pool 2: band properties (bloch_props.cu)
 
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;
@@ -171,6 +172,12 @@ template <typename T> bloch_status set_k(bloch_plan* pl, int nb, const double* k
 template <typename T>
 int launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale,
              const cplx_t<T>* dotp = nullptr, double2* dpart = nullptr);
+// Fourier-space stress S = F{C~ : F^-1(sym q (x) u)} of nb systems (q tables
+// set) into the operator workspace E, 6 Voigt components per system.
+template <typename T> void launch_K_stress(bloch_plan* pl, int nb, const cplx_t<T>* u);
+// In-place 3D FFT of nb three-component fields (DIR -1 forward, +1 inverse,
+// unnormalised), times out_scale; shared-memory passes.
+template <typename T, int DIR> void launch_fft3(bloch_plan* pl, int nb, cplx_t<T>* W, T out_scale);
 // Scaled mass operator: out = out_scale * M~ u (M~ = M / rho_ref).  out may alias u.
 template <typename T> void launch_M(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_scale);
 // Scaled preconditioner on nb systems: z = out_scale * P~^-1 r.

@@ -98,3 +98,55 @@ def test_hellmann_feynman_equals_branch_differences_polycrystal():
         scale = np.max(np.abs(c_hf))
         assert simple.sum() >= 4
         assert np.max(np.abs(c_fd[simple] - c_hf[simple])) <= 1e-6 * scale
+
+
+# ------------------------------------------------ Eq. (rotate_eigenvector)
+def test_eigvec_real_recovers_a_single_phase_field():
+    """A field whose points share one phase phi0 (U = e^{i phi0} R, R real) is
+    rotated back to R (up to the sign that any eigenvector has), and
+    phi = phi0 mod pi."""
+    med = small_poly((6, 5, 4))
+    rng = np.random.default_rng(11)
+    R = rng.normal(size=med.shape)
+    for phi0 in (0.3, -1.2, 2.9):
+        U_hat = np.fft.fftn(np.exp(1j * phi0) * R, axes=(-3, -2, -1))
+        phi, U, _ = O.eigvec_real(med, U_hat)
+        d = (phi - phi0) / math.pi
+        assert abs(d - round(d)) < 1e-12
+        sgn = np.sign(np.vdot(R, U.real))
+        assert np.max(np.abs(U - sgn * R)) < 1e-12 * np.max(np.abs(R))
+
+
+def test_eigvec_real_phase_is_the_least_squares_phase():
+    med = small_poly((5, 4, 3))
+    rng = np.random.default_rng(12)
+    U_hat = rng.normal(size=med.shape) + 1j * rng.normal(size=med.shape)
+    phi, U, _ = O.eigvec_real(med, U_hat)
+    w = np.fft.ifftn(U_hat, axes=(-3, -2, -1))
+    best = np.linalg.norm(U.real)
+    for psi in np.linspace(-math.pi, math.pi, 721):
+        assert np.linalg.norm((np.exp(-1j * psi) * w).real) <= best * (1 + 1e-12)
+
+
+def test_eigvec_real_strain_of_a_plane_wave():
+    """One Fourier bin m with polarisation p: U(x_n) = p e^{i xi.x_n}/V on the
+    grid points x_n = n L/N, so eps_ij = (i/2)(xi_j p_i + xi_i p_j) e^{i xi.x_n}/V,
+    rotated by the same phase -- written here from the definition."""
+    grid = (6, 5, 4)
+    med = small_poly(grid)
+    Nx, Ny, Nz = grid
+    pol = np.array([0.6, -0.3, 0.74])
+    for b in [(1, 0, 0), (2, 3, 1), (3, 2, 2)]:
+        U_hat = np.zeros(med.shape, dtype=complex)
+        U_hat[:, b[2], b[1], b[0]] = pol
+        phi, U, eps = O.eigvec_real(med, U_hat)
+        xi = np.array([med.xi[0].ravel()[b[0]], med.xi[1].ravel()[b[1]], med.xi[2].ravel()[b[2]]])
+        z, y, x = np.meshgrid(np.arange(Nz) * 1e-3 / Nz, np.arange(Ny) * 1e-3 / Ny, np.arange(Nx) * 1e-3 / Nx,
+                              indexing="ij")
+        wave = np.exp(1j * (xi[0] * x + xi[1] * y + xi[2] * z)) / (Nx * Ny * Nz) * np.exp(-1j * phi)
+        pairs = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+        for c, (i, j) in enumerate(pairs):
+            want = 0.5j * (xi[j] * pol[i] + xi[i] * pol[j]) * wave
+            assert np.max(np.abs(eps[c] - want)) <= 1e-12 * np.max(np.abs(xi)) / (Nx * Ny * Nz)
+        for i in range(3):
+            assert np.max(np.abs(U[i] - pol[i] * wave)) < 1e-14
