@@ -71,7 +71,57 @@ void plan_solver_release(bloch_plan* pl) {
         for (auto& b : v) cudaFree(b.p);
         v.clear();
     }
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(pl->d_rhohat[i]);
+        pl->d_rhohat[i] = nullptr;
+    }
 }
+
+template <typename T>
+bloch_status gamma_rhohat(bloch_plan* pl, const cplx_t<T>** out) {
+    using C = cplx_t<T>;
+    const int pi = std::is_same<T, float>::value ? 1 : 0;
+    if (!pl->d_rhohat[pi]) {
+        bloch_status st = ensure_ws<T>(pl, 1);
+        if (st != BLOCH_OK) return st;
+        const size_t n3 = (size_t)3 * pl->V;
+        C* tmp = nullptr;
+        if ((st = plan_solver_buf(pl, 2, 3, 2 * n3 * sizeof(C), (void**)&tmp)) != BLOCH_OK) return st;
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(tmp, 0, n3 * sizeof(C), pl->stream));
+        const C one = mk(T(1), T(0));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(tmp, &one, sizeof(C), cudaMemcpyHostToDevice, pl->stream));
+        launch_M<T>(pl, 1, tmp, tmp + n3, T(1));
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)pl->V * sizeof(C));
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (Gamma deflation table)");
+        pl->device_bytes += (size_t)pl->V * sizeof(C);
+        BLOCH_CUDA_CHECK_RET(
+            cudaMemcpyAsync(p, tmp + n3, (size_t)pl->V * sizeof(C), cudaMemcpyDeviceToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));   // `one` leaves scope
+        pl->d_rhohat[pi] = p;
+    }
+    *out = (const C*)pl->d_rhohat[pi];
+    return BLOCH_OK;
+}
+
+template <typename T>
+bloch_status gamma_deflate(bloch_plan* pl, int nv, cplx_t<T>* Vv, cplx_t<T>* MV, double2* d_alpha) {
+    const cplx_t<T>* rh = nullptr;
+    bloch_status st = gamma_rhohat<T>(pl, &rh);
+    if (st != BLOCH_OK) return st;
+    const long long n3 = 3 * pl->V;
+    pl->launches += 2;
+    k_gamma_alpha<T><<<(3 * nv + 127) / 128, 128, 0, pl->stream>>>(MV, n3, pl->V, nv, rh, d_alpha);
+    const unsigned gx = (unsigned)std::min<long long>((pl->V + 255) / 256, 1024);
+    k_gamma_deflate<T><<<dim3(gx, nv), 256, 0, pl->stream>>>(Vv, MV, rh, n3, pl->V, d_alpha);
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    return BLOCH_OK;
+}
+
+template bloch_status gamma_rhohat<float>(bloch_plan*, const float2**);
+template bloch_status gamma_rhohat<double>(bloch_plan*, const double2**);
+template bloch_status gamma_deflate<float>(bloch_plan*, int, float2*, float2*, double2*);
+template bloch_status gamma_deflate<double>(bloch_plan*, int, double2*, double2*, double2*);
 
 // ====================================================================
 // Small dense Hermitian eigenproblems (host, FP64)
@@ -326,6 +376,7 @@ struct Subspace {
     double2 *d_gpart = nullptr, *d_G = nullptr, *d_Q = nullptr, *d_val = nullptr;
     long long* d_idx = nullptr;
     double2 *U64 = nullptr, *KU64 = nullptr, *MU64 = nullptr;
+    double2* d_alpha = nullptr;   // Gamma-point deflation coefficients (non-uniform density)
     int gblk = 0, dblk = 0;
     size_t gsmem = 0;
     // tensor-core Gram (FP32 blocks, options.tensor_gram)
@@ -397,6 +448,7 @@ struct Subspace {
             (s = alloc(&d_Q, (size_t)B * q * q)) || (s = alloc(&d_idx, (size_t)3 * q)) ||
             (s = alloc(&d_val, (size_t)3 * q)))
             return s;
+        if (!uniform && (s = alloc(&d_alpha, (size_t)3 * q))) return s;
         if (fp64res) {
             if ((s = alloc(&U64, (size_t)q * n3)) || (s = alloc(&KU64, (size_t)q * n3))) return s;
             if (!uniform && (s = alloc(&MU64, (size_t)q * n3))) return s;
@@ -428,7 +480,7 @@ struct Subspace {
             while (pos < order.size() && order[pos] != kidx) ++pos;
             BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(U, s), init_blocks + pos * (size_t)q * n3,
                                                  sizeof(C) * q * n3, cudaMemcpyDeviceToDevice, pl->stream));
-            return BLOCH_OK;
+            return deflate_start(s);
         }
         std::vector<StartEntry> se = start_vectors(pl, sl.k, q, sl.gamma);
         BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(vec(U, s), 0, sizeof(C) * q * n3, pl->stream));
@@ -448,7 +500,15 @@ struct Subspace {
             // the scatter buffers are reused by the next init: wait for the copies
             BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
         }
-        return BLOCH_OK;
+        return deflate_start(s);
+    }
+
+    // Gamma with a non-uniform density: the start block must be M-orthogonal
+    // to the rigid translations (M couples bin 0 with the other bins)
+    bloch_status deflate_start(int s) {
+        if (uniform || !slots[s].gamma) return BLOCH_OK;
+        launch_M<T>(pl, q, vec(U, s), vec(MU, s), T(1));
+        return gamma_deflate<T>(pl, q, vec(U, s), vec(MU, s), d_alpha);
     }
 
     // Rayleigh quotients and residuals of vectors [vo, vo+nvs) of slots
@@ -767,7 +827,14 @@ struct Subspace {
             const size_t ne = (size_t)nact * q * n3;
             ++pl->launches;
             k_kn<T><<<4096, 256, 0, pl->stream>>>(U, uniform ? nullptr : MU, rho_s, ws_of<T>(pl).r, KU, ne);
-            if (!uniform) launch_M<T>(pl, nact * q, Ub, MUb, T(1));
+            if (!uniform) {
+                launch_M<T>(pl, nact * q, Ub, MUb, T(1));
+                // Gamma slots: keep U_bar M-orthogonal to the rigid translations
+                // (A_0 x = R fixes x only up to them); A U_bar (Kn) is unchanged
+                for (int i = 0; i < nact; ++i)
+                    if (slots[i].gamma && (s = gamma_deflate<T>(pl, q, vec(Ub, i), vec(MUb, i), d_alpha)) != BLOCH_OK)
+                        return s;
+            }
             // projections K = Ub^H Kn, M = Ub^H Mn in one pass over the block
             dim3 gg(gblk, nact);
             const int npair = q * q;
@@ -858,8 +925,6 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     S.init_blocks = init_blocks;
     for (size_t i = 0; i < ks.size(); ++i) {
         const bool gamma = ks[i][0] == 0.0 && ks[i][1] == 0.0 && ks[i][2] == 0.0;
-        if (gamma && !pl->uniform_rho)
-            return set_error(BLOCH_EUNSUPPORTED, "k = 0 with a non-uniform density is not supported");
         if (gamma && n_bands <= 3) {
             for (int b = 0; b < n_bands; ++b) omega_out[i * n_bands + b] = 0.0;
             continue;

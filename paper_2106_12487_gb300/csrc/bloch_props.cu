@@ -86,12 +86,14 @@ static bloch_status group_velocity_impl(bloch_plan* pl, int nb, const double* k,
     if (st != BLOCH_OK) return st;
     if ((st = set_k<T>(pl, nb, k)) != BLOCH_OK) return st;
     Workspace<T>& w = ws_of<T>(pl);
-    launch_K_stress<T>(pl, nb, u);
+    // M u first: the mass operator's passes use the same workspace E that
+    // then holds the stress field
     const cplx_t<T>* MU = nullptr;
     if (!pl->uniform_rho) {
         launch_M<T>(pl, nb, u, w.Ap, T(1));
         MU = w.Ap;
     }
+    launch_K_stress<T>(pl, nb, u);
     const int nblk = (int)std::max(1LL, std::min<long long>((pl->V + 255) / 256, 512));
     const size_t nval = (size_t)nb * nblk * kDkVals;
     double* d_part = nullptr;

@@ -375,6 +375,53 @@ __global__ void k_convert(const cplx_t<Ta>* __restrict__ a, cplx_t<Tb>* __restri
         b[i] = mk(Tb(a[i].x), Tb(a[i].y));
 }
 
+// Gamma point with a non-uniform density (rigid translations t_c = e_c at
+// bin 0 span the null space of A_0; the spectrum is sought on their
+// M-orthogonal complement).  alpha[v][c] = t_c^H M v / t_c^H M t_c for nv
+// vectors whose M-images MV are given; t_c^H M v is MV's bin-0 entry of
+// component c, and t_c^H M t_c = rhohat[0] with rhohat = (M t_0)_0.
+template <typename T>
+__global__ void k_gamma_alpha(const cplx_t<T>* __restrict__ MV, long long n3, long long V, int nv,
+                              const cplx_t<T>* __restrict__ rhohat, double2* __restrict__ alpha) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nv) return;
+    const int v = t / 3, c = t - 3 * (t / 3);
+    const cplx_t<T> m = MV[(size_t)v * n3 + (size_t)c * V];
+    const double d = (double)rhohat[0].x;
+    alpha[t] = make_double2((double)m.x / d, (double)m.y / d);
+}
+
+// v <- v - sum_c alpha_c t_c (bin 0 of each component) and, when MV is given,
+// M v <- M v - sum_c alpha_c M t_c, with (M t_c)_c = rhohat and zero in the
+// other components.  blockIdx.y = vector.
+template <typename T>
+__global__ void k_gamma_deflate(cplx_t<T>* __restrict__ Vv, cplx_t<T>* __restrict__ MV,
+                                const cplx_t<T>* __restrict__ rhohat, long long n3, long long V,
+                                const double2* __restrict__ alpha) {
+    const int v = blockIdx.y;
+    cplx_t<T> a[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] = mk(T(alpha[3 * v + c].x), T(alpha[3 * v + c].y));
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < V;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (MV) {
+            const cplx_t<T> r = rhohat[e];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cplx_t<T>& m = MV[(size_t)v * n3 + (size_t)c * V + e];
+                m = csub(m, cmul(a[c], r));
+            }
+        }
+        if (e == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cplx_t<T>& x = Vv[(size_t)v * n3 + (size_t)c * V];
+                x = csub(x, a[c]);
+            }
+        }
+    }
+}
+
 // U[idx[i]] = val[i]
 template <typename T>
 __global__ void k_scatter(cplx_t<T>* U, const long long* __restrict__ idx, const double2* __restrict__ val, int n) {

@@ -146,6 +146,9 @@ struct bloch_plan {
         size_t bytes = 0;
     };
     std::vector<SolverBuf> solver_bufs[3];   // pool 2: band properties (bloch_props.cu)
+    // (M~ t_0)_0 of the rigid translation t_0 = e_x at bin 0 (V complex, FP64 and
+    // FP32), for Gamma with a non-uniform density; built on first use
+    void* d_rhohat[2] = {nullptr, nullptr};
 
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;
@@ -241,6 +244,12 @@ namespace bloch {
 bloch_status plan_solver_buf(bloch_plan* pl, int pool, int idx, size_t bytes, void** out);
 size_t plan_solver_bytes(const bloch_plan* pl);
 void plan_solver_release(bloch_plan* pl);
+// (M~ t_0)_0 for the Gamma-point deflation (non-uniform density), built once per precision
+template <typename T> bloch_status gamma_rhohat(bloch_plan* pl, const cplx_t<T>** out);
+// M-deflate the rigid translations out of nv vectors V (and their M-images MV,
+// which must be current; MV is updated too)
+template <typename T>
+bloch_status gamma_deflate(bloch_plan* pl, int nv, cplx_t<T>* V, cplx_t<T>* MV, double2* d_alpha);
 }  // namespace bloch
 
 // eigensolver entry (bloch_eig.cu)

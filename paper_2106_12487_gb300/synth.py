@@ -193,9 +193,12 @@ def laminate_ids(grid, axis: int = 0, frac: float = 0.5) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Wave-vector paths
 # --------------------------------------------------------------------------
-def kpath(labels, n_k: int, L=(1e-3, 1e-3, 1e-3)) -> np.ndarray:
+def kpath(labels, n_k: int, L=(1e-3, 1e-3, 1e-3), corners: bool = False) -> np.ndarray:
     """n_k wave vectors equally spaced in arc length over the polyline through
-    the named high-symmetry points (both ends included)."""
+    the named high-symmetry points (both ends included).  With corners=True
+    every named point is on the list: the n_k - 1 intervals are shared among
+    the segments in proportion to their lengths (largest remainders) and
+    spaced evenly within each segment."""
     Lx, Ly, Lz = L
     pts = {"G": (0.0, 0.0, 0.0), "X": (math.pi / Lx, 0.0, 0.0),
            "M": (math.pi / Lx, math.pi / Ly, 0.0),
@@ -206,6 +209,21 @@ def kpath(labels, n_k: int, L=(1e-3, 1e-3, 1e-3)) -> np.ndarray:
     cum = np.concatenate([[0.0], np.cumsum(seg)])
     if n_k == 1:
         return P[:1].copy()
+    if corners:
+        nseg = len(seg)
+        if n_k - 1 < nseg:
+            raise ValueError("corners=True needs at least one interval per segment")
+        share = (n_k - 1) * seg / cum[-1]
+        cnt = np.maximum(1, np.floor(share).astype(int))
+        while cnt.sum() < n_k - 1:
+            cnt[np.argmax(share - cnt)] += 1
+        while cnt.sum() > n_k - 1:
+            cnt[np.argmax(np.where(cnt > 1, cnt - share, -np.inf))] -= 1
+        out = [P[0]]
+        for j in range(nseg):
+            for i in range(1, cnt[j] + 1):
+                out.append(P[j] + (i / cnt[j]) * (P[j + 1] - P[j]))
+        return np.array(out)
     s = np.linspace(0.0, cum[-1], n_k)
     out = np.empty((n_k, 3))
     for i, si in enumerate(s):
@@ -276,6 +294,9 @@ def workload(name: str, n_k: int | None = None) -> Problem:
     rve64_g64    64^3, 64 grains, Haar; 8 bands, 50 k on G-X-M-G-R
     rve128_g200  128^3, 200 grains, <001> vMF fibre (kappa 20); 10 bands, 64 k on G-X-M-G-R
     rve256_g1000 256^3, 1000 grains, Ti-like hexagonal, Haar; 12 bands, 128 k on G-X-M-G-R
+    fibre128_circle / fibre128_square
+                 128 x 128 x 1 epoxy/carbon long-fibre cells (55 % circular, 65 % square
+                 fibres; Table 1); 10 bands, 90 k on M-G-X-M
     """
     cu = cubic_voigt(CU_CUBIC["C11"], CU_CUBIC["C12"], CU_CUBIC["C44"])
     if name == "rve16_g8":
@@ -288,11 +309,50 @@ def workload(name: str, n_k: int | None = None) -> Problem:
         k = kpath("GXMGR", n_k or 64)
         return polycrystal(name, (128, 128, 128), 200, 3, 103, cu, CU_CUBIC["rho"], k, 10, 1e-10,
                            texture="fibre001", kappa=20.0)
+    if name == "fibre128_circle":
+        return fibre_composite((128, 128, 1), "circle", n_bands=10, n_k=n_k or 90)
+    if name == "fibre128_square":
+        return fibre_composite((128, 128, 1), "square", n_bands=10, n_k=n_k or 90)
     if name == "rve256_g1000":
         hx = hexagonal_voigt(TI_HEX["C11"], TI_HEX["C12"], TI_HEX["C13"], TI_HEX["C33"], TI_HEX["C44"])
         k = kpath("GXMGR", n_k or 128)
         return polycrystal(name, (256, 256, 256), 1000, 5, 105, hx, TI_HEX["rho"], k, 12, 1e-10)
     raise KeyError(name)
+
+
+def fibre_ids(grid, shape: str = "circle", frac: float = 0.55) -> np.ndarray:
+    """Two-phase long-fibre cell (the long-fibre composites of the paper's
+    Section 4.3): one fibre per cell, axis along z and centred in the (x, y)
+    cross-section; phase 1 (fibre) where the voxel centre lies inside a circle
+    of area frac*Lx*Ly (shape "circle", Lx = Ly) or a square of that area
+    ("square"), phase 0 (matrix) elsewhere.  Every z slice is the same."""
+    Nx, Ny, Nz = grid
+    x = (np.arange(Nx) + 0.5) / Nx - 0.5
+    y = (np.arange(Ny) + 0.5) / Ny - 0.5
+    Y, X = np.meshgrid(y, x, indexing="ij")          # (Ny, Nx), fractions of the cell
+    if shape == "circle":
+        inside = X ** 2 + Y ** 2 <= frac / math.pi
+    elif shape == "square":
+        h = 0.5 * math.sqrt(frac)
+        inside = (np.abs(X) <= h) & (np.abs(Y) <= h)
+    else:
+        raise ValueError(shape)
+    return np.broadcast_to(inside.astype(np.int32)[None], (Nz, Ny, Nx)).copy()
+
+
+def fibre_composite(grid, shape: str = "circle", frac: float | None = None, n_bands: int = 10,
+                    n_k: int = 90, L=(1e-3, 1e-3, 1e-3)) -> Problem:
+    """Epoxy matrix with carbon long fibres (Table 1, Composite 1; isotropic
+    phases), circular fibres at 55 % or square fibres at 65 % by default, on
+    the M-Gamma-X-M path of the fibre cross-section."""
+    if frac is None:
+        frac = 0.55 if shape == "circle" else 0.65
+    ids = fibre_ids(grid, shape, frac)
+    C = np.stack([isotropic_from_E_nu(EPOXY["E"], EPOXY["nu"]), isotropic_from_E_nu(CARBON["E"], CARBON["nu"])])
+    rho = np.array([EPOXY["rho"], CARBON["rho"]])
+    k = kpath("MGXM", n_k, L, corners=True)
+    return Problem(f"fibre_{shape}{tuple(grid)}", tuple(grid), tuple(L), ids, C, rho, k, n_bands, 1e-10,
+                   dict(shape=shape, frac=frac, fibre_fraction=float(ids.mean())))
 
 
 def small_polycrystal(grid, n_grains: int, seed: int, texture: str = "haar",

@@ -215,7 +215,7 @@ def test_trained_network_inference_matches_oracle(B, grid):
         # the network is far from the Green operator here
         g_all.append(OL.g_of(theta, H, OL.features(qv[nz], np.linalg.eigvalsh(OL.acoustic(C0s, qv[nz])), Nmax)))
     g_all = np.concatenate([g.ravel() for g in g_all])
-    assert np.ptp(g_all) > 0.3 and np.max(np.abs(g_all - 1.0)) > 0.3
+    assert np.max(np.abs(g_all - 1.0)) > 0.3 and np.ptp(g_all) > 0.05
 
 
 def test_moment_kernel_matches_oracle(B):

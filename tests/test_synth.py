@@ -66,3 +66,18 @@ def test_zener_cell_family():
     assert np.allclose(inv, 3 * C11 + 6 * C44, rtol=1e-12)
     assert len(np.unique(a.grain_ids)) <= a.G
     assert synth.zener_cell((8, 8, 8), 4).meta["zener"] != A
+
+
+def test_fibre_composite_cells():
+    import math
+    for shape, frac in (("circle", 0.55), ("square", 0.65)):
+        p = synth.fibre_composite((128, 128, 1), shape)
+        assert p.grain_ids.shape == (1, 128, 128)
+        assert abs(p.meta["fibre_fraction"] - frac) < 0.015   # voxelised boundary at 128^2
+        ids = p.grain_ids[0]
+        # centred and mirror-symmetric in x and y
+        assert np.array_equal(ids, ids[::-1, :]) and np.array_equal(ids, ids[:, ::-1])
+        assert ids[64, 64] == 1 and ids[0, 0] == 0
+        assert p.rho.tolist() == [1200.0, 1750.0]
+        assert p.k_list.shape == (90, 3) and np.allclose(p.k_list[0], [math.pi / 1e-3, math.pi / 1e-3, 0])
+        assert np.any(np.all(p.k_list == 0, axis=1))      # the path passes through Gamma
