@@ -356,6 +356,7 @@ static std::vector<StartEntry> start_vectors(const bloch_plan* pl, const double 
 template <typename T>
 struct Subspace {
     using C = cplx_t<T>;
+    static constexpr int kEigThreads = 64;
     bloch_plan* pl;
     int n, q, B;
     long long n3;
@@ -377,6 +378,13 @@ struct Subspace {
     long long* d_idx = nullptr;
     double2 *U64 = nullptr, *KU64 = nullptr, *MU64 = nullptr;
     double2* d_alpha = nullptr;   // Gamma-point deflation coefficients (non-uniform density)
+    // per vector (slot * q + i): Rayleigh-quotient sums and |R|^2 (4 doubles),
+    // 1/lambda, the projected problem's eigenvalues; per slot its status
+    double *d_rq = nullptr, *d_invlam = nullptr, *d_lamq = nullptr;
+    int* d_status = nullptr;
+    long long* d_tally = nullptr;
+    long long tally_host[4] = {0, 0, 0, 0};
+    int eig_pending = 0;          // slots whose projected eigensolve status is read with the next residuals
     int gblk = 0, dblk = 0;
     size_t gsmem = 0;
     // tensor-core Gram (FP32 blocks, options.tensor_gram)
@@ -449,6 +457,14 @@ struct Subspace {
             (s = alloc(&d_val, (size_t)3 * q)))
             return s;
         if (!uniform && (s = alloc(&d_alpha, (size_t)3 * q))) return s;
+        if ((s = alloc(&d_rq, (size_t)B * q * 4)) || (s = alloc(&d_invlam, (size_t)B * q)) ||
+            (s = alloc(&d_lamq, (size_t)B * q)) || (s = alloc(&d_status, (size_t)B)) || (s = alloc(&d_tally, 4)))
+            return s;
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(d_tally, 0, 4 * sizeof(long long), pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(d_rq, 0, (size_t)B * q * 4 * sizeof(double), pl->stream));
+        if (cudaFuncSetAttribute(k_gen_herm_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gen_eig_smem(q, kEigThreads)) != cudaSuccess)
+            return set_error(BLOCH_ECUDA, "cudaFuncSetAttribute (projected eigensolver)");
         if (fp64res) {
             if ((s = alloc(&U64, (size_t)q * n3)) || (s = alloc(&KU64, (size_t)q * n3))) return s;
             if (!uniform && (s = alloc(&MU64, (size_t)q * n3))) return s;
@@ -496,9 +512,8 @@ struct Subspace {
             BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_val, val.data(), sizeof(double2) * val.size(),
                                                  cudaMemcpyHostToDevice, pl->stream));
             ++pl->launches;
+            // (the scatter buffers are rewritten by the next init in stream order)
             k_scatter<T><<<((int)se.size() + 127) / 128, 128, 0, pl->stream>>>(U, d_idx, d_val, (int)se.size());
-            // the scatter buffers are reused by the next init: wait for the copies
-            BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
         }
         return deflate_start(s);
     }
@@ -512,56 +527,21 @@ struct Subspace {
     }
 
     // Rayleigh quotients and residuals of vectors [vo, vo+nvs) of slots
-    // [first, first+count) (nvs == q when count > 1), staged per vector;
-    // residual_finish turns the staged values into the slots' lam, err1, err2.
-    std::vector<double> stg_ukv, stg_umu, stg_kk, stg_r2;
+    // [first, first+count) (nvs == q when count > 1): sums finished on the
+    // device into d_rq, 1/lambda into d_invlam; residual_step reads them back
+    // once and residual_finish turns them into the slots' lam, err1, err2.
+    std::vector<double> stg_rq;
     template <typename TK>
     bloch_status residual_part(int first, int count, int vo, int nvs, const cplx_t<TK>* Uk, const cplx_t<TK>* KUk,
                                const cplx_t<TK>* MUk) {
         const int nv = count * nvs;
         if (nv == 0) return BLOCH_OK;
-        const size_t need = (size_t)B * q;
-        if (stg_ukv.size() < need) {
-            stg_ukv.assign(need, 0.0);
-            stg_umu.assign(need, 0.0);
-            stg_kk.assign(need, 0.0);
-            stg_r2.assign(need, 0.0);
-        }
         dim3 gr(dblk, nv);
-        ++pl->launches;
+        pl->launches += 4;
         k_rq_dots<TK><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, n3, d_part);
-        std::vector<double> part((size_t)nv * dblk * 3);
-        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
-                                             cudaMemcpyDeviceToHost, pl->stream));
-        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        std::vector<double> inv(nv);
-        for (int v = 0; v < nv; ++v) {
-            double a = 0, b = 0, c = 0;
-            for (int j = 0; j < dblk; ++j) {
-                a += part[((size_t)v * dblk + j) * 3 + 0];
-                b += part[((size_t)v * dblk + j) * 3 + 1];
-                c += part[((size_t)v * dblk + j) * 3 + 2];
-            }
-            const size_t at = (size_t)(first + v / nvs) * q + vo + v % nvs;
-            stg_ukv[at] = a;
-            stg_umu[at] = b;
-            stg_kk[at] = c;
-            const double lam = (b > 0) ? a / b : 0.0;
-            inv[v] = lam > 0 ? 1.0 / lam : 0.0;
-        }
-        BLOCH_CUDA_CHECK_RET(
-            cudaMemcpyAsync(d_scal, inv.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, pl->stream));
-        ++pl->launches;
+        k_rq_final<<<nv, 128, 0, pl->stream>>>(d_part, dblk, first, nvs, vo, q, d_rq, d_scal, d_invlam);
         k_residual<TK, T><<<gr, 256, 0, pl->stream>>>(Uk, KUk, MUk, rho_s, d_scal, vec(R, first, vo), n3, d_part);
-        std::vector<double> rp((size_t)nv * dblk);
-        BLOCH_CUDA_CHECK_RET(
-            cudaMemcpyAsync(rp.data(), d_part, sizeof(double) * rp.size(), cudaMemcpyDeviceToHost, pl->stream));
-        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        for (int v = 0; v < nv; ++v) {
-            double r2 = 0;
-            for (int j = 0; j < dblk; ++j) r2 += rp[(size_t)v * dblk + j];
-            stg_r2[(size_t)(first + v / nvs) * q + vo + v % nvs] = r2;
-        }
+        k_r2_final<<<nv, 128, 0, pl->stream>>>(d_part, dblk, first, nvs, vo, q, d_rq);
         return BLOCH_OK;
     }
 
@@ -573,11 +553,11 @@ struct Subspace {
             sl.unorm2.assign(q, 0.0);
             double e2 = 0;
             for (int i = 0; i < q; ++i) {
-                const size_t at = (size_t)(first + s) * q + i;
-                const double lam = stg_umu[at] > 0 ? stg_ukv[at] / stg_umu[at] : 0.0;
+                const double* r = stg_rq.data() + ((size_t)s * q + i) * 4;   // (ukv, umu, kk, r2)
+                const double lam = r[1] > 0 ? r[0] / r[1] : 0.0;
                 sl.lam[i] = lam;
-                sl.unorm2[i] = stg_umu[at];
-                if (i < sl.n_eff && stg_kk[at] > 0) e2 = std::max(e2, lam * std::sqrt(stg_r2[at]) / std::sqrt(stg_kk[at]));
+                sl.unorm2[i] = r[1];
+                if (i < sl.n_eff && r[2] > 0) e2 = std::max(e2, lam * std::sqrt(r[3]) / std::sqrt(r[2]));
             }
             sl.err2_prev = sl.err2;
             sl.err2 = e2;
@@ -608,7 +588,6 @@ struct Subspace {
                 if ((s = residual_part<T>(i, j - i, 0, q, vec(U, i), vec(KU, i), uniform ? nullptr : vec(MU, i))) !=
                     BLOCH_OK)
                     return s;
-                residual_finish(i, j - i);
                 i = j;
             } else {
                 // FP64 refinement: residuals and Rayleigh quotients of the wanted
@@ -634,11 +613,32 @@ struct Subspace {
                                               uniform ? nullptr : vec(MU, i, nw))) != BLOCH_OK)
                         return s;
                 }
-                residual_finish(i, 1);
                 ++i;
             }
         }
         BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        // the one host synchronisation of a sweep: residual sums, the status of
+        // the projected eigensolves that preceded them, PCG totals
+        stg_rq.resize((size_t)count * q * 4);
+        std::vector<int> stat(std::max(eig_pending, 1), 0);
+        long long tl[4];
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(stg_rq.data(), d_rq + (size_t)first * q * 4,
+                                             sizeof(double) * stg_rq.size(), cudaMemcpyDeviceToHost, pl->stream));
+        if (eig_pending)
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(stat.data(), d_status, sizeof(int) * eig_pending,
+                                                 cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(tl, d_tally, sizeof(tl), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        st->cg_iterations += tl[0] - tally_host[0];
+        st->k_applies += tl[0] - tally_host[0];
+        pl->launches += (unsigned long long)(tl[3] - tally_host[3]) * (unsigned long long)pl->pcg_launches_per_iter;
+        const bool nonfinite = tl[2] > tally_host[2];
+        for (int t = 0; t < 4; ++t) tally_host[t] = tl[t];
+        if (nonfinite) return set_error(BLOCH_ENONFINITE, "PCG met a non-finite residual");
+        for (int t = 0; t < eig_pending; ++t)
+            if (stat[t] == 1) return set_error(BLOCH_ENOTCONV_EIG, "projected mass matrix lost definiteness");
+        eig_pending = 0;
+        residual_finish(first, count);
         return BLOCH_OK;
     }
 
@@ -694,6 +694,10 @@ struct Subspace {
         if (!uniform)
             BLOCH_CUDA_CHECK_RET(
                 cudaMemcpyAsync(vec(MU, to), vec(MU, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_invlam + (size_t)to * q, d_invlam + (size_t)from * q,
+                                             sizeof(double) * q, cudaMemcpyDeviceToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_rq + (size_t)to * q * 4, d_rq + (size_t)from * q * 4,
+                                             sizeof(double) * q * 4, cudaMemcpyDeviceToDevice, pl->stream));
         slots[to] = slots[from];
         if (warm) {
             seg_next[to] = seg_next[from];
@@ -803,26 +807,18 @@ struct Subspace {
                     if ((s = residual_step(f, 1)) != BLOCH_OK) return s;
                 if (nact == 0) break;
             }
-            // inverse step on all active slots: delta = A^-1 R
+            // inverse step on all active slots: delta = A^-1 R (enqueued; no host wait)
             if ((s = set_k_range(0, nact)) != BLOCH_OK) return s;
             if ((s = lp_activate<T>(pl, nact, q, q)) != BLOCH_OK) return s;
-            long long cg_it = 0;
-            s = pcg_run<T>(pl, nact * q, R, Ub, 1.0, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
+            s = pcg_enqueue<T>(pl, nact * q, R, Ub, 1.0, tol_lin, max_cg, d_tally);
             lp_deactivate(pl);
-            st->cg_iterations += cg_it;
-            st->k_applies += cg_it;
+            if (s != BLOCH_OK) return s;
             st->linear_solves += (long long)nact * q;
-            if (s != BLOCH_OK && s != BLOCH_ENOTCONV_CG) return s;
-            // U_bar = delta + U / lam
+            // U_bar = delta + U / lam (1/lam from the device)
             const int tr_proj = trace_begin(pl, TR_PROJECT);
-            std::vector<double> inv((size_t)nact * q);
-            for (int i = 0; i < nact; ++i)
-                for (int j = 0; j < q; ++j) inv[(size_t)i * q + j] = slots[i].lam[j] > 0 ? 1.0 / slots[i].lam[j] : 0.0;
-            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_scal, inv.data(), sizeof(double) * inv.size(),
-                                                 cudaMemcpyHostToDevice, pl->stream));
             dim3 gv(dblk, nact * q);
             ++pl->launches;
-            k_add_scaled<T><<<gv, 256, 0, pl->stream>>>(Ub, U, d_scal, n3);
+            k_add_scaled<T><<<gv, 256, 0, pl->stream>>>(Ub, U, d_invlam, n3);
             // Kn = M U - r_cg (into KU), Mn = M U_bar
             const size_t ne = (size_t)nact * q * n3;
             ++pl->launches;
@@ -856,39 +852,22 @@ struct Subspace {
                 k_gram_final<<<dim3((2 * npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair,
                                                                                            nact, d_G);
             }
+            // EIG(K, M) of every slot on the device (FP64), then U = U_bar Q
+            ++pl->launches;
+            k_gen_herm_eig<<<nact, kEigThreads, gen_eig_smem(q, kEigThreads), pl->stream>>>(
+                q, d_G, d_G + (size_t)nact * npair, uniform ? rho_s : 1.0, d_lamq, d_Q, d_status);
+            eig_pending = nact;
+            for (int i = 0; i < nact; ++i) slots[i].sweeps += 1;
+            ++pl->launches;
+            launch_basis<T>(pl->stream, nact, Ub, U, d_Q, q, n3);
             trace_end(pl, tr_proj);
-            std::vector<double2> G((size_t)2 * nact * npair);
-            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(G.data(), d_G, sizeof(double2) * G.size(), cudaMemcpyDeviceToHost,
-                                                 pl->stream));
-            int gerr = 0;
-            if (use_tc)
-                BLOCH_CUDA_CHECK_RET(
-                    cudaMemcpyAsync(&gerr, d_gerr, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
-            BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-            if (gerr) return set_error(BLOCH_ECUDA, "tensor-core Gram: a wait for the MMAs timed out");
-            std::vector<double2> Qh((size_t)nact * npair);
-            for (int i = 0; i < nact; ++i) {
-                std::vector<cd> Km(npair), Mm(npair), Qm;
-                const double ms = uniform ? rho_s : 1.0;
-                for (int t = 0; t < npair; ++t) {
-                    const double2 a = G[(size_t)i * npair + t], b = G[(size_t)(nact + i) * npair + t];
-                    Km[t] = cd(a.x, a.y);
-                    Mm[t] = cd(b.x, b.y) * ms;
-                }
-                std::vector<double> lam;
-                const int rc = gen_herm_eig(q, Km.data(), Mm.data(), lam, Qm);
-                if (rc == 1) return set_error(BLOCH_ENOTCONV_EIG, "projected mass matrix lost definiteness");
-                for (int t = 0; t < npair; ++t) Qh[(size_t)i * npair + t] = make_double2(Qm[t].real(), Qm[t].imag());
-                slots[i].sweeps += 1;
-            }
-            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_Q, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice,
-                                                 pl->stream));
-            {
-                TraceScope tr(pl, TR_PROJECT);
-                ++pl->launches;
-                launch_basis<T>(pl->stream, nact, Ub, U, d_Q, q, n3);
-            }
             BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+            if (use_tc) {
+                int gerr = 0;
+                BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(&gerr, d_gerr, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+                BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+                if (gerr) return set_error(BLOCH_ECUDA, "tensor-core Gram: a wait for the MMAs timed out");
+            }
             if ((s = residual_step(0, nact)) != BLOCH_OK) return s;
         }
         return BLOCH_OK;
@@ -957,18 +936,31 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
 // Shift-invert Lanczos with thick restart (Section 3.3, Eqs. shift and
 // def_invop): Lanczos on OP = A_k^-1 M in the M inner product; the n largest
 // Ritz values theta of OP give lambda = 1/theta.  Restarting keeps the
-// kk = n + (m - n)/2 wanted Ritz vectors and the residual vector (thick
-// restart, equivalent to implicit restart with exact shifts).  Each slot (one
-// wave vector) advances one Lanczos step per iteration; all slots share one
-// batched PCG per step.  Orthogonalisation: classical Gram-Schmidt applied
-// twice against the whole basis.
+// kk = n + (m - n)/2 leading Ritz vectors and the residual vector (thick
+// restart, equivalent to implicit restart with exact shifts).
+//
+// Device resident: the slots (one wave vector each) advance in lockstep,
+// one Lanczos step per slot per step, all slots sharing one batched PCG
+// (Algorithm 2, graph-resident loop).  Every step -- the PCG, the two passes
+// of classical Gram-Schmidt in the M inner product, the Lanczos coefficients
+// and the normalisation -- runs on the device with no host synchronisation;
+// the Ritz analysis of a restart (an FP64 Jacobi eigensolve per slot) runs on
+// the device too, so the host synchronises once per restart cycle to read the
+// convergence flags.  Converged slots are compacted out at a restart; a new
+// batch of wave vectors starts when a batch is finished.
+//
+// A non-uniform density keeps the M-images of the basis vectors beside them
+// (one mass-operator apply per step); at k = 0 the rigid translations are
+// M-deflated from the start vector and from every new Lanczos vector.
 // ====================================================================
 template <typename T>
 struct Lanczos {
     using C = cplx_t<T>;
+    static constexpr int kThreadsRitz = 64;
     bloch_plan* pl;
     int n_bands, m, B;
     long long n3;
+    bool uniform = true;
     double rho_s, tol_eig, tol_lin;
     int max_outer, max_cg;
     const std::vector<std::array<double, 3>>* klist;
@@ -983,306 +975,300 @@ struct Lanczos {
     C* ritz_out = nullptr;
     int q_out = 0;
 
-    C *Vb = nullptr, *Tmp = nullptr, *Bc = nullptr, *Xc = nullptr;
-    double2 *d_part = nullptr, *d_h = nullptr, *d_Q = nullptr;
-    int* d_nv = nullptr;
-    long long *d_src = nullptr, *d_dst = nullptr;
-    double* d_s = nullptr;
+    C *Vb = nullptr, *MVb = nullptr, *Tmp = nullptr, *TmpM = nullptr, *Bc = nullptr, *Xc = nullptr, *MXc = nullptr;
+    double2 *d_part = nullptr, *d_h = nullptr, *d_Q = nullptr, *d_H = nullptr, *d_alpha = nullptr;
+    int *d_nv = nullptr, *d_neff = nullptr, *d_conv = nullptr, *d_jac = nullptr;
+    double *d_s = nullptr, *d_theta = nullptr, *d_est = nullptr;
+    long long* d_tally = nullptr;
     int nblk = 0;
+    long long tally_host[4] = {0, 0, 0, 0};
 
     struct Slot {
         int kidx = -1;
         double k[3];
         bool gamma = false;
         int n_eff = 0;
-        int j = 0;
-        int restarts = 0;
-        std::vector<cd> H;   // (m+1) x m
     };
     std::vector<Slot> slots;
     int nact = 0;
+    int restarts = 0;   // of the current batch (lockstep)
+
     int nalloc = 0;   // buffers taken from the plan's pool 1
     template <typename X>
     bloch_status alloc(X** p, size_t n_el) {
         return plan_solver_buf(pl, 1, nalloc++, n_el * sizeof(X), (void**)p);
     }
+    long long stride() const { return (long long)(m + 1) * n3; }
     C* vb(int s, int i) const { return Vb + ((size_t)s * (m + 1) + i) * n3; }
+    C* mvb(int s, int i) const { return MVb + ((size_t)s * (m + 1) + i) * n3; }
+    int kk_restart() const { return std::min(m - 1, n_bands + (m - n_bands) / 2); }
+    int kk_out() const { return ritz_out ? std::min(m, q_out) : n_bands; }
+    unsigned gx() const { return (unsigned)std::max(1LL, std::min<long long>((n3 + 255) / 256, 2048 / std::max(1, B))); }
 
     bloch_status setup() {
         bloch_status s;
         nblk = (int)std::max(1LL, std::min<long long>((n3 + 255) / 256, std::max(1, 1024 / std::max(1, B))));
-        if ((s = alloc(&Vb, (size_t)B * (m + 1) * n3)) || (s = alloc(&Tmp, (size_t)m * n3)) ||
+        if ((s = alloc(&Vb, (size_t)B * (m + 1) * n3)) || (s = alloc(&Tmp, (size_t)B * m * n3)) ||
             (s = alloc(&Bc, (size_t)B * n3)) || (s = alloc(&Xc, (size_t)B * n3)) ||
             (s = alloc(&d_part, (size_t)B * nblk * (m + 1))) || (s = alloc(&d_h, (size_t)B * (m + 1))) ||
-            (s = alloc(&d_Q, (size_t)m * m)) || (s = alloc(&d_nv, (size_t)B)) || (s = alloc(&d_src, (size_t)B)) ||
-            (s = alloc(&d_dst, (size_t)B)) || (s = alloc(&d_s, (size_t)B)))
+            (s = alloc(&d_Q, (size_t)B * m * m)) || (s = alloc(&d_H, (size_t)B * (m + 1) * m)) ||
+            (s = alloc(&d_nv, (size_t)B)) || (s = alloc(&d_neff, (size_t)B)) || (s = alloc(&d_conv, (size_t)B)) ||
+            (s = alloc(&d_jac, (size_t)B)) || (s = alloc(&d_s, (size_t)B)) ||
+            (s = alloc(&d_theta, (size_t)B * m)) || (s = alloc(&d_est, (size_t)B * m)) || (s = alloc(&d_tally, 4)))
             return s;
+        if (!uniform) {
+            if ((s = alloc(&MVb, (size_t)B * (m + 1) * n3)) || (s = alloc(&TmpM, (size_t)B * m * n3)) ||
+                (s = alloc(&MXc, (size_t)B * n3)) || (s = alloc(&d_alpha, 3)))
+                return s;
+        }
         if ((s = ensure_cg<T>(pl, B)) != BLOCH_OK) return s;
+        if (!uniform && (s = ensure_ws<T>(pl, B)) != BLOCH_OK) return s;
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(d_tally, 0, 4 * sizeof(long long), pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaFuncSetAttribute(k_lz_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)lz_ritz_smem(m, kThreadsRitz)));
         slots.assign(B, Slot());
         return BLOCH_OK;
     }
 
-    bloch_status upload_ll(long long* d, const std::vector<long long>& h) {
-        BLOCH_CUDA_CHECK_RET(
-            cudaMemcpyAsync(d, h.data(), sizeof(long long) * h.size(), cudaMemcpyHostToDevice, pl->stream));
-        return BLOCH_OK;
-    }
-
-    // M-norms of Xc[0..nact) -> host
-    bloch_status xnorms(std::vector<double>& nrm) {
-        Workspace<T>& w = ws_of<T>(pl);
-        launch_dot<T>(pl, nact, Xc, Xc, n3, w.dots, w.part2);
-        std::vector<double2> d(nact);
-        BLOCH_CUDA_CHECK_RET(
-            cudaMemcpyAsync(d.data(), w.dots, sizeof(double2) * nact, cudaMemcpyDeviceToHost, pl->stream));
-        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        nrm.resize(nact);
-        for (int i = 0; i < nact; ++i) nrm[i] = std::sqrt(std::max(0.0, rho_s * d[i].x));
-        return BLOCH_OK;
-    }
-
-    bloch_status init_slot(int s, int kidx) {
-        Slot& sl = slots[s];
-        sl = Slot();
-        sl.kidx = kidx;
-        for (int a = 0; a < 3; ++a) sl.k[a] = (*klist)[kidx][a];
-        sl.gamma = sl.k[0] == 0.0 && sl.k[1] == 0.0 && sl.k[2] == 0.0;
-        sl.n_eff = sl.gamma ? n_bands - 3 : n_bands;
-        sl.j = 0;
-        sl.H.assign((size_t)(m + 1) * m, cd(0, 0));
-        ++pl->launches;
-        k_start_random<T><<<1024, 256, 0, pl->stream>>>(vb(s, 0), n3, pl->V, 12345ULL, sl.gamma ? 1 : 0);
-        // normalise in the M norm
-        Workspace<T>& w = ws_of<T>(pl);
-        launch_dot<T>(pl, 1, vb(s, 0), vb(s, 0), n3, w.dots, w.part2);
-        double2 d;
-        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(&d, w.dots, sizeof(double2), cudaMemcpyDeviceToHost, pl->stream));
-        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-        const double sc = 1.0 / std::sqrt(rho_s * d.x);
-        ++pl->launches;
-        k_scale<T><<<1024, 256, 0, pl->stream>>>(vb(s, 0), vb(s, 0), T(sc), (size_t)n3);
-        return BLOCH_OK;
-    }
-
-    // Ritz analysis of a slot whose basis is full: converge (output) or restart.
-    // Returns true when the slot is finished.
-    bool ritz(int s, bloch_status& err) {
-        Slot& sl = slots[s];
-        std::vector<cd> Hm((size_t)m * m);
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < m; ++j)
-                Hm[(size_t)i * m + j] = 0.5 * (sl.H[(size_t)i * m + j] + std::conj(sl.H[(size_t)j * m + i]));
-        std::vector<double> w;
-        std::vector<cd> Y;
-        herm_jacobi(m, Hm, w, Y);
-        const double beta = std::abs(sl.H[(size_t)m * m + (m - 1)]);
-        // wanted: largest theta (descending)
-        std::vector<int> idx(m);
-        for (int i = 0; i < m; ++i) idx[i] = m - 1 - i;
-        bool conv = true;
-        for (int i = 0; i < sl.n_eff; ++i) {
-            const double th = w[idx[i]];
-            const double res = beta * std::abs(Y[(size_t)(m - 1) * m + idx[i]]);
-            if (!(th > 0.0) || res > tol_eig * std::fabs(th)) conv = false;
+    // q tables, per-slot band counts and the learned tables for the current slot order
+    bloch_status bind_slots() {
+        std::vector<double> kv((size_t)nact * 3);
+        std::vector<int> ne(nact);
+        for (int i = 0; i < nact; ++i) {
+            for (int a = 0; a < 3; ++a) kv[(size_t)i * 3 + a] = slots[i].k[a];
+            ne[i] = slots[i].n_eff;
         }
-        sl.restarts += 1;
-        const bool done = conv || sl.restarts > max_outer;
-        const int kk = done ? (ritz_out ? std::min(m, q_out) : sl.n_eff)
-                            : std::min(m - 1, sl.n_eff + (m - sl.n_eff) / 2);
-        // Q: m x m, columns = the kept Ritz vectors (descending theta), rest zero
-        std::vector<double2> Qh((size_t)m * m, make_double2(0, 0));
-        for (int c = 0; c < kk; ++c)
-            for (int i = 0; i < m; ++i) {
-                const cd y = Y[(size_t)i * m + idx[c]];
-                Qh[(size_t)i * m + c] = make_double2(y.real(), y.imag());
+        bloch_status s;
+        if ((s = set_k<T>(pl, nact, kv.data())) != BLOCH_OK) return s;
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_neff, ne.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, pl->stream));
+        if ((s = lp_activate<T>(pl, nact, 1, 1)) != BLOCH_OK) return s;
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));   // host vectors above leave scope
+        return BLOCH_OK;
+    }
+
+    // M-image of the nact vectors in Bc into MXc, and the Gamma deflation of both
+    bloch_status m_image_and_deflate() {
+        launch_M<T>(pl, nact, Bc, MXc, T(1));
+        for (int i = 0; i < nact; ++i)
+            if (slots[i].gamma) {
+                bloch_status s = gamma_deflate<T>(pl, 1, Bc + (size_t)i * n3, MXc + (size_t)i * n3, d_alpha);
+                if (s != BLOCH_OK) return s;
             }
-        cudaError_t e = cudaMemcpyAsync(d_Q, Qh.data(), sizeof(double2) * Qh.size(), cudaMemcpyHostToDevice,
-                                        pl->stream);
-        if (e != cudaSuccess) {
-            err = set_cuda_error(e, "Lanczos restart upload");
-            return true;
+        return BLOCH_OK;
+    }
+
+    // a new batch of wave vectors: random start vectors, M-normalised
+    bloch_status start_batch() {
+        nact = 0;
+        while (nact < B && next_k < order.size()) {
+            Slot& sl = slots[nact];
+            sl = Slot();
+            sl.kidx = order[next_k++];
+            for (int a = 0; a < 3; ++a) sl.k[a] = (*klist)[sl.kidx][a];
+            sl.gamma = sl.k[0] == 0.0 && sl.k[1] == 0.0 && sl.k[2] == 0.0;
+            sl.n_eff = sl.gamma ? n_bands - 3 : n_bands;
+            ++pl->launches;
+            k_start_random<T><<<1024, 256, 0, pl->stream>>>(Bc + (size_t)nact * n3, n3, pl->V, 12345ULL,
+                                                            sl.gamma ? 1 : 0);
+            ++nact;
         }
+        restarts = 0;
+        bloch_status s;
+        if ((s = bind_slots()) != BLOCH_OK) return s;
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(d_H, 0, sizeof(double2) * (size_t)nact * (m + 1) * m, pl->stream));
+        Workspace<T>& w = ws_of<T>(pl);
+        if (uniform) {
+            launch_dot<T>(pl, nact, Bc, Bc, n3, w.dots, w.part2);
+        } else {
+            if ((s = m_image_and_deflate()) != BLOCH_OK) return s;
+            launch_dot<T>(pl, nact, Bc, MXc, n3, w.dots, w.part2);
+        }
+        pl->launches += 2;
+        k_lz_norm<<<(nact + 63) / 64, 64, 0, pl->stream>>>(w.dots, uniform ? rho_s : 1.0, d_H, -1, m, nact, d_s);
+        k_put_col<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(Bc, Vb, stride(), 0, n3, d_s);
+        if (!uniform) {
+            ++pl->launches;
+            k_put_col<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(MXc, MVb, stride(), 0, n3, d_s);
+        }
+        BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        return BLOCH_OK;
+    }
+
+    // one Lanczos step j -> j + 1 on every slot (no host synchronisation)
+    bloch_status step(int j) {
+        bloch_status s;
+        Workspace<T>& w = ws_of<T>(pl);
         ++pl->launches;
-        launch_basis<T>(pl->stream, 1, vb(s, 0), Tmp, d_Q, m, n3);
-        if (done) {
-            const double lam_scale = pl->Kscale / pl->rho_ref;
-            double* om = omega_out + (size_t)sl.kidx * n_bands;
-            int b0 = 0;
-            if (sl.gamma)
-                for (; b0 < std::min(3, n_bands); ++b0) om[b0] = 0.0;
-            // ascending lambda = descending theta = order of the kept columns
-            for (int i = 0; i < sl.n_eff; ++i) {
-                const double th = w[idx[i]];
-                om[b0 + i] = th > 0 ? std::sqrt(lam_scale / th) : 0.0;
-            }
-            st->outer_iterations += sl.restarts;
-            double mx = 0;
-            for (int i = 0; i < sl.n_eff; ++i) {
-                const double th = w[idx[i]];
-                mx = std::max(mx, beta * std::abs(Y[(size_t)(m - 1) * m + idx[i]]) / std::max(std::fabs(th), 1e-300));
-            }
-            st->max_rel_residual = std::max(st->max_rel_residual, mx);
-            if (!conv) {
-                any_unconverged = true;
-                if (!ritz_out) st->k_unconverged += 1;   // the hybrid's refinement decides for it
-            }
-            if (ritz_out) {
-                size_t pos = 0;
-                while (pos < order.size() && order[pos] != sl.kidx) ++pos;
-                C* dst = ritz_out + pos * (size_t)q_out * n3;
-                cudaMemcpyAsync(dst, Tmp, sizeof(C) * (size_t)kk * n3, cudaMemcpyDeviceToDevice, pl->stream);
-                if (kk < q_out)
-                    cudaMemsetAsync(dst + (size_t)kk * n3, 0, sizeof(C) * (size_t)(q_out - kk) * n3, pl->stream);
-            }
-            if (vecs_out) {
-                C* out = (C*)vecs_out + (size_t)sl.kidx * n_bands * n3;
-                const double nv = 1.0 / std::sqrt(pl->rho_ref);
-                if (sl.gamma) {
-                    cudaMemsetAsync(out, 0, sizeof(C) * std::min(3, n_bands) * n3, pl->stream);
-                    std::vector<double2> one(1, make_double2(1.0 / std::sqrt(pl->rho_ref * rho_s), 0.0));
-                    for (int c = 0; c < std::min(3, n_bands); ++c) {
-                        const C cv = mk(T(one[0].x), T(0));
-                        cudaMemcpyAsync(out + (size_t)c * n3 + (size_t)c * pl->V, &cv, sizeof(C),
-                                        cudaMemcpyHostToDevice, pl->stream);
-                        cudaStreamSynchronize(pl->stream);
-                    }
-                }
+        k_get_col<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(uniform ? Vb : MVb, stride(), j, n3, nullptr, Bc);
+        pl->trace_pcg = TR_PCG_LZ;
+        s = pcg_enqueue<T>(pl, nact, Bc, Xc, uniform ? rho_s : 1.0, tol_lin, max_cg, d_tally);
+        pl->trace_pcg = TR_PCG_SUB;
+        if (s != BLOCH_OK) return s;
+        st->linear_solves += nact;
+        const int tr_orth = trace_begin(pl, TR_ORTHO);
+        if (!uniform) {
+            launch_M<T>(pl, nact, Xc, MXc, T(1));
+            for (int i = 0; i < nact; ++i)
+                if (slots[i].gamma &&
+                    (s = gamma_deflate<T>(pl, 1, Xc + (size_t)i * n3, MXc + (size_t)i * n3, d_alpha)) != BLOCH_OK)
+                    return s;
+        }
+        const int nv = j + 1;
+        ++pl->launches;
+        k_fill_int<<<1, 64, 0, pl->stream>>>(d_nv, nact, nv);
+        const C* Wm = uniform ? Xc : MXc;
+        const double sc = uniform ? rho_s : 1.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            pl->launches += 4;
+            k_vdots<T><<<dim3(nblk, nv, nact), 256, 0, pl->stream>>>(Vb, stride(), Wm, n3, d_nv, n3, nv, d_part);
+            k_vdots_final<<<dim3(nv, nact), 256, 0, pl->stream>>>(d_part, nblk, nv, sc, d_h);
+            k_vaxpy<T><<<dim3(nblk, nact), 256, 0, pl->stream>>>(Vb, stride(), Xc, n3, d_h, d_nv, n3, nv);
+            if (!uniform) {
                 ++pl->launches;
-                k_scale<T><<<1024, 256, 0, pl->stream>>>(Tmp, out + (size_t)b0 * n3, T(nv), (size_t)sl.n_eff * n3);
+                k_vaxpy<T><<<dim3(nblk, nact), 256, 0, pl->stream>>>(MVb, stride(), MXc, n3, d_h, d_nv, n3, nv);
             }
-            cudaStreamSynchronize(pl->stream);
-            return true;
+            k_h_accum<<<nact, 64, 0, pl->stream>>>(d_H, d_h, nv, nv, j, m);
         }
-        // restart: V[0..kk) = V Y_kk, V[kk] = v_{m}; H = [diag(theta); b^T]
-        cudaMemcpyAsync(vb(s, 0), Tmp, sizeof(C) * kk * n3, cudaMemcpyDeviceToDevice, pl->stream);
-        cudaMemcpyAsync(vb(s, kk), vb(s, m), sizeof(C) * n3, cudaMemcpyDeviceToDevice, pl->stream);
-        std::fill(sl.H.begin(), sl.H.end(), cd(0, 0));
-        const cd bm = sl.H.size() ? cd(beta, 0) : cd(0, 0);
-        for (int c = 0; c < kk; ++c) {
-            sl.H[(size_t)c * m + c] = w[idx[c]];
-            sl.H[(size_t)kk * m + c] = bm * Y[(size_t)(m - 1) * m + idx[c]];
+        launch_dot<T>(pl, nact, Xc, Wm, n3, w.dots, w.part2);
+        pl->launches += 2;
+        k_lz_norm<<<(nact + 63) / 64, 64, 0, pl->stream>>>(w.dots, sc, d_H, j, m, nact, d_s);
+        k_put_col<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(Xc, Vb, stride(), j + 1, n3, d_s);
+        if (!uniform) {
+            ++pl->launches;
+            k_put_col<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(MXc, MVb, stride(), j + 1, n3, d_s);
         }
-        sl.j = kk;
-        return false;
+        trace_end(pl, tr_orth);
+        BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        return BLOCH_OK;
+    }
+
+    // outputs of a slot whose Ritz vectors are in Tmp[s] (descending theta)
+    void finish_slot(int s, const double* th, const double* es, bool conv) {
+        Slot& sl = slots[s];
+        const double lam_scale = pl->Kscale / pl->rho_ref;
+        double* om = omega_out + (size_t)sl.kidx * n_bands;
+        int b0 = 0;
+        if (sl.gamma)
+            for (; b0 < std::min(3, n_bands); ++b0) om[b0] = 0.0;
+        double mx = 0.0;
+        for (int i = 0; i < sl.n_eff; ++i) {
+            om[b0 + i] = th[i] > 0 ? std::sqrt(lam_scale / th[i]) : 0.0;
+            mx = std::max(mx, es[i] / std::max(std::fabs(th[i]), 1e-300));
+        }
+        st->outer_iterations += restarts;
+        st->max_rel_residual = std::max(st->max_rel_residual, mx);
+        if (!conv) {
+            any_unconverged = true;
+            if (!ritz_out) st->k_unconverged += 1;   // the hybrid's refinement decides for it
+        }
+        const C* ts = Tmp + (size_t)s * m * n3;
+        if (ritz_out) {
+            size_t pos = 0;
+            while (pos < order.size() && order[pos] != sl.kidx) ++pos;
+            C* dst = ritz_out + pos * (size_t)q_out * n3;
+            const int kc = kk_out();
+            cudaMemcpyAsync(dst, ts, sizeof(C) * (size_t)kc * n3, cudaMemcpyDeviceToDevice, pl->stream);
+            if (kc < q_out)
+                cudaMemsetAsync(dst + (size_t)kc * n3, 0, sizeof(C) * (size_t)(q_out - kc) * n3, pl->stream);
+        }
+        if (vecs_out) {
+            C* out = (C*)vecs_out + (size_t)sl.kidx * n_bands * n3;
+            if (sl.gamma) {
+                cudaMemsetAsync(out, 0, sizeof(C) * std::min(3, n_bands) * n3, pl->stream);
+                const C cv = mk(T(1.0 / std::sqrt(pl->rho_ref * rho_s)), T(0));
+                for (int c = 0; c < std::min(3, n_bands); ++c)
+                    cudaMemcpyAsync(out + (size_t)c * n3 + (size_t)c * pl->V, &cv, sizeof(C), cudaMemcpyHostToDevice,
+                                    pl->stream);
+                cudaStreamSynchronize(pl->stream);   // cv leaves scope
+            }
+            ++pl->launches;
+            k_scale<T><<<1024, 256, 0, pl->stream>>>(ts, out + (size_t)b0 * n3, T(1.0 / std::sqrt(pl->rho_ref)),
+                                                     (size_t)sl.n_eff * n3);
+        }
+    }
+
+    // restart analysis of every slot (device), one host synchronisation;
+    // converged slots are finished and compacted out
+    bloch_status restart() {
+        const int kr = kk_restart();
+        const int kc = std::max(kr, kk_out());
+        pl->launches += 3;
+        k_lz_ritz<<<nact, kThreadsRitz, lz_ritz_smem(m, kThreadsRitz), pl->stream>>>(
+            m, d_H, d_neff, tol_eig, kc, kr, d_Q, d_theta, d_est, d_conv, d_jac);
+        launch_basis<T>(pl->stream, nact, Vb, Tmp, d_Q, m, n3, stride());
+        k_lz_restart_copy<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(Vb, Tmp, m, kr, n3);
+        if (!uniform) {
+            pl->launches += 2;
+            launch_basis<T>(pl->stream, nact, MVb, TmpM, d_Q, m, n3, stride());
+            k_lz_restart_copy<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(MVb, TmpM, m, kr, n3);
+        }
+        BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        std::vector<double> th((size_t)nact * m), es((size_t)nact * m);
+        std::vector<int> cv(nact), jo(nact);
+        long long tl[4];
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(th.data(), d_theta, sizeof(double) * th.size(), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(es.data(), d_est, sizeof(double) * es.size(), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(cv.data(), d_conv, sizeof(int) * nact, cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(jo.data(), d_jac, sizeof(int) * nact, cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(tl, d_tally, sizeof(tl), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        // PCG totals since the previous restart
+        st->cg_iterations += tl[0] - tally_host[0];
+        st->k_applies += tl[0] - tally_host[0];
+        pl->launches += (unsigned long long)(tl[3] - tally_host[3]) * (unsigned long long)pl->pcg_launches_per_iter;
+        const bool nonfinite = tl[2] > tally_host[2];
+        for (int i = 0; i < 4; ++i) tally_host[i] = tl[i];
+        if (nonfinite) return set_error(BLOCH_ENONFINITE, "PCG met a non-finite residual in a Lanczos step");
+        restarts += 1;
+        std::vector<char> done(nact, 0);
+        for (int i = 0; i < nact; ++i) {
+            const bool conv = cv[i] != 0 && jo[i] != 0;
+            if (conv || restarts > max_outer) {
+                finish_slot(i, th.data() + (size_t)i * m, es.data() + (size_t)i * m, conv);
+                done[i] = 1;
+            }
+        }
+        // compact: move the last active slot into each hole (basis kr + 1 vectors, H)
+        int last = nact - 1;
+        for (int h = 0; h < nact; ++h) {
+            if (!done[h]) continue;
+            while (last > h && done[last]) --last;
+            if (last <= h) break;
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vb(h, 0), vb(last, 0), sizeof(C) * (size_t)(kr + 1) * n3,
+                                                 cudaMemcpyDeviceToDevice, pl->stream));
+            if (!uniform)
+                BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(mvb(h, 0), mvb(last, 0), sizeof(C) * (size_t)(kr + 1) * n3,
+                                                     cudaMemcpyDeviceToDevice, pl->stream));
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_H + (size_t)h * (m + 1) * m, d_H + (size_t)last * (m + 1) * m,
+                                                 sizeof(double2) * (size_t)(m + 1) * m, cudaMemcpyDeviceToDevice,
+                                                 pl->stream));
+            slots[h] = slots[last];
+            done[h] = 0;
+            done[last] = 1;
+        }
+        int na = 0;
+        for (int h = 0; h < nact; ++h)
+            if (!done[h]) na = h + 1;
+        const bool changed = na != nact;
+        nact = na;
+        if (nact > 0 && changed) return bind_slots();
+        return BLOCH_OK;
     }
 
     bloch_status run() {
         bloch_status s;
-        nact = 0;
-        while (nact < B && next_k < order.size()) {
-            if ((s = init_slot(nact, order[next_k++])) != BLOCH_OK) return s;
-            ++nact;
-        }
-        while (nact > 0) {
-            // gather v_j of every slot
-            std::vector<long long> src(nact), dst(nact);
-            std::vector<double> one(nact, 1.0);
-            std::vector<int> nv(nact);
-            for (int i = 0; i < nact; ++i) {
-                src[i] = ((long long)i * (m + 1) + slots[i].j) * n3;
-                dst[i] = (long long)i * n3;
-                nv[i] = slots[i].j + 1;
-            }
-            if ((s = upload_ll(d_src, src)) || (s = upload_ll(d_dst, dst))) return s;
-            BLOCH_CUDA_CHECK_RET(
-                cudaMemcpyAsync(d_s, one.data(), sizeof(double) * nact, cudaMemcpyHostToDevice, pl->stream));
-            BLOCH_CUDA_CHECK_RET(
-                cudaMemcpyAsync(d_nv, nv.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, pl->stream));
-            dim3 gc(nblk, nact);
-            ++pl->launches;
-            k_copy_scaled<T><<<gc, 256, 0, pl->stream>>>(Vb, d_src, Bc, d_dst, d_s, n3);
-            // w = A^-1 (M v_j)
-            std::vector<double> kv((size_t)nact * 3);
-            for (int i = 0; i < nact; ++i)
-                for (int a = 0; a < 3; ++a) kv[(size_t)i * 3 + a] = slots[i].k[a];
-            if ((s = set_k<T>(pl, nact, kv.data())) != BLOCH_OK) return s;
-            if ((s = lp_activate<T>(pl, nact, 1, 1)) != BLOCH_OK) return s;
-            long long cg_it = 0;
-            pl->trace_pcg = TR_PCG_LZ;
-            s = pcg_run<T>(pl, nact, Bc, Xc, rho_s, tol_lin, max_cg, false, nullptr, nullptr, &cg_it);
-            pl->trace_pcg = TR_PCG_SUB;
-            lp_deactivate(pl);
-            st->cg_iterations += cg_it;
-            st->k_applies += cg_it;
-            st->linear_solves += nact;
-            if (s != BLOCH_OK && s != BLOCH_ENOTCONV_CG) return s;
-            // two passes of classical Gram-Schmidt in the M inner product
-            const int tr_orth = trace_begin(pl, TR_ORTHO);
-            std::vector<cd> hsum((size_t)nact * (m + 1), cd(0, 0));
-            int maxnv = 0;
-            for (int i = 0; i < nact; ++i) maxnv = std::max(maxnv, nv[i]);
-            for (int pass = 0; pass < 2; ++pass) {
-                dim3 gd(nblk, maxnv, nact);
-                ++pl->launches;
-                k_vdots<T><<<gd, 256, 0, pl->stream>>>(Vb, (long long)(m + 1) * n3, Xc, n3, d_nv, n3, maxnv, d_part);
-                ++pl->launches;
-                k_vdots_final<<<dim3(maxnv, nact), 256, 0, pl->stream>>>(d_part, nblk, maxnv, rho_s, d_h);
-                dim3 ga(nblk, nact);
-                ++pl->launches;
-                k_vaxpy<T><<<ga, 256, 0, pl->stream>>>(Vb, (long long)(m + 1) * n3, Xc, n3, d_h, d_nv, n3, maxnv);
-                std::vector<double2> hh((size_t)nact * maxnv);
-                BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(hh.data(), d_h, sizeof(double2) * hh.size(),
-                                                     cudaMemcpyDeviceToHost, pl->stream));
-                BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
-                for (int i = 0; i < nact; ++i)
-                    for (int t = 0; t < nv[i]; ++t)
-                        hsum[(size_t)i * (m + 1) + t] += cd(hh[(size_t)i * maxnv + t].x, hh[(size_t)i * maxnv + t].y);
-            }
-            std::vector<double> nrm;
-            if ((s = xnorms(nrm)) != BLOCH_OK) return s;
-            std::vector<double> inv(nact);
-            for (int i = 0; i < nact; ++i) {
-                Slot& sl = slots[i];
-                for (int t = 0; t <= sl.j; ++t) sl.H[(size_t)t * m + sl.j] = hsum[(size_t)i * (m + 1) + t];
-                sl.H[(size_t)(sl.j + 1) * m + sl.j] = nrm[i];
-                inv[i] = nrm[i] > 0 ? 1.0 / nrm[i] : 0.0;
-                src[i] = (long long)i * n3;
-                dst[i] = ((long long)i * (m + 1) + sl.j + 1) * n3;
-            }
-            if ((s = upload_ll(d_src, src)) || (s = upload_ll(d_dst, dst))) return s;
-            BLOCH_CUDA_CHECK_RET(
-                cudaMemcpyAsync(d_s, inv.data(), sizeof(double) * nact, cudaMemcpyHostToDevice, pl->stream));
-            ++pl->launches;
-            k_copy_scaled<T><<<gc, 256, 0, pl->stream>>>(Xc, d_src, Vb, d_dst, d_s, n3);
-            trace_end(pl, tr_orth);
-            BLOCH_CUDA_CHECK_RET(cudaGetLastError());
-            // advance; analyse full bases
-            std::vector<int> finished;
-            for (int i = 0; i < nact; ++i) {
-                slots[i].j += 1;
-                if (slots[i].j == m) {
-                    bloch_status err = BLOCH_OK;
-                    if (ritz(i, err)) finished.push_back(i);
-                    if (err != BLOCH_OK) return err;
-                }
-            }
-            if (!finished.empty()) {
-                cudaStreamSynchronize(pl->stream);
-                std::vector<char> hole(nact, 0);
-                for (int f : finished) hole[f] = 1;
-                for (int f : finished)
-                    if (next_k < order.size()) {
-                        if ((s = init_slot(f, order[next_k++])) != BLOCH_OK) return s;
-                        hole[f] = 0;
-                    }
-                int last = nact - 1;
-                for (int h = 0; h < nact; ++h) {
-                    if (!hole[h]) continue;
-                    while (last > h && hole[last]) --last;
-                    if (last <= h) break;
-                    const int nvv = slots[last].j + 1;
-                    BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vb(h, 0), vb(last, 0), sizeof(C) * nvv * n3,
-                                                         cudaMemcpyDeviceToDevice, pl->stream));
-                    slots[h] = slots[last];
-                    hole[h] = 0;
-                    hole[last] = 1;
-                }
-                int na = 0;
-                for (int h = 0; h < nact; ++h)
-                    if (!hole[h]) na = h + 1;
-                nact = na;
+        while (next_k < order.size()) {
+            if ((s = start_batch()) != BLOCH_OK) return s;
+            int j = 0;
+            while (nact > 0) {
+                for (; j < m; ++j)
+                    if ((s = step(j)) != BLOCH_OK) return s;
+                if ((s = restart()) != BLOCH_OK) return s;
+                j = kk_restart();
             }
         }
+        lp_deactivate(pl);
+        cudaStreamSynchronize(pl->stream);
         return BLOCH_OK;
     }
 };
@@ -1291,9 +1277,8 @@ template <typename T>
 static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<double, 3>>& ks, int n_bands,
                                 double* omega_out, void* vecs_out, bloch_stats* st, cplx_t<T>* ritz_out = nullptr,
                                 int q_out = 0, double tol_override = 0.0) {
-    if (!pl->uniform_rho)
-        return set_error(BLOCH_EUNSUPPORTED, "the Lanczos solver needs a uniform density (use subspace iteration)");
     Lanczos<T> S;
+    S.uniform = pl->uniform_rho;
     S.pl = pl;
     S.n3 = 3 * pl->V;
     S.n_bands = n_bands;
@@ -1302,7 +1287,7 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     if (S.m > kBasisQMax - 1)
         return set_error(BLOCH_EUNSUPPORTED, "Lanczos basis above 63 vectors is not supported");
     if (S.m < n_bands + 1) return set_error(BLOCH_EINVAL, "Lanczos basis too small for the requested bands");
-    S.rho_s = pl->rho_uniform_scaled;
+    S.rho_s = pl->uniform_rho ? pl->rho_uniform_scaled : 1.0;
     S.tol_eig = tol_override > 0 ? tol_override : pl->opt.tol_eig;
     S.tol_lin = pl->opt.tol_lin;
     if (std::is_same<T, float>::value) S.tol_lin = std::max(S.tol_lin, 3e-6);
@@ -1327,7 +1312,9 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
     freeb += plan_solver_bytes(pl);   // held by the plan from earlier solves, reused
-    const size_t per_slot = (size_t)(S.m + 1 + 2 + 5) * S.n3 * sizeof(cplx_t<T>);
+    // basis, rotated basis, step vectors and CG workspace (twice the basis part
+    // with a non-uniform density: the M-images are kept too)
+    const size_t per_slot = (size_t)((2 * S.m + 1) * (S.uniform ? 1 : 2) + 2 + 6) * S.n3 * sizeof(cplx_t<T>);
     long long Bmax = std::max<long long>(1, (long long)(0.5 * (double)freeb / (double)per_slot));
     Bmax = std::min<long long>(Bmax, 64);
     int B = pl->opt.k_batch > 0 ? pl->opt.k_batch : (int)Bmax;

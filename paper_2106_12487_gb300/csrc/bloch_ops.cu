@@ -616,8 +616,8 @@ static bloch_status pcg_graph(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t
     Workspace<T>& w = ws_of<T>(pl);
     const int prec = std::is_same<T, float>::value ? 1 : 0;
     for (auto& e : pl->pcg_graphs)
-        if (e.prec == prec && e.nb == nb && e.max_iter == max_iter && e.b == b && e.x == x && e.E == w.E &&
-            e.r == w.r && e.ztab == pl->psel.ztab && e.zgroup == pl->psel.zgroup) {
+        if (e.prec == prec && e.nb == nb && e.max_iter == max_iter && e.tol2 == tol2 && e.b == b && e.x == x &&
+            e.E == w.E && e.r == w.r && e.ztab == pl->psel.ztab && e.zgroup == pl->psel.zgroup) {
             *out = e.exec;
             *launches_per_iter = e.launches_per_iter;
             return BLOCH_OK;
@@ -673,7 +673,8 @@ static bloch_status pcg_graph(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t
         cudaGraphDestroy(graph);
         return set_cuda_error(e, "cudaGraphInstantiate");
     }
-    bloch_plan::PcgGraph pg{prec, nb, max_iter, per_iter, b, x, w.E, w.r, pl->psel.ztab, pl->psel.zgroup, graph, exec};
+    bloch_plan::PcgGraph pg{prec, nb, max_iter, per_iter, tol2, b, x, w.E, w.r, pl->psel.ztab, pl->psel.zgroup,
+                            graph, exec};
     pl->pcg_graphs.push_back(pg);
     *out = exec;
     *launches_per_iter = per_iter;
@@ -758,6 +759,50 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     return BLOCH_OK;
 }
 
+template <typename T>
+bloch_status pcg_enqueue(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
+                         int max_iter, long long* tally) {
+    const double tol2 = tol * tol;
+    if (pl->opt.cuda_graph == 0 || pl->variant == 2 || max_iter <= 0) {
+        // host-driven loop: synchronises per iteration; the tally is added on the host
+        long long it = 0;
+        bloch_status st = pcg_run<T>(pl, nb, b, x, rhs_scale, tol, max_iter, false, nullptr, nullptr, &it);
+        if (st != BLOCH_OK && st != BLOCH_ENOTCONV_CG) return st;
+        long long add[4] = {it, st == BLOCH_ENOTCONV_CG ? 1 : 0, 0, 0};
+        long long cur[4];
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(cur, tally, sizeof(cur), cudaMemcpyDeviceToHost, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        for (int i = 0; i < 4; ++i) cur[i] += add[i];
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(tally, cur, sizeof(cur), cudaMemcpyHostToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+        return BLOCH_OK;
+    }
+    bloch_status st = ensure_cg<T>(pl, nb);
+    if (st != BLOCH_OK) return st;
+    TraceScope trace_pcg(pl, pl->trace_pcg);
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    const int nblk = vec_blocks(pl, nb);
+    dim3 gr(nblk, nb);
+    ++pl->launches;
+    k_cg_init<T><<<gr, 256, 0, pl->stream>>>(b, nullptr, x, w.r, w.p, w.qtab, g, pl->pc, pl->psel, T(rhs_scale), 1,
+                                              w.part3);
+    BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_nactive, 0, sizeof(int), pl->stream));
+    ++pl->launches;
+    k_cg_scalars<<<nb, 256, 0, pl->stream>>>(w.part3, w.dots, nblk, w.sys, 0, tol2, pl->d_nactive);
+    cudaGraphExec_t exec;
+    int per_iter = 0;
+    if ((st = pcg_graph<T>(pl, nb, b, x, tol2, nblk, max_iter, &exec, &per_iter)) != BLOCH_OK) return st;
+    BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(pl->d_iter, 0, sizeof(int), pl->stream));
+    BLOCH_CUDA_CHECK_RET(cudaGraphLaunch(exec, pl->stream));
+    // launches are counted per executed iteration by the caller's tally
+    pl->launches += 1;
+    k_cg_tally<<<1, 32, 0, pl->stream>>>(w.sys, nb, tol2, pl->d_iter, tally);
+    BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+    pl->pcg_launches_per_iter = per_iter;
+    return BLOCH_OK;
+}
+
 #define INST(T)                                                                                          \
     template bloch_status ensure_ws<T>(bloch_plan*, int);                                                \
     template bloch_status ensure_cg<T>(bloch_plan*, int);                                                \
@@ -771,7 +816,9 @@ bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, d
     template void launch_dot<T>(bloch_plan*, int, const cplx_t<T>*, const cplx_t<T>*, long long,         \
                                 double2*, double2*);                                                     \
     template bloch_status pcg_run<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, double, double, int, \
-                                     bool, int*, double*, long long*, void (*)(void*, int), void*);
+                                     bool, int*, double*, long long*, void (*)(void*, int), void*);       \
+    template bloch_status pcg_enqueue<T>(bloch_plan*, int, const cplx_t<T>*, cplx_t<T>*, double, double, int, \
+                                         long long*);
 INST(float)
 INST(double)
 #undef INST

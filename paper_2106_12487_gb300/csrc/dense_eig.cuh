@@ -1,0 +1,243 @@
+// Small dense Hermitian eigenproblems on the device, FP64, one CTA per
+// matrix (the projected problems of Algorithm 1, step EIG(K, M), and the
+// Ritz problems of the Lanczos restarts), so the eigensolver loops need no
+// host round trip.
+//
+// Standard problem: cyclic complex Jacobi.  Each rotation W (acting on rows
+// and columns p < r) zeroes A[p][r]: with A[p][r] = |a| e^{i phi},
+//   tau = (A_rr - A_pp) / (2 |a|),  t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+//   c = 1 / sqrt(1 + t^2),  s = t c,
+//   W_pp = c, W_pr = s, W_rp = -s e^{-i phi}, W_rr = c e^{-i phi},
+// A <- W^H A W, V <- V W.  One thread forms the rotation, the CTA's threads
+// update the two columns and then the two rows in parallel.  Sweeps stop when
+// the off-diagonal mass is below 1e-32 of the total (or after kJacMaxSweeps).
+//
+// Generalised problem K Q = M Q diag(lam), Q^H M Q = I: Cholesky M = L L^H,
+// C = L^-1 K L^-H, Jacobi on C, Q = L^-H W.  Eigenvalues ascending.
+#pragma once
+
+#include "common.cuh"
+
+namespace bloch {
+
+constexpr int kJacMaxSweeps = 40;
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Jacobi on the n x n Hermitian A (shared memory, row-major, destroyed); V
+// (shared, n x n) receives the eigenvectors in columns, w (shared, n) the
+// eigenvalues, both unsorted.  red: shared scratch of 2 * blockDim.x doubles;
+// rot: shared scratch of 5 double2.  Returns true when converged.
+static __device__ bool jacobi_herm(int n, double2* A, double2* V, double* w, double* red, double2* rot) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) V[e] = make_double2((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    bool conv = false;
+    for (int sweep = 0; sweep < kJacMaxSweeps; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < n * n; e += nt) {
+            const double a2 = zabs2(A[e]);
+            tot += a2;
+            if (e / n != e % n) off += a2;
+        }
+        red[tid] = off;
+        red[nt + tid] = tot;
+        __syncthreads();
+        for (int s = nt / 2; s > 0; s >>= 1) {
+            if (tid < s) {
+                red[tid] += red[tid + s];
+                red[nt + tid] += red[nt + tid + s];
+            }
+            __syncthreads();
+        }
+        const double offs = red[0], tots = red[nt];
+        __syncthreads();
+        if (offs <= 1e-32 * tots || tots == 0.0) {
+            conv = true;
+            break;
+        }
+        for (int p = 0; p < n - 1; ++p)
+            for (int r = p + 1; r < n; ++r) {
+                if (tid == 0) {
+                    const double2 apr = A[p * n + r];
+                    const double mag = sqrt(zabs2(apr));
+                    const double app = A[p * n + p].x, arr = A[r * n + r].x;
+                    double skip = 0.0;
+                    if (mag == 0.0) {
+                        skip = 1.0;
+                    } else if (mag < 1e-300 || mag <= 1e-21 * sqrt(fabs(app * arr))) {
+                        A[p * n + r] = A[r * n + p] = make_double2(0.0, 0.0);
+                        skip = 1.0;
+                    }
+                    if (skip == 0.0) {
+                        const double2 em = make_double2(apr.x / mag, -apr.y / mag);   // e^{-i phi}
+                        const double tau = (arr - app) / (2.0 * mag);
+                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                        rot[0] = make_double2(c, 0.0);                    // W_pp
+                        rot[1] = make_double2(s, 0.0);                    // W_pr
+                        rot[2] = make_double2(-s * em.x, -s * em.y);      // W_rp
+                        rot[3] = make_double2(c * em.x, c * em.y);        // W_rr
+                    }
+                    rot[4] = make_double2(skip, 0.0);
+                }
+                __syncthreads();
+                if (rot[4].x == 0.0) {
+                    const double2 Wpp = rot[0], Wpr = rot[1], Wrp = rot[2], Wrr = rot[3];
+                    for (int i = tid; i < n; i += nt) {   // A <- A W, V <- V W (columns p, r)
+                        const double2 aip = A[i * n + p], air = A[i * n + r];
+                        A[i * n + p] = zadd(zmul(aip, Wpp), zmul(air, Wrp));
+                        A[i * n + r] = zadd(zmul(aip, Wpr), zmul(air, Wrr));
+                        const double2 vip = V[i * n + p], vir = V[i * n + r];
+                        V[i * n + p] = zadd(zmul(vip, Wpp), zmul(vir, Wrp));
+                        V[i * n + r] = zadd(zmul(vip, Wpr), zmul(vir, Wrr));
+                    }
+                    __syncthreads();
+                    for (int j = tid; j < n; j += nt) {   // A <- W^H A (rows p, r)
+                        const double2 apj = A[p * n + j], arj = A[r * n + j];
+                        A[p * n + j] = zadd(zmul(zconj(Wpp), apj), zmul(zconj(Wrp), arj));
+                        A[r * n + j] = zadd(zmul(zconj(Wpr), apj), zmul(zconj(Wrr), arj));
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        A[p * n + r] = A[r * n + p] = make_double2(0.0, 0.0);
+                        A[p * n + p].y = 0.0;
+                        A[r * n + r].y = 0.0;
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    for (int i = tid; i < n; i += nt) w[i] = A[i * n + i].x;
+    __syncthreads();
+    return conv;
+}
+
+// perm[0..n) = indices of w in ascending order (stable), thread 0
+static __device__ void sort_ascending(int n, const double* w, int* perm) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        for (int i = 1; i < n; ++i) {
+            const int pi = perm[i];
+            int j = i - 1;
+            while (j >= 0 && w[perm[j]] > w[pi]) {
+                perm[j + 1] = perm[j];
+                --j;
+            }
+            perm[j + 1] = pi;
+        }
+    }
+    __syncthreads();
+}
+
+// Shared memory of k_gen_herm_eig for order n: four n x n double2 matrices,
+// n doubles, n ints, reductions and the rotation.
+__host__ __device__ constexpr size_t gen_eig_smem(int n, int nthreads) {
+    return (size_t)4 * n * n * sizeof(double2) + (size_t)n * sizeof(double) + (size_t)n * sizeof(int) +
+           (size_t)2 * nthreads * sizeof(double) + 5 * sizeof(double2) + 64;
+}
+
+// Batched generalised problems, one per blockIdx.x: K, M (n x n row-major
+// double2, Hermitised here) at K + b*n*n, M + b*n*n (M scaled by mscale);
+// out: lam[b][n] ascending, Q[b] (n x n row-major, eigenvectors in columns,
+// Q^H M Q = I); status[b] = 0 ok, 1 M not positive definite, 2 Jacobi did not
+// converge.
+static __global__ void k_gen_herm_eig(int n, const double2* __restrict__ K, const double2* __restrict__ M, double mscale,
+                               double* __restrict__ lam, double2* __restrict__ Q, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* A = reinterpret_cast<double2*>(smem_raw);
+    double2* L = A + n * n;
+    double2* X = L + n * n;
+    double2* W = X + n * n;
+    double* w = reinterpret_cast<double*>(W + n * n);
+    int* perm = reinterpret_cast<int*>(w + n);
+    double* red = reinterpret_cast<double*>(perm + n + (n & 1));
+    double2* rot = reinterpret_cast<double2*>(red + 2 * blockDim.x);
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int b = blockIdx.x;
+    const double2* Kb = K + (size_t)b * n * n;
+    const double2* Mb = M + (size_t)b * n * n;
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        const double2 k1 = Kb[i * n + j], k2 = Kb[j * n + i];
+        A[e] = make_double2(0.5 * (k1.x + k2.x), 0.5 * (k1.y - k2.y));
+        const double2 m1 = Mb[i * n + j], m2 = Mb[j * n + i];
+        X[e] = make_double2(0.5 * mscale * (m1.x + m2.x), 0.5 * mscale * (m1.y - m2.y));   // Hermitian part of M
+        L[e] = make_double2(0.0, 0.0);
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    // Cholesky M = L L^H (lower), serial: n <= 32 in Algorithm 1
+    if (tid == 0) {
+        for (int i = 0; i < n && !bad; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double2 s = X[i * n + j];
+                for (int k = 0; k < j; ++k) s = zsub(s, zmul(L[i * n + k], zconj(L[j * n + k])));
+                if (i == j) {
+                    if (!(s.x > 0.0)) {
+                        bad = 1;
+                        break;
+                    }
+                    L[i * n + i] = make_double2(sqrt(s.x), 0.0);
+                } else {
+                    const double d = L[j * n + j].x;
+                    L[i * n + j] = make_double2(s.x / d, s.y / d);
+                }
+            }
+    }
+    __syncthreads();
+    if (bad) {
+        if (tid == 0) status[b] = 1;
+        return;
+    }
+    // X = L^-1 A (columns in parallel)
+    for (int c = tid; c < n; c += nt)
+        for (int i = 0; i < n; ++i) {
+            double2 s = A[i * n + c];
+            for (int k = 0; k < i; ++k) s = zsub(s, zmul(L[i * n + k], X[k * n + c]));
+            const double d = L[i * n + i].x;
+            X[i * n + c] = make_double2(s.x / d, s.y / d);
+        }
+    __syncthreads();
+    // Y = L^-1 X^H into W; then C = Y^H into A (Hermitised)
+    for (int c = tid; c < n; c += nt)
+        for (int i = 0; i < n; ++i) {
+            double2 s = zconj(X[c * n + i]);
+            for (int k = 0; k < i; ++k) s = zsub(s, zmul(L[i * n + k], W[k * n + c]));
+            const double d = L[i * n + i].x;
+            W[i * n + c] = make_double2(s.x / d, s.y / d);
+        }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        const double2 c1 = zconj(W[j * n + i]), c2 = zconj(W[i * n + j]);   // C_ij and conj(C_ji)
+        A[e] = make_double2(0.5 * (c1.x + c2.x), 0.5 * (c1.y - c2.y));
+    }
+    __syncthreads();
+    const bool conv = jacobi_herm(n, A, W, w, red, rot);
+    // Q = L^-H W (columns in parallel) into X
+    for (int c = tid; c < n; c += nt)
+        for (int i = n - 1; i >= 0; --i) {
+            double2 s = W[i * n + c];
+            for (int k = i + 1; k < n; ++k) s = zsub(s, zmul(zconj(L[k * n + i]), X[k * n + c]));
+            const double d = L[i * n + i].x;
+            X[i * n + c] = make_double2(s.x / d, s.y / d);
+        }
+    __syncthreads();
+    sort_ascending(n, w, perm);
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        Q[(size_t)b * n * n + e] = X[i * n + perm[j]];
+    }
+    for (int j = tid; j < n; j += nt) lam[(size_t)b * n + j] = w[perm[j]];
+    if (tid == 0) status[b] = conv ? 0 : 2;
+}
+
+}  // namespace bloch

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "dense_eig.cuh"
 #include "vec.cuh"
 
 namespace bloch {
@@ -200,7 +201,8 @@ constexpr int kBasisQMax = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_basis_reg(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
-                                                   const double2* __restrict__ Q, int q, long long n_per) {
+                                                   const double2* __restrict__ Q, int q, long long n_per,
+                                                   long long in_stride) {
     using C = cplx_t<T>;
     __shared__ C sQ[kQMax * kQMax];
     const int slot = blockIdx.y;
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(128) k_basis_reg(const cplx_t<T>* __restrict__
         sQ[t] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
-    const C* ib = In + (size_t)slot * q * n_per;
+    const C* ib = In + (size_t)slot * in_stride;
     C* ob = Out + (size_t)slot * q * n_per;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
          e += (long long)gridDim.x * blockDim.x) {
@@ -235,7 +237,8 @@ constexpr int kBasisJC = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
-                                                    const double2* __restrict__ Q, int q, long long n_per) {
+                                                    const double2* __restrict__ Q, int q, long long n_per,
+                                                    long long in_stride) {
     using C = cplx_t<T>;
     constexpr int JC = kBasisJC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict_
         sQ[t] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
-    const C* ib = In + (size_t)slot * q * n_per;
+    const C* ib = In + (size_t)slot * in_stride;
     C* ob = Out + (size_t)slot * q * n_per;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
          e += (long long)gridDim.x * blockDim.x) {
@@ -274,16 +277,18 @@ __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict_
 }
 
 // Basis rotation of nslot slots (q < kBasisQMax).
+// (In holds slot s at In + s * in_stride; in_stride <= 0 means q * n_per.)
 template <typename T>
 void launch_basis(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* Out, const double2* Q, int q,
-                  long long n_per) {
+                  long long n_per, long long in_stride = 0) {
     const unsigned gx = (unsigned)std::min<long long>((n_per + 127) / 128, 8192);
+    if (in_stride <= 0) in_stride = (long long)q * n_per;
     if (q <= kQMax) {
-        k_basis_reg<T><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, q, n_per);
+        k_basis_reg<T><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, q, n_per, in_stride);
     } else {
         const int nch = (q + kBasisJC - 1) / kBasisJC;
-        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)q * kBasisJC * sizeof(cplx_t<T>), st>>>(In, Out, Q,
-                                                                                                     q, n_per);
+        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)q * kBasisJC * sizeof(cplx_t<T>), st>>>(
+            In, Out, Q, q, n_per, in_stride);
     }
 }
 
@@ -342,6 +347,43 @@ __global__ void k_residual(const cplx_t<TK>* __restrict__ U, const cplx_t<TK>* _
     }
     block_sum<TK, 1>(acc);
     if (threadIdx.x == 0) partial[(size_t)v * gridDim.x + blockIdx.x] = acc[0];
+}
+
+// Final sums of k_rq_dots for the nv vectors of one call (blockIdx.x = v):
+// (Re u^H K u, u^H M u, |K u|^2) go to rq[d][0..2] with d = (first + v/nvs) q
+// + vo + v % nvs, and 1/lambda (0 when lambda <= 0) to inv_call[v] and inv_slot[d].
+static __global__ void k_rq_final(const double* __restrict__ partial, int dblk, int first, int nvs, int vo, int q,
+                                  double* __restrict__ rq, double* __restrict__ inv_call,
+                                  double* __restrict__ inv_slot) {
+    const int v = blockIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int j = threadIdx.x; j < dblk; j += blockDim.x) {
+        const double* p = partial + ((size_t)v * dblk + j) * 3;
+        acc[0] += p[0];
+        acc[1] += p[1];
+        acc[2] += p[2];
+    }
+    block_sum<double, 3>(acc);
+    if (threadIdx.x == 0) {
+        const size_t d = (size_t)(first + v / nvs) * q + vo + v % nvs;
+        rq[d * 4 + 0] = acc[0];
+        rq[d * 4 + 1] = acc[1];
+        rq[d * 4 + 2] = acc[2];
+        const double lam = acc[1] > 0.0 ? acc[0] / acc[1] : 0.0;
+        const double il = lam > 0.0 ? 1.0 / lam : 0.0;
+        inv_call[v] = il;
+        inv_slot[d] = il;
+    }
+}
+
+// Final sums of k_residual: |R|^2 to rq[d][3]
+static __global__ void k_r2_final(const double* __restrict__ partial, int dblk, int first, int nvs, int vo, int q,
+                                  double* __restrict__ rq) {
+    const int v = blockIdx.x;
+    double acc[1] = {0.0};
+    for (int j = threadIdx.x; j < dblk; j += blockDim.x) acc[0] += partial[(size_t)v * dblk + j];
+    block_sum<double, 1>(acc);
+    if (threadIdx.x == 0) rq[((size_t)(first + v / nvs) * q + vo + v % nvs) * 4 + 3] = acc[0];
 }
 
 // X[v] += U[v] * s_v
@@ -499,6 +541,7 @@ __global__ void k_vaxpy(const cplx_t<T>* __restrict__ V, long long vstride, cplx
         sh[i] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
+    if (m == 0) return;
     const C* vb = V + (size_t)slot * vstride;
     C* w = W + (size_t)slot * wstride;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -525,6 +568,145 @@ __global__ void k_copy_scaled(const cplx_t<T>* __restrict__ src, const long long
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
         b[e] = cscale(a[e], sv);
+}
+
+// ------------------------------------------------ device-resident Lanczos
+// All slots advance in lockstep (same step j), so the column of a step is a
+// kernel argument and no per-step host synchronisation is needed.
+
+// dst[s] = Vb[s][j] * (scale ? scale[s] : 1)   (blockIdx.y = slot)
+template <typename T>
+__global__ void k_get_col(const cplx_t<T>* __restrict__ Vb, long long slot_stride, int j, long long n3,
+                          const double* __restrict__ scale, cplx_t<T>* __restrict__ dst) {
+    const int sl = blockIdx.y;
+    const T sv = scale ? T(scale[sl]) : T(1);
+    const cplx_t<T>* a = Vb + (size_t)sl * slot_stride + (size_t)j * n3;
+    cplx_t<T>* b = dst + (size_t)sl * n3;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3;
+         e += (long long)gridDim.x * blockDim.x)
+        b[e] = cscale(a[e], sv);
+}
+
+// Vb[s][j] = src[s] * scale[s]
+template <typename T>
+__global__ void k_put_col(const cplx_t<T>* __restrict__ src, cplx_t<T>* __restrict__ Vb, long long slot_stride,
+                          int j, long long n3, const double* __restrict__ scale) {
+    const int sl = blockIdx.y;
+    const T sv = T(scale[sl]);
+    const cplx_t<T>* a = src + (size_t)sl * n3;
+    cplx_t<T>* b = Vb + (size_t)sl * slot_stride + (size_t)j * n3;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3;
+         e += (long long)gridDim.x * blockDim.x)
+        b[e] = cscale(a[e], sv);
+}
+
+// a[0..n) = v
+static __global__ void k_fill_int(int* __restrict__ a, int n, int v) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = v;
+}
+
+// H[s][t][j] += h[s][t] for t < nv (Gram-Schmidt coefficients of step j;
+// H row-major (m + 1) x m per slot)
+static __global__ void k_h_accum(double2* __restrict__ H, const double2* __restrict__ h, int maxnv, int nv, int j,
+                                 int m) {
+    const int sl = blockIdx.x;
+    double2* Hs = H + (size_t)sl * (m + 1) * m;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        const double2 v = h[(size_t)sl * maxnv + t];
+        Hs[(size_t)t * m + j].x += v.x;
+        Hs[(size_t)t * m + j].y += v.y;
+    }
+}
+
+// beta_s = sqrt(scale * Re dots[s]); H[s][j+1][j] = beta (j >= 0); inv[s] = 1/beta (0 if beta = 0)
+static __global__ void k_lz_norm(const double2* __restrict__ dots, double scale, double2* __restrict__ H, int j,
+                                 int m, int nact, double* __restrict__ inv) {
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nact) return;
+    const double beta = sqrt(fmax(scale * dots[sl].x, 0.0));
+    if (j >= 0) H[(size_t)sl * (m + 1) * m + (size_t)(j + 1) * m + j] = make_double2(beta, 0.0);
+    inv[sl] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+// Shared memory of k_lz_ritz for basis size m
+__host__ __device__ constexpr size_t lz_ritz_smem(int m, int nthreads) {
+    return (size_t)2 * m * m * sizeof(double2) + (size_t)m * sizeof(double) + (size_t)(m + 1) * sizeof(int) +
+           (size_t)2 * nthreads * sizeof(double) + 5 * sizeof(double2) + 64;
+}
+
+// Thick-restart analysis of slot blockIdx.x (Section 3.3 shift-invert
+// Lanczos, Ritz values theta of OP = A^-1 M, wanted: the largest): the
+// Hermitian part of H[0:m][0:m] is diagonalised; theta[s][c] (descending)
+// and the Ritz estimates est[s][c] = beta |y_{m-1,c}| (beta = |H[m][m-1]|)
+// are written for every c < m; conv[s] = all neff[s] wanted estimates
+// satisfy est <= tol |theta| with theta > 0.  Q[s] (m x m) receives the kc
+// leading Ritz vectors in its columns (zero beyond), and H[s] is reset to the
+// thick-restart matrix of kk leading Ritz pairs: diag(theta) and the row
+// kk = beta y_{m-1, c}.
+static __global__ void k_lz_ritz(int m, double2* __restrict__ H, const int* __restrict__ neff, double tol, int kc, int kk,
+                          double2* __restrict__ Q, double* __restrict__ theta, double* __restrict__ est,
+                          int* __restrict__ conv, int* __restrict__ jac_ok) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* A = reinterpret_cast<double2*>(smem_raw);
+    double2* Y = A + m * m;
+    double* w = reinterpret_cast<double*>(Y + m * m);
+    int* perm = reinterpret_cast<int*>(w + m);
+    double* red = reinterpret_cast<double*>(perm + m + (m & 1));
+    double2* rot = reinterpret_cast<double2*>(red + 2 * blockDim.x);
+    __shared__ double beta;
+    const int sl = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    double2* Hs = H + (size_t)sl * (m + 1) * m;
+    for (int e = tid; e < m * m; e += nt) {
+        const int i = e / m, j = e % m;
+        const double2 a = Hs[(size_t)i * m + j], b = Hs[(size_t)j * m + i];
+        A[e] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    }
+    if (tid == 0) beta = sqrt(zabs2(Hs[(size_t)m * m + (m - 1)]));
+    __syncthreads();
+    const bool ok = jacobi_herm(m, A, Y, w, red, rot);
+    sort_ascending(m, w, perm);
+    double* th = theta + (size_t)sl * m;
+    double* es = est + (size_t)sl * m;
+    for (int c = tid; c < m; c += nt) {
+        const int ic = perm[m - 1 - c];
+        th[c] = w[ic];
+        es[c] = beta * sqrt(zabs2(Y[(m - 1) * m + ic]));
+    }
+    for (int e = tid; e < m * m; e += nt) {
+        const int i = e / m, c = e % m;
+        Q[(size_t)sl * m * m + e] = c < kc ? Y[i * m + perm[m - 1 - c]] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int cv = 1;
+        for (int i = 0; i < neff[sl]; ++i) {
+            const double t = th[i];
+            if (!(t > 0.0) || es[i] > tol * fabs(t)) cv = 0;
+        }
+        conv[sl] = cv;
+        jac_ok[sl] = ok ? 1 : 0;
+    }
+    for (int e = tid; e < (m + 1) * m; e += nt) Hs[e] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int c = tid; c < kk; c += nt) {
+        const int ic = perm[m - 1 - c];
+        Hs[(size_t)c * m + c] = make_double2(w[ic], 0.0);
+        const double2 y = Y[(m - 1) * m + ic];
+        Hs[(size_t)kk * m + c] = make_double2(beta * y.x, beta * y.y);
+    }
+}
+
+// Restart copies of every slot: Vb[s][0..kk) = Tmp[s][0..kk), Vb[s][kk] = Vb[s][m]
+template <typename T>
+__global__ void k_lz_restart_copy(cplx_t<T>* __restrict__ Vb, const cplx_t<T>* __restrict__ Tmp, int m, int kk,
+                                  long long n3) {
+    const int sl = blockIdx.y;
+    cplx_t<T>* vb = Vb + (size_t)sl * (m + 1) * n3;
+    const cplx_t<T>* tb = Tmp + (size_t)sl * m * n3;
+    const long long tot = (long long)(kk + 1) * n3;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x)
+        vb[e] = e < (long long)kk * n3 ? tb[e] : vb[(size_t)m * n3 + (e - (long long)kk * n3)];
 }
 
 // Deterministic start vector: counter-based hash -> uniform in [-1, 1) per

@@ -124,6 +124,7 @@ struct bloch_plan {
     // instantiated PCG-loop graphs (conditional WHILE node), keyed by their bound pointers
     struct PcgGraph {
         int prec, nb, max_iter, launches_per_iter;
+        double tol2;
         const void *b, *x, *E, *r, *ztab;
         int zgroup;
         cudaGraph_t graph;
@@ -131,6 +132,7 @@ struct bloch_plan {
     };
     std::vector<PcgGraph> pcg_graphs;
     int* d_iter = nullptr;
+    int pcg_launches_per_iter = 0;     // kernels per PCG iteration of the last enqueued graph
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
 
     // hand-off block of the FP32 Lanczos -> Algorithm 1 form (chunk x q x 3V float2),
@@ -190,6 +192,14 @@ template <typename T>
 bloch_status pcg_run(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
                      int max_iter, bool use_x0, int* iters, double* relres, long long* total_iters,
                      void (*hook)(void*, int) = nullptr, void* hook_ctx = nullptr);
+// Batched PCG enqueued on the plan's stream with no host synchronisation
+// (the loop is the graph's device-side WHILE node; falls back to pcg_run where
+// graphs are off).  Adds iterations, missed tolerances, non-finite residuals
+// and loop iterations to tally[0..3] (device, long long; the host-loop
+// fallback counts its launches itself and adds 0 loop iterations).
+template <typename T>
+bloch_status pcg_enqueue(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* x, double rhs_scale, double tol,
+                         int max_iter, long long* tally);
 // dots[b] = sum conj(a_b) c_b over n_per elements per system (device result).
 template <typename T>
 void launch_dot(bloch_plan* pl, int nb, const cplx_t<T>* a, const cplx_t<T>* c, long long n_per, double2* out,

@@ -372,4 +372,30 @@ static __global__ void k_cg_scalars(const double* partial3, const double2* dots,
     }
 }
 
+// Device tally of PCG runs enqueued without host synchronisation:
+// tally[0] += sum of iterations, tally[1] += systems that missed tol,
+// tally[2] += systems with a non-finite residual, tally[3] += loop
+// iterations executed (*iter, the graph's iteration counter).
+static __global__ void k_cg_tally(const CGSys* __restrict__ sys, int nb, double tol2, const int* __restrict__ iter,
+                                  long long* __restrict__ tally) {
+    long long it = 0, miss = 0, bad = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        it += sys[b].iters;
+        const double rr = sys[b].rr, bb = sys[b].bb;
+        if (!isfinite(rr) || !isfinite(bb)) ++bad;
+        else if (rr > tol2 * bb) ++miss;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        it += __shfl_xor_sync(0xffffffffu, it, o);
+        miss += __shfl_xor_sync(0xffffffffu, miss, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (threadIdx.x == 0) {
+        tally[0] += it;
+        tally[1] += miss;
+        tally[2] += bad;
+        tally[3] += *iter;
+    }
+}
+
 }  // namespace bloch

@@ -164,12 +164,13 @@ def test_bands_nonconvergence_reported(B):
     assert st == 5 and np.all(got > 0)
 
 
+# method 1: Algorithm 1; method 0: shift-invert Lanczos (FP32: Lanczos then Algorithm 1 refinement)
+@pytest.mark.parametrize("method", [1, 0])
 @pytest.mark.parametrize("prec,bar,opt", FORMS)
-def test_bands_nonuniform_density(B, prec, bar, opt):
-    """Two-phase-like density contrast (per-grain rho from 2000 to 9000
-    kg/m^3) with subspace iteration: the mass operator is a real five-pass FFT
-    operator and the projected M is a full Gram matrix, not a multiple of
-    U^H U.  The Lanczos solver rejects a non-uniform density."""
+def test_bands_nonuniform_density(B, prec, bar, opt, method):
+    """Per-grain densities from 2000 to 9000 kg/m^3: the mass operator is a
+    real five-pass FFT operator, the projected M a full Gram matrix and the
+    Lanczos basis is M-orthonormal through its stored M-images."""
     import dataclasses
     p = synth.small_polycrystal((10, 8, 12), 6, 9, n_bands=5)
     rho = np.random.default_rng(4).uniform(2000.0, 9000.0, p.G)
@@ -177,12 +178,70 @@ def test_bands_nonuniform_density(B, prec, bar, opt):
     med = O.Medium.from_problem(p)
     ks = np.array([[0.5, 0.0, 0.0], [0.3, 0.6, 0.9]]) * math.pi / 1e-3
     want = O.solve_bands(med, ks, 5, 1e-12, 1e-12, method="lanczos").omega
-    plan = B.Plan.from_problem(p, precision=prec, method=1, **opt)
-    got, stats, _ = plan.solve_bands(ks, 5)
+    plan = B.Plan.from_problem(p, precision=prec, method=method, **opt)
+    got, stats, st = plan.solve_bands(ks, 5)
+    assert st == 0
     assert freq_err(got, want) < bar
-    with pytest.raises(B.BlochError) as e:
-        B.Plan.from_problem(p, precision=prec, method=0, **opt).solve_bands(ks, 5)
-    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("method", [1, 0])
+@pytest.mark.parametrize("prec,bar,opt", FORMS)
+def test_gamma_nonuniform_density(B, prec, bar, opt, method):
+    """k = 0 with a non-uniform density: three exact zeros (rigid translations)
+    and the rest of the spectrum on their M-orthogonal complement, against the
+    dense generalised eigenproblem of the oracle's operators."""
+    import scipy.linalg
+    p = synth.small_polycrystal((6, 5, 4), 4, 41, n_bands=7)
+    rho = np.array([8960.0, 2000.0, 5000.0, 12000.0])
+    med = O.Medium(p.grid, p.L, p.grain_ids, p.C_per_grain, rho)
+    lam = scipy.linalg.eigh(O.dense_K(med, np.zeros(3)), O.dense_M(med), eigvals_only=True)
+    want = np.concatenate([[0.0, 0.0, 0.0], np.sqrt(lam[3:7])])
+    import dataclasses
+    p = dataclasses.replace(p, rho=rho)
+    plan = B.Plan.from_problem(p, precision=prec, method=method, **opt)
+    ks = np.array([[0.0, 0.0, 0.0], [0.2, 0.0, 0.0]]) * math.pi / 1e-3
+    got, stats, st = plan.solve_bands(ks, 7)
+    assert st == 0
+    assert freq_err(got[:1], want[None]) < bar
+
+
+_FIBRE_REF = {}
+
+
+def _fibre_reference(shape):
+    """Six lowest frequencies of the 16 x 16 x 1 fibre cell at the seven path
+    points, from the dense generalised eigenproblem of the oracle's operators
+    (768 unknowns; the three rigid translations at Gamma mapped to 0)."""
+    import scipy.linalg
+    if shape not in _FIBRE_REF:
+        p = synth.fibre_composite((16, 16, 1), shape, n_bands=6, n_k=7)
+        med = O.Medium.from_problem(p)
+        Md = O.dense_M(med)
+        out = np.zeros((p.k_list.shape[0], 6))
+        for i, k in enumerate(p.k_list):
+            lam = scipy.linalg.eigh(O.dense_K(med, k), Md, eigvals_only=True, subset_by_index=(0, 5))
+            if np.all(k == 0):
+                lam[:3] = 0.0
+            out[i] = np.sqrt(np.maximum(lam, 0.0))
+        _FIBRE_REF[shape] = out
+    return _FIBRE_REF[shape]
+
+
+@pytest.mark.parametrize("shape", ["circle", "square"])
+@pytest.mark.parametrize("prec,bar,opt,method", [(0, 1e-9, dict(tol_lin=1e-11, tol_eig=1e-11), 0),
+                                                 (0, 1e-9, dict(tol_lin=1e-11, tol_eig=1e-11), 1),
+                                                 (1, 1e-6, dict(tol_lin=1e-2, tol_eig=1e-6, max_cg=2000), 0)])
+def test_fibre_composite_path(B, shape, prec, bar, opt, method):
+    """Epoxy/carbon long-fibre cells (Table 1 phases; 55 % circular, 65 %
+    square fibres; N3 = 1) along M-Gamma-X-M through Gamma, against the
+    oracle's Algorithm 1: two phases of different density and a stiffness
+    contrast of 51."""
+    p = synth.fibre_composite((16, 16, 1), shape, n_bands=6, n_k=7)
+    want = _fibre_reference(shape)
+    plan = B.Plan.from_problem(p, precision=prec, method=method, **opt)
+    got, stats, st = plan.solve_bands(p.k_list, 6)
+    assert st == 0
+    assert freq_err(got, want) < bar
 
 
 @pytest.mark.parametrize("n_bands,ncv", [(16, 0), (6, 40), (6, 63)])
