@@ -136,11 +136,12 @@ static __device__ void sort_ascending(int n, const double* w, int* perm) {
     __syncthreads();
 }
 
-// Shared memory of k_gen_herm_eig for order n: four n x n double2 matrices,
-// n doubles, n ints, reductions and the rotation.
+// Shared memory of k_gen_herm_eig for order n, in this order (16-byte
+// aligned double2 first): four n x n double2 matrices, the 5 double2 of the
+// rotation, n doubles, 2 * nthreads doubles of reductions, n ints.
 __host__ __device__ constexpr size_t gen_eig_smem(int n, int nthreads) {
-    return (size_t)4 * n * n * sizeof(double2) + (size_t)n * sizeof(double) + (size_t)n * sizeof(int) +
-           (size_t)2 * nthreads * sizeof(double) + 5 * sizeof(double2) + 64;
+    return (size_t)4 * n * n * sizeof(double2) + 5 * sizeof(double2) + (size_t)n * sizeof(double) +
+           (size_t)2 * nthreads * sizeof(double) + (size_t)n * sizeof(int);
 }
 
 // Batched generalised problems, one per blockIdx.x: K, M (n x n row-major
@@ -155,10 +156,10 @@ static __global__ void k_gen_herm_eig(int n, const double2* __restrict__ K, cons
     double2* L = A + n * n;
     double2* X = L + n * n;
     double2* W = X + n * n;
-    double* w = reinterpret_cast<double*>(W + n * n);
-    int* perm = reinterpret_cast<int*>(w + n);
-    double* red = reinterpret_cast<double*>(perm + n + (n & 1));
-    double2* rot = reinterpret_cast<double2*>(red + 2 * blockDim.x);
+    double2* rot = W + n * n;
+    double* w = reinterpret_cast<double*>(rot + 5);
+    double* red = w + n;
+    int* perm = reinterpret_cast<int*>(red + 2 * blockDim.x);
     __shared__ int bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = blockIdx.x;

@@ -628,10 +628,12 @@ static __global__ void k_lz_norm(const double2* __restrict__ dots, double scale,
     inv[sl] = beta > 0.0 ? 1.0 / beta : 0.0;
 }
 
-// Shared memory of k_lz_ritz for basis size m
+// Shared memory of k_lz_ritz for basis size m, in this order (16-byte aligned
+// double2 first): two m x m double2 matrices, the 5 double2 of the rotation,
+// m doubles, 2 * nthreads doubles of reductions, m ints.
 __host__ __device__ constexpr size_t lz_ritz_smem(int m, int nthreads) {
-    return (size_t)2 * m * m * sizeof(double2) + (size_t)m * sizeof(double) + (size_t)(m + 1) * sizeof(int) +
-           (size_t)2 * nthreads * sizeof(double) + 5 * sizeof(double2) + 64;
+    return (size_t)2 * m * m * sizeof(double2) + 5 * sizeof(double2) + (size_t)m * sizeof(double) +
+           (size_t)2 * nthreads * sizeof(double) + (size_t)m * sizeof(int);
 }
 
 // Thick-restart analysis of slot blockIdx.x (Section 3.3 shift-invert
@@ -649,10 +651,10 @@ static __global__ void k_lz_ritz(int m, double2* __restrict__ H, const int* __re
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* A = reinterpret_cast<double2*>(smem_raw);
     double2* Y = A + m * m;
-    double* w = reinterpret_cast<double*>(Y + m * m);
-    int* perm = reinterpret_cast<int*>(w + m);
-    double* red = reinterpret_cast<double*>(perm + m + (m & 1));
-    double2* rot = reinterpret_cast<double2*>(red + 2 * blockDim.x);
+    double2* rot = Y + m * m;
+    double* w = reinterpret_cast<double*>(rot + 5);
+    double* red = w + m;
+    int* perm = reinterpret_cast<int*>(red + 2 * blockDim.x);
     __shared__ double beta;
     const int sl = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     double2* Hs = H + (size_t)sl * (m + 1) * m;
