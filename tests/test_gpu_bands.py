@@ -230,12 +230,15 @@ def _fibre_reference(shape):
 @pytest.mark.parametrize("shape", ["circle", "square"])
 @pytest.mark.parametrize("prec,bar,opt,method", [(0, 1e-9, dict(tol_lin=1e-11, tol_eig=1e-11), 0),
                                                  (0, 1e-9, dict(tol_lin=1e-11, tol_eig=1e-11), 1),
-                                                 (1, 1e-6, dict(tol_lin=1e-2, tol_eig=1e-6, max_cg=2000), 0)])
+                                                 (1, 1e-6, dict(tol_lin=1e-2, tol_eig=1e-5, max_cg=2000,
+                                                                max_outer=100), 0)])
 def test_fibre_composite_path(B, shape, prec, bar, opt, method):
     """Epoxy/carbon long-fibre cells (Table 1 phases; 55 % circular, 65 %
     square fibres; N3 = 1) along M-Gamma-X-M through Gamma, against the
-    oracle's Algorithm 1: two phases of different density and a stiffness
-    contrast of 51."""
+    oracle's dense eigensolve: two phases of different density and a stiffness
+    contrast of 51.  The FP32 form runs with the bench's eigen tolerance 1e-5
+    (its FP64 residual check stalls near 1e-4 at this contrast when asked for
+    1e-5 residuals); its frequencies must still meet 1e-6."""
     p = synth.fibre_composite((16, 16, 1), shape, n_bands=6, n_k=7)
     want = _fibre_reference(shape)
     plan = B.Plan.from_problem(p, precision=prec, method=method, **opt)
