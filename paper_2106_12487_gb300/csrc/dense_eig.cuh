@@ -32,14 +32,35 @@ __device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.
 
 // Jacobi on the n x n Hermitian A (shared memory, row-major, destroyed); V
 // (shared, n x n) receives the eigenvectors in columns, w (shared, n) the
-// eigenvalues, both unsorted.  red: shared scratch of 2 * blockDim.x doubles;
-// rot: shared scratch of 5 double2.  Returns true when converged.
+// eigenvalues, both unsorted.  Parallel ordering: each round applies n'/2
+// disjoint rotations at once (n' = n rounded up to even; the pairs of a round
+// come from the circle method -- index n'-1 fixed, the others rotating -- so
+// n' - 1 rounds cover every pair once per sweep; pairs with the padding index
+// are skipped).  Rotation parameters are formed from A at the start of the
+// round, then all column updates (A W, V W), then all row updates (W^H A).
+// red: shared scratch of 2 * blockDim.x doubles; rot: shared scratch of
+// 5 * (n'/2) double2.  Returns true when converged.
+__host__ __device__ constexpr int jacobi_rot_slots(int n) { return 5 * ((n + 1) / 2); }
+
+static __device__ __forceinline__ void round_pair(int np, int rd, int i, int& p, int& r) {
+    const int c = np - 1;   // the fixed index
+    if (i == 0) {
+        p = rd;
+        r = c;
+    } else {
+        p = (rd + i) % c;
+        r = (rd - i + c) % c;
+    }
+}
+
 static __device__ bool jacobi_herm(int n, double2* A, double2* V, double* w, double* red, double2* rot) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int np = n + (n & 1);
+    const int half = np / 2;
     for (int e = tid; e < n * n; e += nt) V[e] = make_double2((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
     __syncthreads();
-    bool conv = false;
-    for (int sweep = 0; sweep < kJacMaxSweeps; ++sweep) {
+    bool conv = n < 2;
+    for (int sweep = 0; sweep < kJacMaxSweeps && !conv; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int e = tid; e < n * n; e += nt) {
             const double a2 = zabs2(A[e]);
@@ -62,57 +83,69 @@ static __device__ bool jacobi_herm(int n, double2* A, double2* V, double* w, dou
             conv = true;
             break;
         }
-        for (int p = 0; p < n - 1; ++p)
-            for (int r = p + 1; r < n; ++r) {
-                if (tid == 0) {
+        for (int rd = 0; rd < np - 1; ++rd) {
+            // rotation parameters of the round's pairs (W_pp, W_pr, W_rp, W_rr, skip)
+            for (int i = tid; i < half; i += nt) {
+                int p, r;
+                round_pair(np, rd, i, p, r);
+                double2* R = rot + 5 * i;
+                double skip = 1.0;
+                if (p < n && r < n) {
                     const double2 apr = A[p * n + r];
                     const double mag = sqrt(zabs2(apr));
                     const double app = A[p * n + p].x, arr = A[r * n + r].x;
-                    double skip = 0.0;
-                    if (mag == 0.0) {
-                        skip = 1.0;
-                    } else if (mag < 1e-300 || mag <= 1e-21 * sqrt(fabs(app * arr))) {
-                        A[p * n + r] = A[r * n + p] = make_double2(0.0, 0.0);
-                        skip = 1.0;
-                    }
-                    if (skip == 0.0) {
+                    if (mag != 0.0 && (mag < 1e-300 || mag <= 1e-21 * sqrt(fabs(app * arr)))) {
+                        A[p * n + r] = A[r * n + p] = make_double2(0.0, 0.0);   // negligible: drop it
+                    } else if (mag != 0.0) {
+                        skip = 0.0;
                         const double2 em = make_double2(apr.x / mag, -apr.y / mag);   // e^{-i phi}
                         const double tau = (arr - app) / (2.0 * mag);
                         const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                        rot[0] = make_double2(c, 0.0);                    // W_pp
-                        rot[1] = make_double2(s, 0.0);                    // W_pr
-                        rot[2] = make_double2(-s * em.x, -s * em.y);      // W_rp
-                        rot[3] = make_double2(c * em.x, c * em.y);        // W_rr
-                    }
-                    rot[4] = make_double2(skip, 0.0);
-                }
-                __syncthreads();
-                if (rot[4].x == 0.0) {
-                    const double2 Wpp = rot[0], Wpr = rot[1], Wrp = rot[2], Wrr = rot[3];
-                    for (int i = tid; i < n; i += nt) {   // A <- A W, V <- V W (columns p, r)
-                        const double2 aip = A[i * n + p], air = A[i * n + r];
-                        A[i * n + p] = zadd(zmul(aip, Wpp), zmul(air, Wrp));
-                        A[i * n + r] = zadd(zmul(aip, Wpr), zmul(air, Wrr));
-                        const double2 vip = V[i * n + p], vir = V[i * n + r];
-                        V[i * n + p] = zadd(zmul(vip, Wpp), zmul(vir, Wrp));
-                        V[i * n + r] = zadd(zmul(vip, Wpr), zmul(vir, Wrr));
-                    }
-                    __syncthreads();
-                    for (int j = tid; j < n; j += nt) {   // A <- W^H A (rows p, r)
-                        const double2 apj = A[p * n + j], arj = A[r * n + j];
-                        A[p * n + j] = zadd(zmul(zconj(Wpp), apj), zmul(zconj(Wrp), arj));
-                        A[r * n + j] = zadd(zmul(zconj(Wpr), apj), zmul(zconj(Wrr), arj));
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        A[p * n + r] = A[r * n + p] = make_double2(0.0, 0.0);
-                        A[p * n + p].y = 0.0;
-                        A[r * n + r].y = 0.0;
+                        R[0] = make_double2(c, 0.0);
+                        R[1] = make_double2(s, 0.0);
+                        R[2] = make_double2(-s * em.x, -s * em.y);
+                        R[3] = make_double2(c * em.x, c * em.y);
                     }
                 }
-                __syncthreads();
+                R[4] = make_double2(skip, 0.0);
             }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += nt) {   // A <- A W, V <- V W (columns of every pair)
+                const int i = e / n, row = e - i * n;
+                const double2* R = rot + 5 * i;
+                if (R[4].x != 0.0) continue;
+                int p, r;
+                round_pair(np, rd, i, p, r);
+                const double2 aip = A[row * n + p], air = A[row * n + r];
+                A[row * n + p] = zadd(zmul(aip, R[0]), zmul(air, R[2]));
+                A[row * n + r] = zadd(zmul(aip, R[1]), zmul(air, R[3]));
+                const double2 vip = V[row * n + p], vir = V[row * n + r];
+                V[row * n + p] = zadd(zmul(vip, R[0]), zmul(vir, R[2]));
+                V[row * n + r] = zadd(zmul(vip, R[1]), zmul(vir, R[3]));
+            }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += nt) {   // A <- W^H A (rows of every pair)
+                const int i = e / n, col = e - i * n;
+                const double2* R = rot + 5 * i;
+                if (R[4].x != 0.0) continue;
+                int p, r;
+                round_pair(np, rd, i, p, r);
+                const double2 apj = A[p * n + col], arj = A[r * n + col];
+                A[p * n + col] = zadd(zmul(zconj(R[0]), apj), zmul(zconj(R[2]), arj));
+                A[r * n + col] = zadd(zmul(zconj(R[1]), apj), zmul(zconj(R[3]), arj));
+            }
+            __syncthreads();
+            for (int i = tid; i < half; i += nt) {   // a rotated pair is exactly decoupled
+                if (rot[5 * i + 4].x != 0.0) continue;
+                int p, r;
+                round_pair(np, rd, i, p, r);
+                A[p * n + r] = A[r * n + p] = make_double2(0.0, 0.0);
+                A[p * n + p].y = 0.0;
+                A[r * n + r].y = 0.0;
+            }
+            __syncthreads();
+        }
     }
     for (int i = tid; i < n; i += nt) w[i] = A[i * n + i].x;
     __syncthreads();
@@ -137,11 +170,12 @@ static __device__ void sort_ascending(int n, const double* w, int* perm) {
 }
 
 // Shared memory of k_gen_herm_eig for order n, in this order (16-byte
-// aligned double2 first): four n x n double2 matrices, the 5 double2 of the
-// rotation, n doubles, 2 * nthreads doubles of reductions, n ints.
+// aligned double2 first): four n x n double2 matrices, the rotation slots
+// (jacobi_rot_slots(n) double2), n doubles, 2 * nthreads doubles of
+// reductions, n ints.
 __host__ __device__ constexpr size_t gen_eig_smem(int n, int nthreads) {
-    return (size_t)4 * n * n * sizeof(double2) + 5 * sizeof(double2) + (size_t)n * sizeof(double) +
-           (size_t)2 * nthreads * sizeof(double) + (size_t)n * sizeof(int);
+    return (size_t)4 * n * n * sizeof(double2) + (size_t)jacobi_rot_slots(n) * sizeof(double2) +
+           (size_t)n * sizeof(double) + (size_t)2 * nthreads * sizeof(double) + (size_t)n * sizeof(int);
 }
 
 // Batched generalised problems, one per blockIdx.x: K, M (n x n row-major
@@ -157,7 +191,7 @@ static __global__ void k_gen_herm_eig(int n, const double2* __restrict__ K, cons
     double2* X = L + n * n;
     double2* W = X + n * n;
     double2* rot = W + n * n;
-    double* w = reinterpret_cast<double*>(rot + 5);
+    double* w = reinterpret_cast<double*>(rot + jacobi_rot_slots(n));
     double* red = w + n;
     int* perm = reinterpret_cast<int*>(red + 2 * blockDim.x);
     __shared__ int bad;

@@ -629,11 +629,12 @@ static __global__ void k_lz_norm(const double2* __restrict__ dots, double scale,
 }
 
 // Shared memory of k_lz_ritz for basis size m, in this order (16-byte aligned
-// double2 first): two m x m double2 matrices, the 5 double2 of the rotation,
-// m doubles, 2 * nthreads doubles of reductions, m ints.
+// double2 first): two m x m double2 matrices, the rotation slots
+// (jacobi_rot_slots(m) double2), m doubles, 2 * nthreads doubles of
+// reductions, m ints.
 __host__ __device__ constexpr size_t lz_ritz_smem(int m, int nthreads) {
-    return (size_t)2 * m * m * sizeof(double2) + 5 * sizeof(double2) + (size_t)m * sizeof(double) +
-           (size_t)2 * nthreads * sizeof(double) + (size_t)m * sizeof(int);
+    return (size_t)2 * m * m * sizeof(double2) + (size_t)jacobi_rot_slots(m) * sizeof(double2) +
+           (size_t)m * sizeof(double) + (size_t)2 * nthreads * sizeof(double) + (size_t)m * sizeof(int);
 }
 
 // Thick-restart analysis of slot blockIdx.x (Section 3.3 shift-invert
@@ -652,7 +653,7 @@ static __global__ void k_lz_ritz(int m, double2* __restrict__ H, const int* __re
     double2* A = reinterpret_cast<double2*>(smem_raw);
     double2* Y = A + m * m;
     double2* rot = Y + m * m;
-    double* w = reinterpret_cast<double*>(rot + 5);
+    double* w = reinterpret_cast<double*>(rot + jacobi_rot_slots(m));
     double* red = w + m;
     int* perm = reinterpret_cast<int*>(red + 2 * blockDim.x);
     __shared__ double beta;

@@ -602,8 +602,9 @@ bloch_status bloch_lp_add_pairs(bloch_lp* lp, bloch_plan* pl, const double* k, i
     if (!lp || !pl || !k || !r || !e) return set_error(BLOCH_EINVAL, "NULL argument");
     if (n_pairs < 1 || n_pairs > 65535 / 6) return set_error(BLOCH_EINVAL, "n_pairs must be in [1, 10922]");
     bloch_status st;
-    if ((st = set_k<float>(pl, 1, k)) != BLOCH_OK) return st;
+    // grow the workspace first: growing reallocates the q tables set_k fills
     if ((st = ensure_cg<float>(pl, n_pairs)) != BLOCH_OK) return st;
+    if ((st = set_k<float>(pl, 1, k)) != BLOCH_OK) return st;
     if ((st = lp_weights_cap(lp, n_pairs)) != BLOCH_OK) return st;
     const float2* rr = (const float2*)r;
     const float2* ee = (const float2*)e;
