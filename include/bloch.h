@@ -452,10 +452,15 @@ bloch_status bloch_plan_autotune(bloch_plan* plan, int32_t precision, int32_t sy
  *   2 FP32 residual applies (A_k u, M u, Rayleigh quotients, residual norms)
  *   3 FP64 residual applies (the FP64 check of the FP32 form, incl. conversion)
  *   4 Lanczos orthogonalisation (inner products, updates, normalisation)
- *   5 Algorithm 1 projections (correction, Gram matrices, basis rotation)
- *   6 GPU span of the solve (first to last event; 6 minus the sum of 0-5 is
- *     idle time and untraced work on the stream)
- *   7 host wall time of the solve
+ *   5 Algorithm 1 projections (correction, Gram matrices, the projected
+ *     eigensolve, basis rotation)
+ *   6 Lanczos restarts (Ritz analysis, basis rotation, restart copies,
+ *     compaction of converged wave vectors)
+ *   7 slot set-up and output (start vectors, wave-vector tables, hand-off
+ *     between the solvers, eigenvector output)
+ *   8 GPU span of the solve (first to last event; 8 minus the sum of 0-7 is
+ *     the time the stream had no traced work: idle gaps and small kernels)
+ *   9 host wall time of the solve
  * count[i] = intervals recorded.  bloch_plan_trace synchronises the plan's
  * stream, writes the totals since the previous call to *out (may be NULL),
  * resets them, and then turns tracing on (enable = 1) or off (0).  Tracing
@@ -463,8 +468,8 @@ bloch_status bloch_plan_autotune(bloch_plan* plan, int32_t precision, int32_t sy
  * Errors: BLOCH_EINVAL, BLOCH_ECUDA.
  */
 typedef struct {
-    double ms[8];
-    int64_t count[8];
+    double ms[10];
+    int64_t count[10];
 } bloch_trace;
 
 bloch_status bloch_plan_trace(bloch_plan* plan, int32_t enable, bloch_trace* out);

@@ -48,10 +48,10 @@ class Options(ctypes.Structure):
 
 
 class Trace(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_int64 * 8)]
+    _fields_ = [("ms", ctypes.c_double * 10), ("count", ctypes.c_int64 * 10)]
 
     PHASES = ("pcg_subspace", "pcg_lanczos", "residual_fp32", "residual_fp64", "lanczos_orth", "projection",
-              "gpu_span", "wall")
+              "lanczos_restart", "setup", "gpu_span", "wall")
 
     def as_dict(self):
         return {ph: {"ms": self.ms[i], "count": int(self.count[i])} for i, ph in enumerate(self.PHASES)}

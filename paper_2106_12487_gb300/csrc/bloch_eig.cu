@@ -484,6 +484,7 @@ struct Subspace {
     }
 
     bloch_status init_slot(int s, int kidx) {
+        TraceScope tr(pl, TR_SETUP);
         Slot& sl = slots[s];
         sl = Slot();
         sl.kidx = kidx;
@@ -643,6 +644,7 @@ struct Subspace {
     }
 
     void finalize_slot(int s, bool converged) {
+        TraceScope tr(pl, TR_SETUP);
         Slot& sl = slots[s];
         const double lam_scale = pl->Kscale / pl->rho_ref;
         double* om = omega_out + (size_t)sl.kidx * n_bands;
@@ -688,6 +690,7 @@ struct Subspace {
 
     // move slot `from` into slot `to` (device blocks U, R, MU and host state)
     bloch_status move_slot(int from, int to) {
+        TraceScope tr(pl, TR_SETUP);
         const size_t bytes = sizeof(C) * q * n3;
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(U, to), vec(U, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(R, to), vec(R, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
@@ -1059,6 +1062,7 @@ struct Lanczos {
 
     // a new batch of wave vectors: random start vectors, M-normalised
     bloch_status start_batch() {
+        TraceScope tr(pl, TR_SETUP);
         nact = 0;
         while (nact < B && next_k < order.size()) {
             Slot& sl = slots[nact];
@@ -1192,6 +1196,7 @@ struct Lanczos {
     bloch_status restart() {
         const int kr = kk_restart();
         const int kc = std::max(kr, kk_out());
+        const int tr_rs = trace_begin(pl, TR_RESTART);
         pl->launches += 3;
         k_lz_ritz<<<nact, kThreadsRitz, lz_ritz_smem(m, kThreadsRitz), pl->stream>>>(
             m, d_H, d_neff, tol_eig, kc, kr, d_Q, d_theta, d_est, d_conv, d_jac);
@@ -1203,6 +1208,7 @@ struct Lanczos {
             k_lz_restart_copy<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(MVb, TmpM, m, kr, n3);
         }
         BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+        trace_end(pl, tr_rs);
         std::vector<double> th((size_t)nact * m), es((size_t)nact * m);
         std::vector<int> cv(nact), jo(nact);
         long long tl[4];
@@ -1220,6 +1226,7 @@ struct Lanczos {
         for (int i = 0; i < 4; ++i) tally_host[i] = tl[i];
         if (nonfinite) return set_error(BLOCH_ENONFINITE, "PCG met a non-finite residual in a Lanczos step");
         restarts += 1;
+        TraceScope tr_out(pl, TR_RESTART);
         std::vector<char> done(nact, 0);
         for (int i = 0; i < nact; ++i) {
             const bool conv = cv[i] != 0 && jo[i] != 0;

@@ -42,7 +42,10 @@ constexpr int kDefaultPmax = 32;
 constexpr int kFastZThreads = 256;
 
 // Phases of a band solve timed by the tracer (bloch_plan_trace).
-enum TracePhase { TR_PCG_SUB = 0, TR_PCG_LZ, TR_RES32, TR_RES64, TR_ORTHO, TR_PROJECT, TR_SPAN, TR_WALL, TR_NPHASE };
+enum TracePhase {
+    TR_PCG_SUB = 0, TR_PCG_LZ, TR_RES32, TR_RES64, TR_ORTHO, TR_PROJECT, TR_RESTART, TR_SETUP, TR_SPAN, TR_WALL,
+    TR_NPHASE
+};
 
 // Event-pair timing of solver phases on the plan's stream; pairs are read
 // back after the solve's final synchronisation.

@@ -107,12 +107,14 @@ def test_trace_phases_are_consistent(B, prec, method):
     plan.solve_bands(ks, 4)
     tr = plan.trace(False)
     parts = sum(tr[k]["ms"] for k in ("pcg_subspace", "pcg_lanczos", "residual_fp32", "residual_fp64",
-                                      "lanczos_orth", "projection"))
+                                      "lanczos_orth", "projection", "lanczos_restart", "setup"))
     assert 0 < parts <= tr["gpu_span"]["ms"] * 1.001
     assert tr["gpu_span"]["ms"] <= tr["wall"]["ms"] * 1.001
     assert tr["gpu_span"]["count"] == 1 and tr["wall"]["count"] == 1
     assert (tr["pcg_lanczos"]["count"] > 0) == (method == 0)
     assert (tr["lanczos_orth"]["count"] > 0) == (method == 0)
+    assert (tr["lanczos_restart"]["count"] > 0) == (method == 0)
+    assert tr["setup"]["count"] > 0
     assert tr["pcg_subspace"]["count"] > 0 or method == 0
     if prec == 0:
         assert tr["residual_fp64"]["count"] > 0 or method == 0
