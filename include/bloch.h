@@ -53,11 +53,11 @@ typedef enum {
     BLOCH_ENOTCONV_EIG = 5,  /* the eigensolver hit its sweep/restart cap        */
     BLOCH_ENONFINITE = 6,    /* NaN or Inf met in inputs or iterates             */
     BLOCH_EUNSUPPORTED = 7   /* grid size with a prime factor > 7 or too large;
-                                Lanczos with a non-uniform density             */
+                                a block or basis above the solver's limits      */
 } bloch_status;
 
 typedef enum { BLOCH_FP64 = 0, BLOCH_FP32 = 1 } bloch_precision;
-typedef enum { BLOCH_LANCZOS = 0, BLOCH_SUBSPACE = 1 } bloch_method;
+typedef enum { BLOCH_LANCZOS = 0, BLOCH_SUBSPACE = 1, BLOCH_LOBPCG = 2 } bloch_method;
 
 typedef struct bloch_plan bloch_plan;   /* opaque; owned by the library */
 
@@ -67,10 +67,14 @@ typedef struct {
                             BLOCH_FP32: fields and CG in FP32 complex with FP32
                             accumulation, then an FP64 Rayleigh-Ritz refinement of the
                             converged block.  Default BLOCH_FP64.                       */
-    int32_t method;      /* BLOCH_LANCZOS (shift-invert Lanczos with thick restart; needs a
-                            uniform density, else bloch_solve_bands returns
-                            BLOCH_EUNSUPPORTED) or BLOCH_SUBSPACE (Algorithm 1, any
-                            density).  Default BLOCH_SUBSPACE.                          */
+    int32_t method;      /* BLOCH_LANCZOS (shift-invert Lanczos with thick restart, Section
+                            3.3), BLOCH_SUBSPACE (Algorithm 1) or BLOCH_LOBPCG (locally
+                            optimal block preconditioned CG on the pencil (A_k, M), block
+                            [X, W = T R, P] with T the Green preconditioner of Eq.
+                            (precond) and a rank-revealing Rayleigh-Ritz; no inner PCG;
+                            block q = n + 2 unless set, 3q <= 44, 48 with a uniform
+                            density).  Every method handles any density and k = 0.
+                            Default BLOCH_SUBSPACE.                                     */
     double tol_lin;      /* PCG stop: ||Y - A U||_2 <= tol_lin ||Y||_2.  Default 1e-10.  */
     double tol_eig;      /* eigensolver stop (see bloch_solve_bands).  Default 1e-10.    */
     int32_t max_cg;      /* PCG iteration cap per solve.  Default 2000.                  */

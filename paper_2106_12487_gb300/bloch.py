@@ -20,7 +20,7 @@ BLOCH_OK = 0
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV_CG", 5: "ENOTCONV_EIG",
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
 FP64, FP32 = 0, 1
-LANCZOS, SUBSPACE = 0, 1
+LANCZOS, SUBSPACE, LOBPCG = 0, 1, 2
 
 EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", "bloch_apply_K",
             "bloch_apply_M", "bloch_apply_precond", "bloch_pcg", "bloch_solve_bands",

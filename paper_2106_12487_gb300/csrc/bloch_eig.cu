@@ -362,6 +362,17 @@ struct Subspace {
     long long n3;
     bool fp64res;     // FP32 fields with an FP64 residual refinement phase
     bool uniform;
+    // LOBPCG (block method for a single wave vector; batched over wave
+    // vectors like Algorithm 1): the block [X, W, P] is stored as three
+    // segments of B*q vectors, X = U, W = T R (T = the Green operator), P the
+    // previous search directions; A and M images alongside (KU, MU segments).
+    bool lob = false;
+    C *Wb = nullptr, *Pb = nullptr, *AWb = nullptr, *APb = nullptr, *MWb = nullptr, *MPb = nullptr;
+    C *P2 = nullptr, *AP2 = nullptr, *MP2 = nullptr;
+    double2* d_C3 = nullptr;
+    double* d_lam3 = nullptr;
+    size_t gsmem3 = 0;
+    long long segs = 0;   // elements between the segments of the block
     double rho_s;
     double tol_eig, tol_lin;
     int max_outer, max_cg;
@@ -426,15 +437,35 @@ struct Subspace {
     bloch_status setup() {
         bloch_status s;
         const size_t blk = (size_t)B * q * n3;
-        if ((s = alloc(&U, blk)) || (s = alloc(&Ub, blk)) || (s = alloc(&KU, blk)) || (s = alloc(&R, blk))) return s;
+        segs = (long long)blk;
+        const size_t ns = lob ? 3 : 1;   // X (and W, P) segments
+        if ((s = alloc(&U, ns * blk)) || (s = alloc(&Ub, blk)) || (s = alloc(&KU, ns * blk)) || (s = alloc(&R, blk)))
+            return s;
         if (!uniform) {
-            if ((s = alloc(&MU, blk)) || (s = alloc(&MUb, blk))) return s;
+            if ((s = alloc(&MU, ns * blk)) || (s = alloc(&MUb, blk))) return s;
+        }
+        if (lob) {
+            Wb = U + blk;
+            Pb = U + 2 * blk;
+            AWb = KU + blk;
+            APb = KU + 2 * blk;
+            if (!uniform) {
+                MWb = MU + blk;
+                MPb = MU + 2 * blk;
+            }
+            if ((s = alloc(&P2, blk)) || (s = alloc(&AP2, blk))) return s;
+            if (!uniform && (s = alloc(&MP2, blk))) return s;
+            if ((s = alloc(&d_C3, (size_t)B * 9 * q * q)) || (s = alloc(&d_lam3, (size_t)B * 3 * q))) return s;
+            gsmem3 = gk_smem<T>(3 * q, !uniform);
+            if (cudaFuncSetAttribute(k_svqb_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)gen_eig_smem(3 * q, kEigThreads)) != cudaSuccess)
+                return set_error(BLOCH_ECUDA, "cudaFuncSetAttribute (LOBPCG Rayleigh-Ritz)");
         }
         dblk = (int)std::max(1LL, std::min<long long>((n3 + 255) / 256, std::max(1, 2048 / std::max(1, B * q))));
         gblk = (int)std::max(1LL, std::min<long long>((n3 + kGKChunk - 1) / kGKChunk, std::max(1, 608 / B)));
         gsmem = gk_smem<T>(q, !uniform);
-        if (cudaFuncSetAttribute(k_gram_km<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_gram_km<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max(gsmem, gsmem3)) != cudaSuccess)
             return set_error(BLOCH_ECUDA, "cudaFuncSetAttribute (Gram kernel)");
         if constexpr (std::is_same<T, float>::value) {
             use_tc = pl->opt.tensor_gram != 0 && q <= kQMaxTC;
@@ -452,7 +483,8 @@ struct Subspace {
         }
         const int gpart_blk = std::max(gblk, gblk_tc);
         if ((s = alloc(&d_part, (size_t)B * q * dblk * 3)) || (s = alloc(&d_scal, (size_t)B * q * 2)) ||
-            (s = alloc(&d_gpart, (size_t)B * gpart_blk * 2 * q * q)) || (s = alloc(&d_G, (size_t)2 * B * q * q)) ||
+            (s = alloc(&d_gpart, (size_t)B * gpart_blk * 2 * q * q * (lob ? 9 : 1))) ||
+            (s = alloc(&d_G, (size_t)2 * B * q * q * (lob ? 9 : 1))) ||
             (s = alloc(&d_Q, (size_t)B * q * q)) || (s = alloc(&d_idx, (size_t)3 * q)) ||
             (s = alloc(&d_val, (size_t)3 * q)))
             return s;
@@ -483,8 +515,20 @@ struct Subspace {
         return set_k<T>(pl, count * q, kv.data());
     }
 
+    // LOBPCG: no search direction yet (a zero P is dropped by the rank-revealing Rayleigh-Ritz)
+    bloch_status clear_directions(int s) {
+        if (!lob) return BLOCH_OK;
+        const size_t bytes = sizeof(C) * q * n3;
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(vec(Pb, s), 0, bytes, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(vec(APb, s), 0, bytes, pl->stream));
+        if (!uniform) BLOCH_CUDA_CHECK_RET(cudaMemsetAsync(vec(MPb, s), 0, bytes, pl->stream));
+        return BLOCH_OK;
+    }
+
     bloch_status init_slot(int s, int kidx) {
         TraceScope tr(pl, TR_SETUP);
+        bloch_status cs = clear_directions(s);
+        if (cs != BLOCH_OK) return cs;
         Slot& sl = slots[s];
         sl = Slot();
         sl.kidx = kidx;
@@ -697,6 +741,14 @@ struct Subspace {
         if (!uniform)
             BLOCH_CUDA_CHECK_RET(
                 cudaMemcpyAsync(vec(MU, to), vec(MU, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        if (lob) {
+            BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(vec(Pb, to), vec(Pb, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+            BLOCH_CUDA_CHECK_RET(
+                cudaMemcpyAsync(vec(APb, to), vec(APb, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+            if (!uniform)
+                BLOCH_CUDA_CHECK_RET(
+                    cudaMemcpyAsync(vec(MPb, to), vec(MPb, from), bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        }
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_invlam + (size_t)to * q, d_invlam + (size_t)from * q,
                                              sizeof(double) * q, cudaMemcpyDeviceToDevice, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(d_rq + (size_t)to * q * 4, d_rq + (size_t)from * q * 4,
@@ -717,6 +769,8 @@ struct Subspace {
         const double* kn = (*klist)[kidx].data();
         const bool gn = kn[0] == 0.0 && kn[1] == 0.0 && kn[2] == 0.0;
         if (prev.gamma || gn) return init_slot(s, kidx);
+        bloch_status cs = clear_directions(s);
+        if (cs != BLOCH_OK) return cs;
         Slot& sl = slots[s];
         sl = Slot();
         sl.kidx = kidx;
@@ -724,6 +778,70 @@ struct Subspace {
         sl.gamma = false;
         sl.n_eff = n_bands;
         sl.phase = 0;
+        return BLOCH_OK;
+    }
+
+    // One LOBPCG iteration on every active slot (enqueued, no host wait):
+    // W = T R with T = P^-1 (the Green operator, Eq. precond), A W and M W,
+    // the Rayleigh-Ritz projection of (A, M) on [X, W, P] (3q vectors, one
+    // Gram pass), its rank-revealing solve, X <- [X, W, P] C_q and
+    // P <- [W, P] C_q (with A P, M P carried alongside).  The next residual
+    // step applies A to the new X afresh.
+    bloch_status lobpcg_step() {
+        bloch_status s;
+        const int q3 = 3 * q;
+        if ((s = set_k_range(0, nact)) != BLOCH_OK) return s;
+        if ((s = lp_activate<T>(pl, nact, q, q)) != BLOCH_OK) return s;
+        TraceScope tr(pl, TR_PROJECT);
+        launch_precond<T>(pl, nact * q, R, Wb, T(1));
+        lp_deactivate(pl);
+        {
+            TraceScope trk(pl, std::is_same<T, float>::value ? TR_RES32 : TR_RES64);
+            launch_K<T>(pl, nact * q, Wb, AWb, T(1));
+            if (!uniform) launch_M<T>(pl, nact * q, Wb, MWb, T(1));
+        }
+        st->k_applies += (long long)nact * q;
+        if (!uniform)
+            for (int i = 0; i < nact; ++i)
+                if (slots[i].gamma && (s = gamma_deflate<T>(pl, q, vec(Wb, i), vec(MWb, i), d_alpha)) != BLOCH_OK)
+                    return s;
+        const int np3 = q3 * q3;
+        pl->launches += 3;
+        k_gram_km<T><<<dim3(gblk, nact), kGKThreads, gsmem3, pl->stream>>>(U, KU, uniform ? nullptr : MU, q3, n3,
+                                                                          d_gpart, q, segs);
+        k_gram_final<<<dim3((2 * np3 + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, np3, nact, d_G);
+        // rank-revealing Rayleigh-Ritz: directions of [X, W, P] whose M-norm falls
+        // below the field precision's resolution are dropped
+        const double eps = std::is_same<T, float>::value ? 1e-6 : 1e-13;
+        k_svqb_eig<<<nact, kEigThreads, gen_eig_smem(q3, kEigThreads), pl->stream>>>(
+            q3, d_G, d_G + (size_t)nact * np3, uniform ? rho_s : 1.0, eps, d_lam3, d_C3, d_status);
+        eig_pending = 0;
+        RotView rx;
+        rx.in_slot = (long long)q * n3;
+        rx.segstride = segs;
+        rx.out_slot = (long long)q * n3;
+        rx.qstride = np3;
+        rx.qi = q3;
+        rx.qo = q;
+        rx.seg = q;
+        rx.ldq = q3;
+        RotView rp = rx;
+        rp.qi = 2 * q;   // [W, P] with the rows q..3q of C
+        pl->launches += 3;
+        launch_rotate<T>(pl->stream, nact, U, Ub, d_C3, rx, n3);
+        launch_rotate<T>(pl->stream, nact, Wb, P2, d_C3 + q * q3, rp, n3);
+        launch_rotate<T>(pl->stream, nact, AWb, AP2, d_C3 + q * q3, rp, n3);
+        if (!uniform) {
+            ++pl->launches;
+            launch_rotate<T>(pl->stream, nact, MWb, MP2, d_C3 + q * q3, rp, n3);
+        }
+        const size_t bytes = sizeof(C) * (size_t)nact * q * n3;
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(U, Ub, bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(Pb, P2, bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(APb, AP2, bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        if (!uniform) BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(MPb, MP2, bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        for (int i = 0; i < nact; ++i) slots[i].sweeps += 1;
+        BLOCH_CUDA_CHECK_RET(cudaGetLastError());
         return BLOCH_OK;
     }
 
@@ -810,6 +928,11 @@ struct Subspace {
                     if ((s = residual_step(f, 1)) != BLOCH_OK) return s;
                 if (nact == 0) break;
             }
+            if (lob) {
+                if ((s = lobpcg_step()) != BLOCH_OK) return s;
+                if ((s = residual_step(0, nact)) != BLOCH_OK) return s;
+                continue;
+            }
             // inverse step on all active slots: delta = A^-1 R (enqueued; no host wait)
             if ((s = set_k_range(0, nact)) != BLOCH_OK) return s;
             if ((s = lp_activate<T>(pl, nact, q, q)) != BLOCH_OK) return s;
@@ -850,7 +973,7 @@ struct Subspace {
             if (!use_tc) {
                 ++pl->launches;
                 k_gram_km<T><<<gg, kGKThreads, gsmem, pl->stream>>>(Ub, KU, uniform ? nullptr : MUb, q, n3,
-                                                                    d_gpart);
+                                                                    d_gpart, q, 0LL);
                 ++pl->launches;
                 k_gram_final<<<dim3((2 * npair + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, npair,
                                                                                            nact, d_G);
@@ -886,10 +1009,21 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     S.n3 = 3 * pl->V;
     S.n_bands = n_bands;
     S.n = n_bands;
-    const int qa = std::min(2 * n_bands, n_bands + 8);
+    S.lob = pl->opt.method == BLOCH_LOBPCG && init_blocks == nullptr;
+    const int qa = S.lob ? n_bands + 2 : std::min(2 * n_bands, n_bands + 8);
     S.q = pl->opt.block > 0 ? pl->opt.block : qa;
     S.q = std::max(S.q, n_bands + 1);
     if (S.q > kQMax) return set_error(BLOCH_EUNSUPPORTED, "block size above 32 vectors is not supported");
+    if (S.lob) {
+        // one Gram pass over [X, W, P]: 3q <= 44 (48 with a uniform density) tiles per CTA,
+        // and its staging must fit the shared memory of a CTA
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const int qmax3 = pl->uniform_rho ? 48 : 44;
+        if (3 * S.q > qmax3 || gk_smem<T>(3 * S.q, !pl->uniform_rho) > (size_t)optin)
+            return set_error(BLOCH_EUNSUPPORTED, "LOBPCG block too large for one Gram pass (reduce the bands or the block)");
+    }
     if ((long long)S.q > 3 * pl->V - 3) return set_error(BLOCH_EINVAL, "block larger than the problem");
     S.fp64res = fp64res;
     S.uniform = pl->uniform_rho;
@@ -918,7 +1052,7 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     cudaMemGetInfo(&freeb, &totb);
     freeb += plan_solver_bytes(pl);   // held by the plan from earlier solves, reused
     const size_t blk = (size_t)S.q * S.n3 * sizeof(cplx_t<T>);
-    const size_t per_slot = blk * (S.uniform ? 9 : 11) + 64 * 1024;
+    const size_t per_slot = blk * (S.lob ? (S.uniform ? 15 : 20) : (S.uniform ? 9 : 11)) + 64 * 1024;
     long long Bmax = std::max<long long>(1, (long long)(0.6 * (double)freeb / (double)per_slot));
     Bmax = std::min<long long>(Bmax, 10922 / S.q);
     int B = pl->opt.k_batch > 0 ? pl->opt.k_batch : (int)Bmax;
@@ -1408,7 +1542,7 @@ bloch_status bloch_solve_bands_impl(bloch_plan* pl, int n_k, const double* k_lis
         s = bloch_plan_autotune(pl, pl->opt.precision, std::max(1, std::min(q, 10922)), nullptr);
         if (s != BLOCH_OK) return s;
     }
-    if (pl->opt.method == BLOCH_SUBSPACE) {
+    if (pl->opt.method == BLOCH_SUBSPACE || pl->opt.method == BLOCH_LOBPCG) {
         if (pl->opt.precision == BLOCH_FP32)
             s = run_subspace<float>(pl, ks, n_bands, omega_out, vecs_out, &st, true);
         else

@@ -275,4 +275,95 @@ static __global__ void k_gen_herm_eig(int n, const double2* __restrict__ K, cons
     if (tid == 0) status[b] = conv ? 0 : 2;
 }
 
+// Rank-revealing Rayleigh-Ritz of a pencil (K, M) whose M may be singular
+// (SVQB, Stathopoulos & Wu 2002): M = V D V^H (Jacobi); the directions with
+// D > eps * max(D) are kept, Z = V_keep D_keep^-1/2 (M-orthonormal); then
+// C = Z^H K Z = Y diag(lam) Y^H (Jacobi) and the Ritz vectors in the original
+// coordinates are Q = Z Y.  One CTA per pencil (blockIdx.x); K, M, Q n x n
+// row-major (double2) at b * n * n; M scaled by mscale.  Out: lam[b][0..r)
+// ascending, Q[b] columns 0..r (the rest zero), rank[b] = r.  Shared memory:
+// gen_eig_smem(n, blockDim.x).
+static __global__ void k_svqb_eig(int n, const double2* __restrict__ K, const double2* __restrict__ M, double mscale,
+                                  double eps, double* __restrict__ lam, double2* __restrict__ Q,
+                                  int* __restrict__ rank) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* A = reinterpret_cast<double2*>(smem_raw);   // M, then C
+    double2* Vm = A + n * n;                            // eigenvectors of M, then Z
+    double2* Kh = Vm + n * n;
+    double2* Y = Kh + n * n;
+    double2* rot = Y + n * n;
+    double* w = reinterpret_cast<double*>(rot + jacobi_rot_slots(n));
+    double* red = w + n;
+    int* perm = reinterpret_cast<int*>(red + 2 * blockDim.x);
+    __shared__ int r_sh;
+    __shared__ double dmax_sh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int b = blockIdx.x;
+    const double2* Kb = K + (size_t)b * n * n;
+    const double2* Mb = M + (size_t)b * n * n;
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        const double2 m1 = Mb[i * n + j], m2 = Mb[j * n + i];
+        A[e] = make_double2(0.5 * mscale * (m1.x + m2.x), 0.5 * mscale * (m1.y - m2.y));
+        const double2 k1 = Kb[i * n + j], k2 = Kb[j * n + i];
+        Kh[e] = make_double2(0.5 * (k1.x + k2.x), 0.5 * (k1.y - k2.y));
+    }
+    __syncthreads();
+    jacobi_herm(n, A, Vm, w, red, rot);
+    if (tid == 0) {
+        double dm = 0.0;
+        for (int i = 0; i < n; ++i) dm = fmax(dm, w[i]);
+        dmax_sh = dm;
+        int r = 0;   // kept directions, compacted to the front in original order
+        for (int i = 0; i < n; ++i)
+            if (w[i] > eps * dm && dm > 0.0) perm[r++] = i;
+        r_sh = r;
+    }
+    __syncthreads();
+    const int r = r_sh;
+    // Z[:, c] = Vm[:, perm[c]] / sqrt(w[perm[c]]) into Y (n x r, row-major n x n storage)
+    for (int e = tid; e < n * r; e += nt) {
+        const int i = e / r, c = e % r;
+        const double s = 1.0 / sqrt(w[perm[c]]);
+        const double2 v = Vm[i * n + perm[c]];
+        Y[i * n + c] = make_double2(v.x * s, v.y * s);
+    }
+    __syncthreads();
+    // T = Kh Z (n x r) into Vm
+    for (int e = tid; e < n * r; e += nt) {
+        const int i = e / r, c = e % r;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < n; ++k) acc = zadd(acc, zmul(Kh[i * n + k], Y[k * n + c]));
+        Vm[i * n + c] = acc;
+    }
+    __syncthreads();
+    // C = Z^H T (r x r, stored r x r row-major) into A
+    for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e % r;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < n; ++k) acc = zadd(acc, zmul(zconj(Y[k * n + i]), Vm[k * n + j]));
+        A[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += nt) {   // Hermitian part (in Kh, r x r)
+        const int i = e / r, j = e % r;
+        const double2 a = A[i * r + j], c = A[j * r + i];
+        Kh[e] = make_double2(0.5 * (a.x + c.x), 0.5 * (a.y - c.y));
+    }
+    __syncthreads();
+    jacobi_herm(r, Kh, Vm, w, red, rot);   // eigenvectors (r x r) in Vm
+    sort_ascending(r, w, perm);
+    // Q = Z Y_sorted (n x r), zero beyond r
+    double2* Qb = Q + (size_t)b * n * n;
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, c = e % n;
+        double2 acc = make_double2(0.0, 0.0);
+        if (c < r)
+            for (int k = 0; k < r; ++k) acc = zadd(acc, zmul(Y[i * n + k], Vm[k * r + perm[c]]));
+        Qb[e] = acc;
+    }
+    for (int c = tid; c < n; c += nt) lam[(size_t)b * n + c] = c < r ? w[perm[c]] : 0.0;
+    if (tid == 0) rank[b] = r;
+}
+
 }  // namespace bloch

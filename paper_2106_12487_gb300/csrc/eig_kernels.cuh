@@ -17,8 +17,11 @@ constexpr int kQMax = 32;
 //   K[slot][i][j] = sum_e conj(A[i][e]) Bk[i][e]                    (all i, j < q)
 //   M[slot][i][j] = sum_e conj(A[i][e]) Bm[j][e]    Bm != nullptr   (all i, j)
 //                 = sum_e conj(A[i][e]) A[j][e]     Bm == nullptr   (i <= j tiles, mirrored)
-// partial[slot][blk][0..1][q][q] (K, then M); vectors of one slot are
-// contiguous (A + (slot*q + i)*n_per).  Each thread owns a 4x4 tile of (i, j)
+// partial[slot][blk][0..1][q][q] (K, then M).  Vector i of a slot lies at
+// base + (i / seg) * segstride + (slot * seg + i % seg) * n_per: with seg = q
+// the q vectors of a slot are contiguous; with seg < q the block is the
+// concatenation of q / seg segments of seg vectors each, segment t starting
+// t * segstride elements further (LOBPCG's [X, W, P]).  Each thread owns a 4x4 tile of (i, j)
 // and one group of elements of every chunk.  Chunks of kGKChunk elements are
 // staged element-major (row length RS, odd, so consecutive elements fall in
 // different banks and the tile rows a warp reads are spread) by cp.async, two
@@ -40,7 +43,8 @@ template <typename T>
 __global__ void __launch_bounds__(kGKThreads) k_gram_km(const cplx_t<T>* __restrict__ A,
                                                         const cplx_t<T>* __restrict__ Bk,
                                                         const cplx_t<T>* __restrict__ Bm, int q, long long n_per,
-                                                        double2* __restrict__ partial) {
+                                                        double2* __restrict__ partial, int seg,
+                                                        long long segstride) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
@@ -77,7 +81,6 @@ __global__ void __launch_bounds__(kGKThreads) k_gram_km(const cplx_t<T>* __restr
     }
     const int bmat = which == 0 ? 1 : (has_m ? 2 : 0);   // staged matrix of the right operand
     const int slot = blockIdx.y;
-    const size_t sbase = (size_t)slot * q * n_per;
     const int stage_elems = nmat * kGKChunk * RS;
     auto stage_load = [&](long long ch, int buf) {
         C* dst = sm + (size_t)buf * stage_elems;
@@ -89,8 +92,9 @@ __global__ void __launch_bounds__(kGKThreads) k_gram_km(const cplx_t<T>* __restr
             const int i = r / kGKChunk, c = r - i * kGKChunk;
             const long long e = e0 + c;
             const bool ok = i < q && e < n_per;
-            const C* src = (m == 0 ? A : (m == 1 ? Bk : Bm)) + sbase;
-            cp_async_cplx(dst + ((size_t)m * kGKChunk + c) * RS + i, src + (ok ? (size_t)i * n_per + e : 0), ok);
+            const C* src = (m == 0 ? A : (m == 1 ? Bk : Bm));
+            const size_t vo = ok ? (size_t)(i / seg) * segstride + ((size_t)slot * seg + i % seg) * n_per + e : 0;
+            cp_async_cplx(dst + ((size_t)m * kGKChunk + c) * RS + i, src + vo, ok);
         }
         cp_async_commit();
     };
@@ -189,42 +193,53 @@ static __global__ void k_gram_final(const double2* __restrict__ partial, int nbl
     out[((size_t)w * nslot + slot) * npair + pr] = make_double2(re, im);
 }
 
-// Out[slot][j][e] = sum_i In[slot][i][e] Q[slot][i][j]  (Q row-major q x q, double2).
-//
-// k_basis_reg (q <= 32): each thread loads the q inputs of its element into
-// registers at once (q loads in flight) and forms the outputs one by one from
-// Q in shared memory (broadcast reads).
-// k_basis_cols (q <= 63, Lanczos restarts with a large basis): output columns
-// in chunks of 32 (blockIdx.y = slot * nchunk + chunk), the q x 32 slice of Q
-// in dynamic shared memory, 32 accumulators per thread.
+// Basis rotation Out[slot][j][e] = sum_{i < qi} In_slot,i[e] Q[slot][i][j], j < qo.
+// Input vector i of a slot lies at In + slot * in_slot + (i / seg) * segstride
+// + (i % seg) * n_per (seg = qi: contiguous; seg < qi: segmented block such as
+// LOBPCG's [X, W, P]); Q[slot] at Q + slot * qstride with row stride ldq;
+// outputs contiguous per slot at Out + slot * out_slot.
+struct RotView {
+    long long in_slot, segstride, out_slot, qstride;
+    int qi, qo, seg, ldq;
+};
+__device__ __forceinline__ size_t rot_in(const RotView& r, int slot, int i, long long n_per) {
+    return (size_t)slot * r.in_slot + (size_t)(i / r.seg) * r.segstride + (size_t)(i % r.seg) * n_per;
+}
+
+// k_basis_reg (qi, qo <= 32): each thread loads the qi inputs of its element
+// into registers at once (qi loads in flight) and forms the outputs one by one
+// from Q in shared memory (broadcast reads).
+// k_basis_cols (any qi, qo): output columns in chunks of 32 (blockIdx.y =
+// slot * nchunk + chunk), the qi x 32 slice of Q in dynamic shared memory, 32
+// accumulators per thread.
 constexpr int kBasisQMax = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_basis_reg(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
-                                                   const double2* __restrict__ Q, int q, long long n_per,
-                                                   long long in_stride) {
+                                                   const double2* __restrict__ Q, RotView rv, long long n_per) {
     using C = cplx_t<T>;
     __shared__ C sQ[kQMax * kQMax];
     const int slot = blockIdx.y;
-    for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
-        const double2 v = Q[(size_t)slot * q * q + t];
+    const int qi = rv.qi, qo = rv.qo;
+    for (int t = threadIdx.x; t < qi * qo; t += blockDim.x) {
+        const int i = t / qo, j = t - i * qo;
+        const double2 v = Q[(size_t)slot * rv.qstride + (size_t)i * rv.ldq + j];
         sQ[t] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
-    const C* ib = In + (size_t)slot * in_stride;
-    C* ob = Out + (size_t)slot * q * n_per;
+    C* ob = Out + (size_t)slot * rv.out_slot;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
          e += (long long)gridDim.x * blockDim.x) {
         C v[kQMax];
 #pragma unroll
         for (int i = 0; i < kQMax; ++i)
-            if (i < q) v[i] = ib[(size_t)i * n_per + e];
-        for (int j = 0; j < q; ++j) {
+            if (i < qi) v[i] = In[rot_in(rv, slot, i, n_per) + e];
+        for (int j = 0; j < qo; ++j) {
             T re = 0, im = 0;
 #pragma unroll
             for (int i = 0; i < kQMax; ++i)
-                if (i < q) {
-                    const C w = sQ[i * q + j];
+                if (i < qi) {
+                    const C w = sQ[i * qo + j];
                     re = fma(v[i].x, w.x, fma(-v[i].y, w.y, re));
                     im = fma(v[i].x, w.y, fma(v[i].y, w.x, im));
                 }
@@ -237,32 +252,32 @@ constexpr int kBasisJC = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
-                                                    const double2* __restrict__ Q, int q, long long n_per,
-                                                    long long in_stride) {
+                                                    const double2* __restrict__ Q, RotView rv, long long n_per) {
     using C = cplx_t<T>;
     constexpr int JC = kBasisJC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sQ = reinterpret_cast<C*>(smem_raw);   // sQ[i * JC + jj] = Q[i][j0 + jj]
-    const int nch = (q + JC - 1) / JC;
+    const int qi = rv.qi, qo = rv.qo;
+    const int nch = (qo + JC - 1) / JC;
     const int slot = blockIdx.y / nch;
     const int j0 = (blockIdx.y - slot * nch) * JC;
-    const int ncol = min(JC, q - j0);
-    for (int t = threadIdx.x; t < q * JC; t += blockDim.x) {
+    const int ncol = min(JC, qo - j0);
+    for (int t = threadIdx.x; t < qi * JC; t += blockDim.x) {
         const int i = t / JC, jj = t - i * JC;
-        const double2 v = jj < ncol ? Q[(size_t)slot * q * q + (size_t)i * q + j0 + jj] : make_double2(0.0, 0.0);
+        const double2 v = jj < ncol ? Q[(size_t)slot * rv.qstride + (size_t)i * rv.ldq + j0 + jj]
+                                    : make_double2(0.0, 0.0);
         sQ[t] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
-    const C* ib = In + (size_t)slot * in_stride;
-    C* ob = Out + (size_t)slot * q * n_per;
+    C* ob = Out + (size_t)slot * rv.out_slot;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
          e += (long long)gridDim.x * blockDim.x) {
         T re[JC], im[JC];
 #pragma unroll
         for (int jj = 0; jj < JC; ++jj) re[jj] = im[jj] = T(0);
 #pragma unroll 2
-        for (int i = 0; i < q; ++i) {
-            const C v = ib[(size_t)i * n_per + e];
+        for (int i = 0; i < qi; ++i) {
+            const C v = In[rot_in(rv, slot, i, n_per) + e];
 #pragma unroll
             for (int jj = 0; jj < JC; ++jj) {
                 const C w = sQ[i * JC + jj];
@@ -276,20 +291,31 @@ __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict_
     }
 }
 
-// Basis rotation of nslot slots (q < kBasisQMax).
-// (In holds slot s at In + s * in_stride; in_stride <= 0 means q * n_per.)
+template <typename T>
+void launch_rotate(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* Out, const double2* Q,
+                   const RotView& rv, long long n_per) {
+    const unsigned gx = (unsigned)std::min<long long>((n_per + 127) / 128, 8192);
+    if (rv.qi <= kQMax && rv.qo <= kQMax) {
+        k_basis_reg<T><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
+    } else {
+        const int nch = (rv.qo + kBasisJC - 1) / kBasisJC;
+        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)rv.qi * kBasisJC * sizeof(cplx_t<T>), st>>>(
+            In, Out, Q, rv, n_per);
+    }
+}
+
+// Square rotation of nslot slots, Out[slot] = In[slot] Q[slot] (q x q row-major),
+// In slot s at In + s * in_stride (in_stride <= 0: q * n_per).
 template <typename T>
 void launch_basis(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* Out, const double2* Q, int q,
                   long long n_per, long long in_stride = 0) {
-    const unsigned gx = (unsigned)std::min<long long>((n_per + 127) / 128, 8192);
-    if (in_stride <= 0) in_stride = (long long)q * n_per;
-    if (q <= kQMax) {
-        k_basis_reg<T><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, q, n_per, in_stride);
-    } else {
-        const int nch = (q + kBasisJC - 1) / kBasisJC;
-        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)q * kBasisJC * sizeof(cplx_t<T>), st>>>(
-            In, Out, Q, q, n_per, in_stride);
-    }
+    RotView rv;
+    rv.in_slot = in_stride > 0 ? in_stride : (long long)q * n_per;
+    rv.segstride = 0;
+    rv.out_slot = (long long)q * n_per;
+    rv.qstride = (long long)q * q;
+    rv.qi = rv.qo = rv.seg = rv.ldq = q;
+    launch_rotate<T>(st, nslot, In, Out, Q, rv, n_per);
 }
 
 // Per vector v (blockIdx.y): partial sums of Re(u^H Ku), u^H (M u), |Ku|^2.

@@ -292,3 +292,26 @@ def test_tensor_gram_bands(B, uniform, method):
         got_cc, _, _ = B.Plan.from_problem(p, tensor_gram=0, **opt).solve_bands(ks, n_bands)
         assert freq_err(got_tc, want) < 1e-6
         assert np.max(np.abs(got_tc / got_cc - 1)) < 1e-6
+
+
+@pytest.mark.parametrize("rho_mix", [False, True])
+@pytest.mark.parametrize("prec,bar,opt", [(0, 1e-9, dict(tol_lin=1e-10, tol_eig=1e-11)),
+                                          (1, 1e-6, dict(tol_lin=1e-3, tol_eig=1e-5))])
+def test_lobpcg_matches_oracle(B, prec, bar, opt, rho_mix):
+    """BLOCH_LOBPCG (block [X, T R, P], Green preconditioner T, rank-revealing
+    Rayleigh-Ritz, no inner PCG) on one wave vector and on a short path through
+    Gamma, against the oracle; uniform and per-grain densities."""
+    import dataclasses
+    p = synth.small_polycrystal((12, 10, 8), 6, 19, n_bands=6)
+    if rho_mix:
+        p = dataclasses.replace(p, rho=np.random.default_rng(8).uniform(3000.0, 9000.0, p.G))
+    med = O.Medium.from_problem(p)
+    single = np.array([[0.37, 0.21, -0.29]]) * math.pi / 1e-3
+    path = np.array([[0.0, 0.0, 0.0], [0.15, 0.0, 0.0], [0.6, 0.3, 0.0]]) * math.pi / 1e-3
+    for ks in (single, path):
+        want = O.solve_bands(med, ks, 6, 1e-12, 1e-12, method="subspace").omega
+        plan = B.Plan.from_problem(p, precision=prec, method=B.LOBPCG, **opt)
+        got, stats, st = plan.solve_bands(ks, 6)
+        assert st == 0 and stats["k_unconverged"] == 0
+        assert freq_err(got, want) < bar
+        assert stats["cg_iterations"] == 0          # no inner solves
