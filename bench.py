@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rve128_g200")
-    ap.add_argument("--form", default="chosen", choices=["chosen", "chosen-subspace", "plain"])
+    ap.add_argument("--form", default="chosen", choices=["chosen", "chosen-subspace", "lobpcg", "plain"])
     ap.add_argument("--k-per-step", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -405,6 +405,10 @@ def run_ours(args, ws, rank, local):
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
                    max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph,
                    tensor_gram=args.tensor_gram)
+    elif args.form == "lobpcg":
+        # FP32 LOBPCG with the Green preconditioner (no inner PCG), FP64 residual check
+        opt = dict(precision=prec, method=bloch.LOBPCG, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
+                   max_outer=max(args.max_outer, 300), fft_variant=args.fft_variant, cuda_graph=args.cuda_graph)
     elif args.form == "chosen-subspace":
         # FP32 fields and PCG, subspace iteration with warm starts, FP64 residual check
         opt = dict(precision=prec, method=bloch.SUBSPACE, tol_lin=1e-3, tol_eig=1e-6, max_cg=500,
@@ -584,7 +588,7 @@ def run_ours(args, ws, rank, local):
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
                            "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"],
                            "tensor_gram": opt.get("tensor_gram", 0), "block": opt.get("block", 0),
-                           "method": "subspace" if opt["method"] else "lanczos",
+                           "method": {0: "lanczos", 1: "subspace", 2: "lobpcg"}[opt["method"]],
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},
                 "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
