@@ -276,10 +276,11 @@ static __global__ void k_gen_herm_eig(int n, const double2* __restrict__ K, cons
 }
 
 // Rank-revealing Rayleigh-Ritz of a pencil (K, M) whose M may be singular
-// (SVQB, Stathopoulos & Wu 2002): M = V D V^H (Jacobi); the directions with
-// D > eps * max(D) are kept, Z = V_keep D_keep^-1/2 (M-orthonormal); then
-// C = Z^H K Z = Y diag(lam) Y^H (Jacobi) and the Ritz vectors in the original
-// coordinates are Q = Z Y.  One CTA per pencil (blockIdx.x); K, M, Q n x n
+// (SVQB, Stathopoulos & Wu 2002): the basis is first scaled to unit M-norm,
+// s_i = M_ii^-1/2 (0 for a zero column), M' = S M S, K' = S K S; then
+// M' = V D V^H (Jacobi), the directions with D > eps * max(D) are kept,
+// Z = V_keep D_keep^-1/2 (M'-orthonormal), C = Z^H K' Z = Y diag(lam) Y^H
+// (Jacobi) and the Ritz vectors in the original coordinates are Q = S Z Y.  One CTA per pencil (blockIdx.x); K, M, Q n x n
 // row-major (double2) at b * n * n; M scaled by mscale.  Out: lam[b][0..r)
 // ascending, Q[b] columns 0..r (the rest zero), rank[b] = r.  Shared memory:
 // gen_eig_smem(n, blockDim.x).
@@ -297,16 +298,23 @@ static __global__ void k_svqb_eig(int n, const double2* __restrict__ K, const do
     int* perm = reinterpret_cast<int*>(red + 2 * blockDim.x);
     __shared__ int r_sh;
     __shared__ double dmax_sh;
+    __shared__ double sc[64];   // s_i (n <= 64)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = blockIdx.x;
     const double2* Kb = K + (size_t)b * n * n;
     const double2* Mb = M + (size_t)b * n * n;
+    for (int i = tid; i < n; i += nt) {
+        const double d = mscale * Mb[i * n + i].x;
+        sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    }
+    __syncthreads();
     for (int e = tid; e < n * n; e += nt) {
         const int i = e / n, j = e % n;
+        const double sij = sc[i] * sc[j];
         const double2 m1 = Mb[i * n + j], m2 = Mb[j * n + i];
-        A[e] = make_double2(0.5 * mscale * (m1.x + m2.x), 0.5 * mscale * (m1.y - m2.y));
+        A[e] = make_double2(0.5 * sij * mscale * (m1.x + m2.x), 0.5 * sij * mscale * (m1.y - m2.y));
         const double2 k1 = Kb[i * n + j], k2 = Kb[j * n + i];
-        Kh[e] = make_double2(0.5 * (k1.x + k2.x), 0.5 * (k1.y - k2.y));
+        Kh[e] = make_double2(0.5 * sij * (k1.x + k2.x), 0.5 * sij * (k1.y - k2.y));
     }
     __syncthreads();
     jacobi_herm(n, A, Vm, w, red, rot);
@@ -360,7 +368,7 @@ static __global__ void k_svqb_eig(int n, const double2* __restrict__ K, const do
         double2 acc = make_double2(0.0, 0.0);
         if (c < r)
             for (int k = 0; k < r; ++k) acc = zadd(acc, zmul(Y[i * n + k], Vm[k * r + perm[c]]));
-        Qb[e] = acc;
+        Qb[e] = make_double2(sc[i] * acc.x, sc[i] * acc.y);
     }
     for (int c = tid; c < n; c += nt) lam[(size_t)b * n + c] = c < r ? w[perm[c]] : 0.0;
     if (tid == 0) rank[b] = r;
