@@ -414,6 +414,7 @@ struct Subspace {
         std::vector<double> lam, lam_prev, unorm2;
         double err1 = INFINITY, err2 = INFINITY, err2_prev = INFINITY;
         int stall = 0;
+        double err2_best = INFINITY;   // LOBPCG: best FP32 residual so far
         bool has_prev = false;
     };
     std::vector<Slot> slots;
@@ -879,9 +880,23 @@ struct Subspace {
                     // FP32 residuals drive the sweeps until the stop test passes in
                     // FP32 (or err2 stalls at the FP32 noise floor); the FP64
                     // residual then verifies, and drives further sweeps if needed.
-                    if (sl.err2 > 0.9 * sl.err2_prev) sl.stall += 1;
-                    else sl.stall = 0;
-                    if (test || (sl.sweeps >= 4 && sl.stall >= 2)) sl.phase = 1;
+                    // (LOBPCG's FP32 residual fluctuates at that floor rather than
+                    // settling: it counts sweeps without a 10 % gain on its best)
+                    int need = 2;
+                    if (lob) {
+                        if (sl.err2 < 0.9 * sl.err2_best) {
+                            sl.err2_best = sl.err2;
+                            sl.stall = 0;
+                        } else {
+                            sl.stall += 1;
+                        }
+                        need = 3;
+                    } else if (sl.err2 > 0.9 * sl.err2_prev) {
+                        sl.stall += 1;
+                    } else {
+                        sl.stall = 0;
+                    }
+                    if (test || (sl.sweeps >= 4 && sl.stall >= need)) sl.phase = 1;
                     if (sl.sweeps >= max_outer) done.push_back(i);
                 } else if (test || sl.sweeps >= max_outer) {
                     done.push_back(i);
