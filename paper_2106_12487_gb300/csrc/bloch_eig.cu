@@ -650,6 +650,16 @@ struct Subspace {
                 if ((s = set_k<double>(pl, nw, kv.data())) != BLOCH_OK) return s;
                 launch_K<double>(pl, nw, U64, KU64, 1.0);
                 if (!uniform) launch_M<double>(pl, nw, U64, MU64, 1.0);
+                if (lob) {
+                    // LOBPCG's next Rayleigh-Ritz reads A X (and M X) of the block:
+                    // the fresh FP64 images, rounded, replace the previous ones
+                    ++pl->launches;
+                    k_convert<double, T><<<1024, 256, 0, pl->stream>>>(KU64, vec(KU, i), ne);
+                    if (!uniform) {
+                        ++pl->launches;
+                        k_convert<double, T><<<1024, 256, 0, pl->stream>>>(MU64, vec(MU, i), ne);
+                    }
+                }
                 if ((s = residual_part<double>(i, 1, 0, nw, U64, KU64, uniform ? nullptr : MU64)) != BLOCH_OK) return s;
                 if (nw < q) {
                     if ((s = set_k<T>(pl, q - nw, kv.data())) != BLOCH_OK) return s;
