@@ -842,15 +842,12 @@ struct Subspace {
         launch_rotate<T>(pl->stream, nact, U, Ub, d_C3, rx, n3);
         launch_rotate<T>(pl->stream, nact, Wb, P2, d_C3 + q * q3, rp, n3);
         launch_rotate<T>(pl->stream, nact, AWb, AP2, d_C3 + q * q3, rp, n3);
-        if (!uniform) {
-            ++pl->launches;
-            launch_rotate<T>(pl->stream, nact, MWb, MP2, d_C3 + q * q3, rp, n3);
-        }
         const size_t bytes = sizeof(C) * (size_t)nact * q * n3;
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(U, Ub, bytes, cudaMemcpyDeviceToDevice, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(Pb, P2, bytes, cudaMemcpyDeviceToDevice, pl->stream));
         BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(APb, AP2, bytes, cudaMemcpyDeviceToDevice, pl->stream));
-        if (!uniform) BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(MPb, MP2, bytes, cudaMemcpyDeviceToDevice, pl->stream));
+        // M P afresh (a carried M P drifts in FP32 and spoils the next projection's metric)
+        if (!uniform) launch_M<T>(pl, nact * q, Pb, MPb, T(1));
         for (int i = 0; i < nact; ++i) slots[i].sweeps += 1;
         BLOCH_CUDA_CHECK_RET(cudaGetLastError());
         return BLOCH_OK;
