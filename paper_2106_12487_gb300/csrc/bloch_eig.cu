@@ -822,9 +822,8 @@ struct Subspace {
                                                                           d_gpart, q, segs);
         k_gram_final<<<dim3((2 * np3 + 127) / 128, nact), 128, 0, pl->stream>>>(d_gpart, gblk, np3, nact, d_G);
         // rank-revealing Rayleigh-Ritz: directions of [X, W, P] whose M-norm falls
-        // below what the Gram matrices resolve are dropped (FP32 blocks: products
-        // summed in FP32 per thread over up to ~1e4 elements, ~1e-5 relative)
-        const double eps = std::is_same<T, float>::value ? 1e-4 : 1e-13;
+        // below the field precision's resolution are dropped
+        const double eps = std::is_same<T, float>::value ? 1e-6 : 1e-13;
         k_svqb_eig<<<nact, kEigThreads, gen_eig_smem(q3, kEigThreads), pl->stream>>>(
             q3, d_G, d_G + (size_t)nact * np3, uniform ? rho_s : 1.0, eps, d_lam3, d_C3, d_status);
         eig_pending = 0;
