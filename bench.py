@@ -69,6 +69,9 @@ def parse():
                     help="skip the extra traced (untimed) step that reports the solver's phase breakdown")
     ap.add_argument("--tensor-gram", type=int, default=0, choices=[0, 1],
                     help="1: Algorithm 1 projections of FP32 blocks on the tensor cores (tcgen05)")
+    ap.add_argument("--ncv", type=int, default=0, help="Lanczos basis size of the chosen form (0: max(2n+1, 20))")
+    ap.add_argument("--hybrid-tol", type=float, default=0.0,
+                    help="Lanczos-stage hand-over tolerance of the chosen form (0: max(1e-5, 10 tol_eig))")
     ap.add_argument("--cuda-graph", type=int, default=1, choices=[0, 1],
                     help="1: PCG loop as one CUDA graph with a device-side while node; 0: host-driven loop "
                          "(same kernels; used for per-launch profiling)")
@@ -404,7 +407,7 @@ def run_ours(args, ws, rank, local):
         # so two guard vectors suffice (12 was fastest of 12-18 at equal frequencies)
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
                    max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph,
-                   tensor_gram=args.tensor_gram)
+                   tensor_gram=args.tensor_gram, ncv=args.ncv, hybrid_tol=args.hybrid_tol)
     elif args.form == "lobpcg":
         # FP32 LOBPCG with the Green preconditioner (no inner PCG), FP64 residual check
         opt = dict(precision=prec, method=bloch.LOBPCG, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
@@ -588,6 +591,7 @@ def run_ours(args, ws, rank, local):
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
                            "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"],
                            "tensor_gram": opt.get("tensor_gram", 0), "block": opt.get("block", 0),
+                           "ncv": opt.get("ncv", 0), "hybrid_tol": opt.get("hybrid_tol", 0.0),
                            "method": {0: "lanczos", 1: "subspace", 2: "lobpcg"}[opt["method"]],
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},
