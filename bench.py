@@ -65,6 +65,10 @@ def parse():
                          "preconditioner first (untimed, reported under 'precond') and solve with it")
     ap.add_argument("--lp-cells", type=int, default=16, help="training cells (64^3 Zener family) for --precond learned")
     ap.add_argument("--lp-steps", type=int, default=500, help="Adam steps for --precond learned")
+    ap.add_argument("--learned-config4", action="store_true",
+                    help="the learned-preconditioner study at its configured scale: train on --lp-cells seeded 64^3 "
+                         "Zener cells (400 for the study), then on a 128^3, 300-grain test cell report PCG iterations "
+                         "at equal tolerance and chosen-form eigenpairs/s with the Green and the learned operator")
     ap.add_argument("--no-trace", action="store_true",
                     help="skip the extra traced (untimed) step that reports the solver's phase breakdown")
     ap.add_argument("--tensor-gram", type=int, default=0, choices=[0, 1],
@@ -388,6 +392,66 @@ def train_learned(args):
                 "loss": [L0, L1], "train_s": time.perf_counter() - t0}
 
 
+def learned_config4(args):
+    """Learned preconditioner at the study's scale (one JSON line).  Training
+    data: per cell, two wave vectors of its path and two seeded right-hand
+    sides, 12 recorded PCG iterates each.  Test cell: 128^3, 300 Voronoi grains
+    (seed 4), Haar orientations (seed 104), cubic with Zener ratio 2.5 (the
+    middle of the training range)."""
+    import torch
+    from paper_2106_12487_gb300 import bloch, synth
+    lp, info = train_learned(args)
+    C11, C12 = synth.CU_CUBIC["C11"], synth.CU_CUBIC["C12"]
+    C6 = synth.cubic_voigt(C11, C12, 2.5 * (C11 - C12) / 2)
+    p = synth.polycrystal("config4_test", (128, 128, 128), 300, 4, 104, C6, synth.CU_CUBIC["rho"],
+                          synth.kpath("GXMGR", 64), 10, 1e-10)
+    out = {"study": "learned preconditioner, train 64^3 Zener cells, test 128^3 / 300 grains", "train": info}
+    # PCG iterations at equal tolerance, 4 wave vectors x 4 right-hand sides
+    kidx = [5, 20, 36, 50]
+    iters = {}
+    for name, use in (("green", False), ("learned", True)):
+        plan = bloch.Plan.from_problem(p, precision=bloch.FP32, cuda_graph=1)
+        if use:
+            bloch.set_preconditioner(plan, lp)
+        for tol in (1e-2, 1e-5):
+            tot = []
+            for j, ki in enumerate(kidx):
+                b = torch.from_numpy(synth.random_field(p.grid, 300 + j, batch=4) * 1e18).to(
+                    device="cuda", dtype=torch.complex64)
+                x = torch.zeros_like(b)
+                it, rel, _ = plan.pcg(np.repeat(p.k_list[ki:ki + 1], 4, 0), b, x, tol, 3000, allow_nonconv=True)
+                tot.extend(int(v) for v in it)
+            iters.setdefault(name, {})[str(tol)] = {"mean": float(np.mean(tot)), "all": tot}
+        plan.close()
+    out["pcg_iterations"] = iters
+    # chosen-form band solve of 8 wave vectors (after one warm-up batch), both operators
+    opt = dict(precision=bloch.FP32, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500,
+               block=p.n_bands + 2, max_outer=args.max_outer)
+    stream = torch.cuda.current_stream()
+    om_ref = None
+    for name, use in (("green", False), ("learned", True)):
+        plan = bloch.Plan.from_problem(p, **opt)
+        if use:
+            bloch.set_preconditioner(plan, lp)
+        plan.solve_bands(p.k_list[0:8], p.n_bands, allow_nonconv=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        om, st, status = plan.solve_bands(p.k_list[8:16], p.n_bands, allow_nonconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1000.0
+        out.setdefault("band_solve", {})[name] = {"eigenpairs_per_s": 8 * p.n_bands / dt, "status": int(status),
+                                                  "cg_iterations": st["cg_iterations"]}
+        if om_ref is None:
+            om_ref = om
+        else:
+            out["band_solve"]["max_rel_freq_diff"] = float(np.max(np.abs(om / om_ref - 1.0)))
+        plan.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2106_12487_gb300 import bloch, synth
@@ -395,6 +459,9 @@ def run_ours(args, ws, rank, local):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
+    if args.learned_config4:
+        learned_config4(args)
+        return
     p = synth.workload(args.workload)
     prec = bloch.FP64 if args.form == "plain" else bloch.FP32
     if args.form == "chosen":
