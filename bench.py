@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--ncv", type=int, default=0, help="Lanczos basis size of the chosen form (0: max(2n+1, 20))")
     ap.add_argument("--hybrid-tol", type=float, default=0.0,
                     help="Lanczos-stage hand-over tolerance of the chosen form (0: max(1e-5, 10 tol_eig))")
+    ap.add_argument("--refine-arith", type=int, default=1, choices=[0, 1],
+                    help="arithmetic of the chosen form's FP64 check: 0 IEEE FP64, 1 float-float operator "
+                         "applies with FP64 sums")
     ap.add_argument("--cuda-graph", type=int, default=1, choices=[0, 1],
                     help="1: PCG loop as one CUDA graph with a device-side while node; 0: host-driven loop "
                          "(same kernels; used for per-launch profiling)")
@@ -268,7 +271,7 @@ def gpu_band_same_config(name, omega_ref):
     out = {}
     forms = {"fp64_plain": dict(precision=bloch.FP64, method=bloch.LANCZOS, tol_lin=1e-10, tol_eig=1e-10),
              "chosen": dict(precision=bloch.FP32, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5,
-                            block=p.n_bands + 2, max_cg=500)}
+                            block=p.n_bands + 2, max_cg=500, refine_arith=1)}
     stream = torch.cuda.current_stream()
     for form, opt in forms.items():
         plan = bloch.Plan.from_problem(p, **opt)
@@ -426,7 +429,7 @@ def learned_config4(args):
     out["pcg_iterations"] = iters
     # chosen-form band solve of 8 wave vectors (after one warm-up batch), both operators
     opt = dict(precision=bloch.FP32, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500,
-               block=p.n_bands + 2, max_outer=args.max_outer)
+               block=p.n_bands + 2, max_outer=args.max_outer, refine_arith=args.refine_arith)
     stream = torch.cuda.current_stream()
     om_ref = None
     for name, use in (("green", False), ("learned", True)):
@@ -474,7 +477,8 @@ def run_ours(args, ws, rank, local):
         # so two guard vectors suffice (12 was fastest of 12-18 at equal frequencies)
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
                    max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph,
-                   tensor_gram=args.tensor_gram, ncv=args.ncv, hybrid_tol=args.hybrid_tol)
+                   tensor_gram=args.tensor_gram, ncv=args.ncv, hybrid_tol=args.hybrid_tol,
+                   refine_arith=args.refine_arith)
     elif args.form == "lobpcg":
         # FP32 LOBPCG with the Green preconditioner (no inner PCG), FP64 residual check
         opt = dict(precision=prec, method=bloch.LOBPCG, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
@@ -659,6 +663,7 @@ def run_ours(args, ws, rank, local):
                            "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"],
                            "tensor_gram": opt.get("tensor_gram", 0), "block": opt.get("block", 0),
                            "ncv": opt.get("ncv", 0), "hybrid_tol": opt.get("hybrid_tol", 0.0),
+                           "refine_arith": opt.get("refine_arith", 0),
                            "method": {0: "lanczos", 1: "subspace", 2: "lobpcg"}[opt["method"]],
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
                                  % (3 * plan.V * 8 / 1e6)},

@@ -56,7 +56,10 @@ typedef enum {
                                 a block or basis above the solver's limits      */
 } bloch_status;
 
-typedef enum { BLOCH_FP64 = 0, BLOCH_FP32 = 1 } bloch_precision;
+/* BLOCH_FF: double2 buffers, arithmetic in float-float (pairs hi + lo of floats,
+   a 48-bit significand, about 4e-15 relative per operation) on the FP32 pipes;
+   accepted by bloch_apply_K. */
+typedef enum { BLOCH_FP64 = 0, BLOCH_FP32 = 1, BLOCH_FF = 2 } bloch_precision;
 typedef enum { BLOCH_LANCZOS = 0, BLOCH_SUBSPACE = 1, BLOCH_LOBPCG = 2 } bloch_method;
 
 typedef struct bloch_plan bloch_plan;   /* opaque; owned by the library */
@@ -117,6 +120,12 @@ typedef struct {
                             estimates reach this relative accuracy and hands its block to
                             the Algorithm 1 refinement, which alone decides convergence
                             (tol_eig).  0 = max(1e-5, 10 tol_eig).  Default 0.          */
+    int32_t refine_arith; /* arithmetic of the FP64 check of the FP32 form (the operator
+                            applies to the wanted vectors): 0 = IEEE FP64; 1 = float-float
+                            operator applies (BLOCH_FF) whose results are summed in FP64
+                            into the Rayleigh quotients and residuals.  GB300 runs FP64 at
+                            1/74 of its FP32 rate, so 1 makes the check several times
+                            cheaper at ~4e-15 relative accuracy.  Default 0.            */
 } bloch_options;
 
 /* Outcome of bloch_plan_autotune. */
@@ -177,7 +186,9 @@ void bloch_plan_destroy(bloch_plan* plan);
 /*
  * Stiffness operator, Eq. (hatA), on nb Fourier-space vectors at once.
  *   k          host, nb x 3 wave vectors (rad/m), one per vector
- *   precision  BLOCH_FP32 (u, Ku are float2) or BLOCH_FP64 (double2)
+ *   precision  BLOCH_FP32 (u, Ku are float2), BLOCH_FP64 (double2) or BLOCH_FF
+ *              (double2 buffers, float-float arithmetic; u is rounded to
+ *              float-float on entry)
  *   u          device, nb x 3 x V complex, Fourier basis; not modified
  *   Ku         device, nb x 3 x V complex; may not alias u
  * Enqueued on the plan's stream (asynchronous).  Scratch: 6 x V complex per

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libbloch.so")
 BLOCH_OK = 0
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV_CG", 5: "ENOTCONV_EIG",
           6: "ENONFINITE", 7: "EUNSUPPORTED"}
-FP64, FP32 = 0, 1
+FP64, FP32, FF = 0, 1, 2
 LANCZOS, SUBSPACE, LOBPCG = 0, 1, 2
 
 EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", "bloch_apply_K",
@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("block", ctypes.c_int32), ("k_batch", ctypes.c_int32), ("ncv", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("cuda_graph", ctypes.c_int32), ("fft_variant", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("tile_pmax", ctypes.c_int32), ("tensor_gram", ctypes.c_int32),
-                ("hybrid_tol", ctypes.c_double)]
+                ("hybrid_tol", ctypes.c_double), ("refine_arith", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -162,7 +162,7 @@ def default_options(**kw) -> Options:
 
 def _tensor_ptr(t, precision: int, n_expected: int):
     import torch
-    want = torch.complex64 if precision == FP32 else torch.complex128
+    want = torch.complex64 if precision == FP32 else torch.complex128   # FP64 and FF use double2
     if t.dtype != want:
         raise TypeError(f"expected {want}, got {t.dtype}")
     if not t.is_cuda or not t.is_contiguous():

@@ -502,6 +502,7 @@ struct Subspace {
             if ((s = alloc(&U64, (size_t)q * n3)) || (s = alloc(&KU64, (size_t)q * n3))) return s;
             if (!uniform && (s = alloc(&MU64, (size_t)q * n3))) return s;
             if ((s = ensure_ws<double>(pl, q)) != BLOCH_OK) return s;
+            if (pl->opt.refine_arith == 1 && (s = ensure_ws<dfloat>(pl, q)) != BLOCH_OK) return s;
         }
         if ((s = ensure_cg<T>(pl, B * q)) != BLOCH_OK) return s;
         slots.assign(B, Slot());
@@ -642,14 +643,27 @@ struct Subspace {
                 TraceScope tr(pl, TR_RES64);
                 const int nw = std::max(1, std::min(q, slots[i].n_eff));
                 const size_t ne = (size_t)nw * n3;
-                ++pl->launches;
-                k_convert<T, double><<<1024, 256, 0, pl->stream>>>(vec(U, i), U64, ne);
                 std::vector<double> kv((size_t)q * 3);
                 for (int v = 0; v < q; ++v)
                     for (int a = 0; a < 3; ++a) kv[(size_t)v * 3 + a] = slots[i].k[a];
-                if ((s = set_k<double>(pl, nw, kv.data())) != BLOCH_OK) return s;
-                launch_K<double>(pl, nw, U64, KU64, 1.0);
-                if (!uniform) launch_M<double>(pl, nw, U64, MU64, 1.0);
+                if (pl->opt.refine_arith == 1) {
+                    // operator applies in float-float (the U64 / KU64 / MU64 buffers hold
+                    // float-float values first, FP64 ones after the in-place conversion)
+                    pl->launches += 3 + (uniform ? 0 : 1);
+                    k_convert<T, dfloat><<<1024, 256, 0, pl->stream>>>(vec(U, i), (dfloat2*)U64, ne);
+                    if ((s = set_k<dfloat>(pl, nw, kv.data())) != BLOCH_OK) return s;
+                    launch_K<dfloat>(pl, nw, (const dfloat2*)U64, (dfloat2*)KU64, dfloat(1.0f));
+                    if (!uniform) launch_M<dfloat>(pl, nw, (const dfloat2*)U64, (dfloat2*)MU64, dfloat(1.0f));
+                    k_convert_inplace<dfloat, double><<<1024, 256, 0, pl->stream>>>(KU64, ne);
+                    if (!uniform) k_convert_inplace<dfloat, double><<<1024, 256, 0, pl->stream>>>(MU64, ne);
+                    k_convert<T, double><<<1024, 256, 0, pl->stream>>>(vec(U, i), U64, ne);
+                } else {
+                    ++pl->launches;
+                    k_convert<T, double><<<1024, 256, 0, pl->stream>>>(vec(U, i), U64, ne);
+                    if ((s = set_k<double>(pl, nw, kv.data())) != BLOCH_OK) return s;
+                    launch_K<double>(pl, nw, U64, KU64, 1.0);
+                    if (!uniform) launch_M<double>(pl, nw, U64, MU64, 1.0);
+                }
                 if (lob) {
                     // LOBPCG's next Rayleigh-Ritz reads A X (and M X) of the block:
                     // the fresh FP64 images, rounded, replace the previous ones

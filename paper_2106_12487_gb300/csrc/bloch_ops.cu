@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "eig_kernels.cuh"
 #include "internal.h"
 
 namespace bloch {
@@ -28,23 +29,30 @@ bloch_status set_cuda_error(cudaError_t e, const char* what) {
 
 template <> Workspace<float>& ws_of<float>(bloch_plan* pl) { return pl->ws_f; }
 template <> Workspace<double>& ws_of<double>(bloch_plan* pl) { return pl->ws_d; }
+template <> Workspace<dfloat>& ws_of<dfloat>(bloch_plan* pl) { return pl->ws_x; }
+// float-float runs the FP64 radix schedule and tiles (same 16-byte complex)
+template <> const Geo& geo_of<dfloat>(const bloch_plan* pl) { return pl->geo_d; }
 template <> const Geo& geo_of<float>(const bloch_plan* pl) { return pl->geo_f; }
 template <> const Geo& geo_of<double>(const bloch_plan* pl) { return pl->geo_d; }
 template <typename T> static const TileCfg& tile_of(const bloch_plan* pl);
 template <> const TileCfg& tile_of<float>(const bloch_plan* pl) { return pl->tile_f; }
 template <> const TileCfg& tile_of<double>(const bloch_plan* pl) { return pl->tile_d; }
+template <> const TileCfg& tile_of<dfloat>(const bloch_plan* pl) { return pl->tile_d; }
 template <typename T> static const cplx_t<T>* tw_of(const bloch_plan* pl, int axis);
 template <> const float2* tw_of<float>(const bloch_plan* pl, int axis) { return pl->d_twf[axis]; }
 template <> const double2* tw_of<double>(const bloch_plan* pl, int axis) { return pl->d_twd[axis]; }
+template <> const dfloat2* tw_of<dfloat>(const bloch_plan* pl, int axis) { return pl->d_twx[axis]; }
 template <typename T> static const T* ctab_of(const bloch_plan* pl);
 template <> const float* ctab_of<float>(const bloch_plan* pl) { return pl->d_Cf; }
 template <> const double* ctab_of<double>(const bloch_plan* pl) { return pl->d_Cd; }
+template <> const dfloat* ctab_of<dfloat>(const bloch_plan* pl) { return pl->d_Cx; }
 template <typename T> static const T* cpk_of(const bloch_plan* pl);
 template <> const float* cpk_of<float>(const bloch_plan* pl) { return pl->d_Cpf; }
 template <> const double* cpk_of<double>(const bloch_plan* pl) { return pl->d_Cpd; }
 template <typename T> static const T* rtab_of(const bloch_plan* pl);
 template <> const float* rtab_of<float>(const bloch_plan* pl) { return pl->d_rf; }
 template <> const double* rtab_of<double>(const bloch_plan* pl) { return pl->d_rd; }
+template <> const dfloat* rtab_of<dfloat>(const bloch_plan* pl) { return pl->d_rx; }
 
 // ------------------------------------------------------------ host helpers
 static bool fast_axis(int N);
@@ -473,6 +481,14 @@ void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out
     k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5, out_scale);
 }
 
+// Float-float operator: the shared-memory passes in every configuration
+template <>
+int launch_K<dfloat>(bloch_plan* pl, int nb, const dfloat2* u, dfloat2* out, dfloat out_scale, const dfloat2*,
+                     double2*) {
+    launch_K_generic<dfloat>(pl, nb, u, out, out_scale);
+    return 0;
+}
+
 // Fourier-space stress of nb systems whose q tables are set, into the
 // operator workspace E (6 components per system, Voigt order xx yy zz yz xz
 // xy): S = F{ C~(x) : F^-1(sym q (x) u) }, i.e. the K-apply's passes 1-4 and a
@@ -520,7 +536,8 @@ void launch_M(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_
     if (pl->uniform_rho) {
         const int blocks = (int)std::min<long long>(4096, (n + 255) / 256);
         ++pl->launches;
-        k_scale<T><<<blocks, 256, 0, pl->stream>>>(u, out, T(pl->rho_uniform_scaled * out_scale), (size_t)n);
+        k_scale<T><<<blocks, 256, 0, pl->stream>>>(
+            u, out, T(pl->rho_uniform_scaled * static_cast<double>(out_scale)), (size_t)n);
         return;
     }
     Workspace<T>& w = ws_of<T>(pl);
@@ -822,6 +839,9 @@ bloch_status pcg_enqueue(bloch_plan* pl, int nb, const cplx_t<T>* b, cplx_t<T>* 
 INST(float)
 INST(double)
 #undef INST
+template bloch_status ensure_ws<dfloat>(bloch_plan*, int);
+template bloch_status set_k<dfloat>(bloch_plan*, int, const double*);
+template void launch_M<dfloat>(bloch_plan*, int, const dfloat2*, dfloat2*, dfloat);
 
 }  // namespace bloch
 
@@ -882,6 +902,7 @@ static void free_ws_all(bloch_plan* pl) {
     };
     fr(pl->ws_f);
     fr(pl->ws_d);
+    fr(pl->ws_x);
 }
 
 void bloch_plan_destroy(bloch_plan* pl) {
@@ -904,7 +925,10 @@ void bloch_plan_destroy(bloch_plan* pl) {
     for (int a = 0; a < 3; ++a) {
         cudaFree(pl->d_twf[a]);
         cudaFree(pl->d_twd[a]);
+        cudaFree(pl->d_twx[a]);
     }
+    cudaFree(pl->d_Cx);
+    cudaFree(pl->d_rx);
     cudaFree(pl->d_nactive);
     cudaFreeHost(pl->h_nactive);
     cudaFree(pl->d_ztab);
@@ -991,6 +1015,10 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     if (pl->opt.fft_variant < 0 || pl->opt.fft_variant > 2) {
         delete pl;
         return set_error(BLOCH_EINVAL, "fft_variant must be 0, 1 or 2");
+    }
+    if (pl->opt.refine_arith != 0 && pl->opt.refine_arith != 1) {
+        delete pl;
+        return set_error(BLOCH_EINVAL, "refine_arith must be 0 or 1");
     }
     pl->stream = (cudaStream_t)cuda_stream;
     std::memset(&pl->last_stats, 0, sizeof(pl->last_stats));
@@ -1091,6 +1119,13 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         CK(cudaMemcpy(pl->d_Cf, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(pl->d_rd, rd.data(), sizeof(double) * rd.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(pl->d_rf, rf.data(), sizeof(float) * rf.size(), cudaMemcpyHostToDevice));
+        std::vector<dfloat> cx(cd.size()), rx(rd.size());
+        for (size_t i = 0; i < cd.size(); ++i) cx[i] = dfloat(cd[i]);
+        for (size_t i = 0; i < rd.size(); ++i) rx[i] = dfloat(rd[i]);
+        CK(dmalloc(&pl->d_Cx, cx.size(), acc));
+        CK(dmalloc(&pl->d_rx, rx.size(), acc));
+        CK(cudaMemcpy(pl->d_Cx, cx.data(), sizeof(dfloat) * cx.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(pl->d_rx, rx.data(), sizeof(dfloat) * rx.size(), cudaMemcpyHostToDevice));
     }
     for (int a = 0; a < 3; ++a) {
         const int N = grid[a];
@@ -1105,6 +1140,15 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         CK(dmalloc(&pl->d_twf[a], (size_t)N, acc));
         CK(cudaMemcpy(pl->d_twd[a], td.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(pl->d_twf[a], tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+        std::vector<dfloat2> tx(N);
+        for (int t = 0; t < N; ++t) {   // hi/lo split of the twiddle, from the extended-precision angle
+            const long double ang = -2.0L * 3.141592653589793238462643383279502884L * t / N;
+            const long double c = std::cos(ang), sn = std::sin(ang);
+            const float ch = (float)c, sh = (float)sn;
+            tx[t] = dfloat2{dfloat(ch, (float)(c - (long double)ch)), dfloat(sh, (float)(sn - (long double)sh))};
+        }
+        CK(dmalloc(&pl->d_twx[a], (size_t)N, acc));
+        CK(cudaMemcpy(pl->d_twx[a], tx.data(), sizeof(dfloat2) * N, cudaMemcpyHostToDevice));
     }
     CK(dmalloc(&pl->d_nactive, 1, acc));
     CK(dmalloc(&pl->d_iter, 1, acc));
@@ -1112,6 +1156,7 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     CK(cudaMallocHost((void**)&pl->h_nactive, sizeof(int)));
     CK(set_smem_attrs<float>());
     CK(set_smem_attrs<double>());
+    CK(set_smem_attrs<dfloat>());
     set_fast_attrs<float>();
     set_fast_attrs<double>();
     pl->fast = pl->opt.fft_variant == 0;
@@ -1137,23 +1182,50 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     return BLOCH_OK;
 }
 
-static bloch_status check_common(bloch_plan* pl, int nb, int precision) {
+static bloch_status check_common(bloch_plan* pl, int nb, int precision, bool ff_ok = false) {
     if (!pl) return set_error(BLOCH_EINVAL, "plan is NULL");
     if (nb < 1 || nb > 65535 / 6) return set_error(BLOCH_EINVAL, "nb must be in [1, 10922]");
-    if (precision != BLOCH_FP32 && precision != BLOCH_FP64)
-        return set_error(BLOCH_EINVAL, "precision must be BLOCH_FP32 or BLOCH_FP64");
+    if (precision != BLOCH_FP32 && precision != BLOCH_FP64 && !(ff_ok && precision == BLOCH_FF))
+        return set_error(BLOCH_EINVAL, ff_ok ? "precision must be BLOCH_FP32, BLOCH_FP64 or BLOCH_FF"
+                                             : "precision must be BLOCH_FP32 or BLOCH_FP64");
+    return BLOCH_OK;
+}
+
+// scratch of nb float-float three-component vectors (the rounded input of a BLOCH_FF apply)
+static bloch_status ensure_cg_ff(bloch_plan* pl, int nb) {
+    Workspace<dfloat>& w = pl->ws_x;
+    bloch_status st = ensure_ws<dfloat>(pl, nb);
+    if (st != BLOCH_OK) return st;
+    if (nb <= w.cg_cap) return BLOCH_OK;
+    cudaStreamSynchronize(pl->stream);
+    if (w.r) pl->device_bytes -= (size_t)w.cg_cap * 3 * pl->V * sizeof(dfloat2);
+    cudaFree(w.r);
+    w.r = nullptr;
+    w.cg_cap = 0;
+    BLOCH_CUDA_CHECK_RET(dmalloc(&w.r, (size_t)3 * pl->V * nb, &pl->device_bytes));
+    w.cg_cap = nb;
     return BLOCH_OK;
 }
 
 bloch_status bloch_apply_K(bloch_plan* pl, int32_t nb, const double* k, int32_t precision, const void* u,
                            void* Ku) {
-    bloch_status st = check_common(pl, nb, precision);
+    bloch_status st = check_common(pl, nb, precision, true);
     if (st != BLOCH_OK) return st;
     if (!k || !u || !Ku) return set_error(BLOCH_EINVAL, "NULL argument");
     if (u == Ku) return set_error(BLOCH_EINVAL, "Ku may not alias u");
     if (precision == BLOCH_FP32) {
         if ((st = set_k<float>(pl, nb, k)) != BLOCH_OK) return st;
         launch_K<float>(pl, nb, (const float2*)u, (float2*)Ku, (float)pl->Kscale);
+    } else if (precision == BLOCH_FF) {
+        // double2 in, float-float passes (input rounded into a float-float copy), double2 out
+        Workspace<dfloat>& w = ws_of<dfloat>(pl);
+        if ((st = ensure_cg_ff(pl, nb)) != BLOCH_OK) return st;
+        if ((st = set_k<dfloat>(pl, nb, k)) != BLOCH_OK) return st;
+        const size_t n = (size_t)nb * 3 * pl->V;
+        pl->launches += 2;
+        k_convert<double, dfloat><<<2048, 256, 0, pl->stream>>>((const double2*)u, w.r, n);
+        launch_K<dfloat>(pl, nb, w.r, (dfloat2*)Ku, dfloat(pl->Kscale));
+        k_convert_inplace<dfloat, double><<<2048, 256, 0, pl->stream>>>(Ku, n);
     } else {
         if ((st = set_k<double>(pl, nb, k)) != BLOCH_OK) return st;
         launch_K<double>(pl, nb, (const double2*)u, (double2*)Ku, pl->Kscale);

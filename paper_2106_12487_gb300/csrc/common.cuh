@@ -4,14 +4,77 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Float-float ("double-float") real: the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2, a 48-bit significand evaluated on the FP32
+// pipes.  Sum and product are formed from the error-free transformations --
+// Knuth's two-sum (s + e = a + b exactly) and, for the product, the residual
+// of a*b recovered with one fused multiply-add -- then renormalised.  The
+// _rn intrinsics keep every step individually rounded (no contraction).
+struct dfloat {
+    float hi, lo;
+    __host__ __device__ dfloat() : hi(0.f), lo(0.f) {}
+    __host__ __device__ dfloat(float a) : hi(a), lo(0.f) {}
+    __host__ __device__ dfloat(int a) : hi((float)a), lo(0.f) {}
+    __host__ __device__ dfloat(double a) : hi((float)a), lo((float)(a - (double)(float)a)) {}
+    __host__ __device__ dfloat(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return dfloat(s, e);
+}
+__device__ __forceinline__ dfloat df_quick_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+    dfloat s = df_two_sum(a.hi, b.hi);
+    const dfloat t = df_two_sum(a.lo, b.lo);
+    s = df_quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_quick_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_quick_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
+__device__ __forceinline__ bool operator==(dfloat a, dfloat b) { return a.hi == b.hi && a.lo == b.lo; }
+#endif
+
+struct dfloat2 {
+    dfloat x, y;
+};
+
+#ifdef __CUDACC__
+// read-only cached load of a real table entry of any of the field types
+__device__ __forceinline__ float ldg_t(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldg_t(const double* p) { return __ldg(p); }
+__device__ __forceinline__ dfloat ldg_t(const dfloat* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return dfloat(v.x, v.y);
+}
+#endif
+
 template <typename T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
+template <> struct CplxOf<dfloat> { using type = dfloat2; };
 
 template <typename T> using cplx_t = typename CplxOf<T>::type;
 
 __host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ dfloat2 mk(dfloat a, dfloat b) { return dfloat2{a, b}; }
 
 template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }

@@ -443,6 +443,16 @@ __global__ void k_convert(const cplx_t<Ta>* __restrict__ a, cplx_t<Tb>* __restri
         b[i] = mk(Tb(a[i].x), Tb(a[i].y));
 }
 
+// the same conversion in place, for two types of equal size (float-float <-> FP64)
+template <typename Ta, typename Tb>
+__global__ void k_convert_inplace(void* p, size_t n) {
+    static_assert(sizeof(cplx_t<Ta>) == sizeof(cplx_t<Tb>), "in-place conversion needs equal sizes");
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const cplx_t<Ta> a = reinterpret_cast<const cplx_t<Ta>*>(p)[i];
+        reinterpret_cast<cplx_t<Tb>*>(p)[i] = mk(Tb(a.x), Tb(a.y));
+    }
+}
+
 // Gamma point with a non-uniform density (rigid translations t_c = e_c at
 // bin 0 span the null space of A_0; the spectrum is sought on their
 // M-orthogonal complement).  alpha[v][c] = t_c^H M v / t_c^H M t_c for nv

@@ -44,6 +44,22 @@ __device__ __forceinline__ R cos16(int m) {
     }
 }
 
+// float-float values: hi = cos rounded to float, lo = the rounded remainder
+template <>
+__device__ __forceinline__ dfloat cos16<dfloat>(int m) {
+    switch (m & 15) {
+        case 0: return dfloat(1.0f, 0.0f);
+        case 1: case 15: return dfloat(0.9238795042037964f, 2.830748968563057e-08f);
+        case 2: case 14: return dfloat(0.7071067690849304f, 1.2101617485882343e-08f);
+        case 3: case 13: return dfloat(0.3826834261417389f, 6.2233507236442165e-09f);
+        case 4: case 12: return dfloat(0.0f, 0.0f);
+        case 5: case 11: return dfloat(-0.3826834261417389f, -6.2233507236442165e-09f);
+        case 6: case 10: return dfloat(-0.7071067690849304f, -1.2101617485882343e-08f);
+        case 7: case 9: return dfloat(-0.9238795042037964f, -2.830748968563057e-08f);
+        default: return dfloat(-1.0f, 0.0f);
+    }
+}
+
 // x * exp(DIR * 2 pi i k / R) for power-of-two R <= 16 (k compile-time after unrolling)
 template <int R, int DIR, typename C>
 __device__ __forceinline__ C twiddle_pow2(C x, int k) {

@@ -104,6 +104,10 @@ struct bloch_plan {
     double* d_rd = nullptr;
     float2* d_twf[3] = {nullptr, nullptr, nullptr};
     double2* d_twd[3] = {nullptr, nullptr, nullptr};
+    // float-float copies (the FP64-class check of the FP32 form on the FP32 pipes)
+    dfloat2* d_twx[3] = {nullptr, nullptr, nullptr};
+    dfloat* d_Cx = nullptr;
+    dfloat* d_rx = nullptr;
     int* d_nactive = nullptr;
     int* h_nactive = nullptr;     // pinned
 
@@ -157,6 +161,7 @@ struct bloch_plan {
 
     bloch::Workspace<float> ws_f;
     bloch::Workspace<double> ws_d;
+    bloch::Workspace<dfloat> ws_x;
     size_t device_bytes = 0;
     unsigned long long launches = 0;   // kernels launched by this plan
     bloch_stats last_stats;

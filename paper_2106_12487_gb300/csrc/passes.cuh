@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8) ? 2 : 1) k_pass_x_stress
                 T sr = 0, si = 0;
 #pragma unroll
                 for (int j = 0; j < 6; ++j) {
-                    const T cij = __ldg(Cg + i * 6 + j);
+                    const T cij = ldg_t(Cg + i * 6 + j);
                     sr = fma(cij, gam[j].x, sr);
                     si = fma(cij, gam[j].y, si);
                 }
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256) k_pass_x_rho(cplx_t<T>* W, const int32_t*
     for (int e = tid; e < NP; e += nthr) {
         const int p = e / N, n = e - p * N;
         if (p < nr) {
-            const T r = __ldg(rtab + ids[(size_t)(r0 + p) * N + n]);
+            const T r = ldg_t(rtab + ids[(size_t)(r0 + p) * N + n]);
 #pragma unroll
             for (int c = 0; c < 3; ++c) buf[c][e] = cscale(buf[c][e], r);
         }

@@ -321,3 +321,21 @@ def test_lobpcg_matches_oracle(B, prec, bar, opt, rho_mix):
         assert st == 0 and stats["k_unconverged"] == 0
         assert freq_err(got, want) < bar
         assert stats["cg_iterations"] == 0          # no inner solves
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_fp32_forms_with_float_float_check(B, method):
+    """refine_arith = 1: the FP32 forms' FP64 check applies the operator in
+    float-float; frequencies against the oracle within the FP32 form's bar,
+    uniform and non-uniform density, a path through Gamma."""
+    import dataclasses
+    p = synth.small_polycrystal((12, 10, 8), 6, 19, n_bands=6)
+    ks = np.array([[0.0, 0.0, 0.0], [0.15, 0.0, 0.0], [0.6, 0.3, 0.0], [0.37, 0.21, -0.29]]) * math.pi / 1e-3
+    for rho_mix in (False, True):
+        q = p if not rho_mix else dataclasses.replace(p, rho=np.random.default_rng(8).uniform(3000.0, 9000.0, p.G))
+        want = O.solve_bands(O.Medium.from_problem(q), ks, 6, 1e-12, 1e-12, method="lanczos").omega
+        plan = B.Plan.from_problem(q, precision=1, method=method, tol_lin=1e-2, tol_eig=1e-5, block=8,
+                                   refine_arith=1)
+        got, stats, st = plan.solve_bands(ks, 6)
+        assert st == 0
+        assert freq_err(got, want) < 1e-6

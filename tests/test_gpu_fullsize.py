@@ -13,7 +13,8 @@ from paper_2106_12487_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-CHOSEN = dict(precision=1, method=0, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, max_outer=100)   # the bench's
+CHOSEN = dict(precision=1, method=0, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, max_outer=100,
+              refine_arith=1)   # the bench's
 # (the bench also sets block = n_bands + 2)
 
 

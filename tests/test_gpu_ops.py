@@ -216,3 +216,25 @@ def test_apply_K_real_basis(B, grid, prec):
     for b in range(2):
         want = np.fft.ifftn(O.apply_K(med, ks[b], np.fft.fftn(u[b], axes=ax)), axes=ax)
         assert rel(got[b], want) < TOL[prec]
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+def test_apply_K_float_float_matches_oracle(B, grid):
+    """BLOCH_FF: the stiffness operator in float-float arithmetic (48-bit
+    significand on the FP32 pipes; double buffers) against the FP64 oracle at
+    the FP64 path's tolerance -- the arithmetic of the FP32 form's check."""
+    import torch
+    p = synth.small_polycrystal(grid, 5, 3)
+    med = O.Medium.from_problem(p)
+    plan = B.Plan.from_problem(p, precision=0)
+    ks = np.array([[0.31, -0.12, 0.77], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]]) * math.pi / 1e-3
+    u = synth.random_field(grid, 11, batch=3)
+    out = to_dev(np.zeros_like(u), 0)
+    plan.apply_K(ks, to_dev(u, 0), out, precision=B.FF)
+    got = out.cpu().numpy()
+    for b in range(3):
+        ref = O.apply_K(med, ks[b], u[b])
+        if np.linalg.norm(ref) == 0:
+            assert np.linalg.norm(got[b]) <= 1e-30
+            continue
+        assert rel(got[b], ref) < 1e-12, (b, rel(got[b], ref))
