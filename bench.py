@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 METRIC = "k-point eigenpairs/s at 128^3 (freq rel err <=1e-6)"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0}   # algorithmic bytes per voxel, 5-pass chain
+KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0, 2: 868.0}   # algorithmic bytes per voxel, 5-pass chain (FF: 16 B complex)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum over the five passes) per system of the
 # FP32 fast-pass K-apply at 128^3, from one ncu capture of a 4-system launch (1845.6 MB read +
 # 1550.9 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--max-outer", type=int, default=100, help="sweep cap (profiling runs bound it)")
     ap.add_argument("--kapply-only", action="store_true", help="time only the K-apply chain")
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
-    ap.add_argument("--kapply-prec", default="form", choices=["form", "fp32", "fp64"],
+    ap.add_argument("--kapply-prec", default="form", choices=["form", "fp32", "fp64", "ff"],
                     help="with --kapply-only: precision of the timed chain (form = the form's), with --fft-variant "
                          "taken as given")
     ap.add_argument("--fft-variant", type=int, default=0, choices=[0, 1, 2],
@@ -354,14 +354,14 @@ def kapply_roofline(plan, p, prec, nb=0, fft_variant=0):
     kq = np.repeat(p.k_list[5:6], q, axis=0)
     stream = torch.cuda.current_stream()
     for _ in range(3):
-        plan.apply_K(kq, u, out)
+        plan.apply_K(kq, u, out, precision=prec)
     torch.cuda.synchronize()
     reps = 10
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        plan.apply_K(kq, u, out)
+        plan.apply_K(kq, u, out, precision=prec)
     e1.record(stream)
     torch.cuda.synchronize()
     t_apply = e0.elapsed_time(e1) / 1000.0 / reps
@@ -501,8 +501,8 @@ def run_ours(args, ws, rank, local):
     if args.kapply_only:
         if args.kapply_prec != "form":
             plan.close()
-            prec = bloch.FP64 if args.kapply_prec == "fp64" else bloch.FP32
-            opt = dict(opt, precision=prec, fft_variant=args.fft_variant)
+            prec = {"fp64": bloch.FP64, "fp32": bloch.FP32, "ff": bloch.FF}[args.kapply_prec]
+            opt = dict(opt, precision=bloch.FP64 if prec == bloch.FF else prec, fft_variant=args.fft_variant)
             plan = bloch.Plan.from_problem(p, **opt)
         roof = kapply_roofline(plan, p, prec, args.kapply_nb, opt["fft_variant"])
         if rank == 0:

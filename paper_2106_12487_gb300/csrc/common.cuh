@@ -8,7 +8,8 @@
 // floats with |lo| <= ulp(hi)/2, a 48-bit significand evaluated on the FP32
 // pipes.  Sum and product are formed from the error-free transformations --
 // Knuth's two-sum (s + e = a + b exactly) and, for the product, the residual
-// of a*b recovered with one fused multiply-add -- then renormalised.  The
+// of a*b recovered with one fused multiply-add (Dekker's product) -- then
+// renormalised.  The
 // _rn intrinsics keep every step individually rounded (no contraction).
 struct dfloat {
     float hi, lo;
@@ -32,11 +33,12 @@ __device__ __forceinline__ dfloat df_quick_two_sum(float a, float b) {   // |a| 
     const float s = __fadd_rn(a, b);
     return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
+// The low parts are added without their own error term: the sum is then
+// accurate to about 2^-48 of the larger operand (a normwise bound, the form
+// FFT error analysis uses) rather than of the result.
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
-    dfloat s = df_two_sum(a.hi, b.hi);
-    const dfloat t = df_two_sum(a.lo, b.lo);
-    s = df_quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return df_quick_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+    const dfloat s = df_two_sum(a.hi, b.hi);
+    return df_quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
