@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--max-outer", type=int, default=100, help="sweep cap (profiling runs bound it)")
     ap.add_argument("--kapply-only", action="store_true", help="time only the K-apply chain")
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
+    ap.add_argument("--pcg-only", type=int, default=0, metavar="ITERS",
+                    help="time only ITERS FP32 PCG iterations on --kapply-nb systems (default 4)")
     ap.add_argument("--kapply-prec", default="form", choices=["form", "fp32", "fp64", "ff"],
                     help="with --kapply-only: precision of the timed chain (form = the form's), with --fft-variant "
                          "taken as given")
@@ -373,6 +375,39 @@ def kapply_roofline(plan, p, prec, nb=0, fft_variant=0):
             "ms_per_launch": t_apply * 1000.0, "alg_bytes_per_launch": alg_bytes}
 
 
+PCG_BYTES_PER_VOXEL = 676.0   # FP32: K-apply 54c + 4, (p, Ap) partials 3c, CG vector kernels 27c (c = 8 B)
+
+
+def pcg_roofline(plan, p, nb, iters):
+    """One FP32 PCG iteration (Algorithm 2) on nb systems: `iters` iterations
+    with a tolerance no system reaches, timed with CUDA events on the
+    launching stream after one warm-up solve; the time per iteration includes
+    the loop's control (graph conditional node or host loop)."""
+    import torch
+    from paper_2106_12487_gb300 import bloch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    b = torch.randn(nb * 3 * plan.V, dtype=torch.complex64, device="cuda", generator=g)
+    x = torch.zeros_like(b)
+    kq = np.repeat(p.k_list[5:6], nb, axis=0)
+    stream = torch.cuda.current_stream()
+    plan.pcg(kq, b, x, 1e-30, max_iter=iters, precision=bloch.FP32, allow_nonconv=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    it, _, _ = plan.pcg(kq, b, x, 1e-30, max_iter=iters, precision=bloch.FP32, allow_nonconv=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    n_it = int(it.max())
+    t_it = e0.elapsed_time(e1) / 1000.0 / max(n_it, 1)
+    alg = PCG_BYTES_PER_VOXEL * plan.V * nb
+    peak, peak_src = peaks()
+    return {"bound": "hbm", "achieved": alg / t_it / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg / t_it / 1e9 / peak, "kernel": f"FP32 PCG iteration, {nb} systems at {tuple(p.grid)} "
+            f"({peak_src} peak)", "iterations": n_it, "ms_per_iteration": t_it * 1000.0,
+            "alg_bytes_per_iteration": alg}
+
+
 def train_learned(args):
     """Learned Fourier-space preconditioner: record CG pairs on 64^3 cells of
     the Zener family (two wave vectors each), then full-batch Adam.  Untimed;
@@ -498,6 +533,12 @@ def run_ours(args, ws, rank, local):
     if args.precond == "learned":
         lp, lp_info = train_learned(args)
         bloch.set_preconditioner(plan, lp)
+    if args.pcg_only:
+        roof = pcg_roofline(plan, p, args.kapply_nb or 4, args.pcg_only)
+        if rank == 0:
+            print(json.dumps({"pcg": roof}), flush=True)
+        plan.close()
+        return
     if args.kapply_only:
         if args.kapply_prec != "form":
             plan.close()
