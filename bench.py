@@ -33,8 +33,8 @@ KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0, 2: 868.0}   # algorithmic bytes pe
 # 1550.9 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
 # to `sources_sha256` (fpasses.cuh, fft.cuh, common.cuh in that order); otherwise traffic is null.
 KAPPLY_TRAFFIC = {"grid": (128, 128, 128), "precision": 1, "fft_variant": 0,
-                  "bytes_per_system": 3396.5e6 / 4,
-                  "sources_sha256": "9455e1d962ad0ae4dbb7acd9413840e5605b0182f8136f654b9ceb46b4397061"}
+                  "bytes_per_system": 3383.66e6 / 4,
+                  "sources_sha256": "a089297b59baf58ba1706c191aa3f8bf8fd2ff722aab9d402da608ca207dae57"}
 
 
 def parse():
@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--max-outer", type=int, default=100, help="sweep cap (profiling runs bound it)")
     ap.add_argument("--kapply-only", action="store_true", help="time only the K-apply chain")
     ap.add_argument("--kapply-nb", type=int, default=0, help="systems per K-apply launch (0 = block size)")
+    ap.add_argument("--alu-peaks", action="store_true",
+                    help="measure FP64/FP32 FMA throughput and time the FP64, float-float and FP32 operator chains "
+                         "on --kapply-nb systems against it")
     ap.add_argument("--pcg-only", type=int, default=0, metavar="ITERS",
                     help="time only ITERS FP32 PCG iterations on --kapply-nb systems (default 4)")
     ap.add_argument("--kapply-prec", default="form", choices=["form", "fp32", "fp64", "ff"],
@@ -375,6 +378,36 @@ def kapply_roofline(plan, p, prec, nb=0, fft_variant=0):
             "ms_per_launch": t_apply * 1000.0, "alg_bytes_per_launch": alg_bytes}
 
 
+def kapply_flops_per_voxel(grid):
+    """Algorithmic flops of one A_k apply per voxel: 36 length-N complex
+    transforms per voxel (6 along z, 6 along y, 12 along x, 6 along y, 6 along
+    z) at 5 log2(N) flops per point each, plus the pointwise strain (24),
+    stress (a real 6x6 on a complex 6-vector, 144) and divergence (30)."""
+    import math
+    nx, ny, nz = grid
+    return 5.0 * (12 * math.log2(nz) + 12 * math.log2(ny) + 12 * math.log2(nx)) + 24 + 144 + 30
+
+
+def alu_peaks_leg(p, opt, nb):
+    """FMA peaks of the device and the operator chains timed against them."""
+    from paper_2106_12487_gb300 import bloch
+    g64, g32 = bloch.fma_peaks()
+    fpv = kapply_flops_per_voxel(p.grid)
+    out = {"fma_peaks": {"fp64_gflops": g64, "fp32_gflops": g32, "how": "bloch_fma_peaks: CUDA events, "
+                         "8 x 256-thread CTAs per SM of independent FMA chains, FMA = 2 flops"},
+           "flops_per_voxel": fpv, "systems": nb, "chains": {}}
+    for name, prec in (("fp64", bloch.FP64), ("ff", bloch.FF), ("fp32", bloch.FP32)):
+        plan = bloch.Plan.from_problem(p, **dict(opt, precision=bloch.FP32 if prec == bloch.FP32 else bloch.FP64,
+                                                 fft_variant=0))
+        r = kapply_roofline(plan, p, prec, nb, 0)
+        plan.close()
+        gf = fpv * plan.V * nb / (r["ms_per_launch"] * 1e-3) / 1e9
+        out["chains"][name] = {"ms_per_launch": r["ms_per_launch"], "gflops": gf,
+                               "frac_of_fp64_fma_peak": gf / g64, "frac_of_fp32_fma_peak": gf / g32,
+                               "hbm_frac": r["frac"]}
+    return out
+
+
 PCG_BYTES_PER_VOXEL = 676.0   # FP32: K-apply 54c + 4, (p, Ap) partials 3c, CG vector kernels 27c (c = 8 B)
 
 
@@ -533,6 +566,12 @@ def run_ours(args, ws, rank, local):
     if args.precond == "learned":
         lp, lp_info = train_learned(args)
         bloch.set_preconditioner(plan, lp)
+    if args.alu_peaks:
+        plan.close()
+        leg = alu_peaks_leg(p, opt, args.kapply_nb or 4)
+        if rank == 0:
+            print(json.dumps({"alu": leg}), flush=True)
+        return
     if args.pcg_only:
         roof = pcg_roofline(plan, p, args.kapply_nb or 4, args.pcg_only)
         if rank == 0:

@@ -489,6 +489,20 @@ typedef struct {
 
 bloch_status bloch_plan_trace(bloch_plan* plan, int32_t enable, bloch_trace* out);
 
+/*
+ * FMA throughput of the current device (no counterpart in the paper): the
+ * denominators of the ALU-bound chains' rooflines (the FP64 operator is
+ * bound by GB300's FP64 units, not by HBM).  Times, with CUDA events after
+ * three warm-up launches, one launch of 8 CTAs of 256 threads per SM in
+ * which every thread runs independent chains of fused multiply-adds on 8
+ * accumulators (no memory traffic but one store per thread), once in FP64
+ * and once in FP32; an FMA counts as 2 flops.
+ *   fp64_gflops, fp32_gflops  (out, host) GFLOP/s; either may be NULL
+ * Allocates 2.4 MB of device scratch for the call.
+ * Errors: BLOCH_ENOMEM, BLOCH_ECUDA.
+ */
+bloch_status bloch_fma_peaks(double* fp64_gflops, double* fp32_gflops);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* bloch_last_error(void);
 

@@ -29,7 +29,7 @@ EXPORTED = ["bloch_default_options", "bloch_plan_create", "bloch_plan_destroy", 
             "bloch_lp_collect", "bloch_lp_loss_grad", "bloch_lp_train", "bloch_lp_num_blocks", "bloch_lp_export_block",
             "bloch_plan_set_preconditioner", "bloch_plan_autotune",
             "bloch_plan_trace", "bloch_apply_K_real", "bloch_lp_add_pairs", "bloch_group_velocity",
-            "bloch_eigvec_real"]
+            "bloch_eigvec_real", "bloch_fma_peaks"]
 
 
 class BlochError(RuntimeError):
@@ -128,13 +128,14 @@ def lib():
     L.bloch_plan_set_preconditioner.argtypes = [VP, VP]
     L.bloch_plan_autotune.argtypes = [VP, I32, I32, P(TuneReport)]
     L.bloch_plan_trace.argtypes = [VP, I32, P(Trace)]
+    L.bloch_fma_peaks.argtypes = [P(D), P(D)]
     for f in ["bloch_lp_create", "bloch_lp_params", "bloch_lp_collect", "bloch_lp_add_pairs", "bloch_lp_loss_grad",
               "bloch_lp_train",
               "bloch_lp_export_block", "bloch_plan_set_preconditioner"]:
         getattr(L, f).restype = ctypes.c_int
     for f in ["bloch_plan_create", "bloch_apply_K", "bloch_apply_K_noalloc", "bloch_apply_M", "bloch_apply_precond", "bloch_pcg",
               "bloch_solve_bands", "bloch_host_gen_eig", "bloch_plan_autotune", "bloch_plan_trace",
-              "bloch_apply_K_real", "bloch_group_velocity", "bloch_eigvec_real"]:
+              "bloch_apply_K_real", "bloch_group_velocity", "bloch_eigvec_real", "bloch_fma_peaks"]:
         getattr(L, f).restype = ctypes.c_int
     _LIB = L
     return L
@@ -420,6 +421,15 @@ class LearnedPrecond:
                                            _dptr(ns, ctypes.c_int32)))
         return dict(grid=tuple(int(v) for v in grid), q=q, mom=mom.reshape(V, 13), C0V=C0V.reshape(6, 6),
                     samples=int(ns[0]))
+
+
+def fma_peaks() -> tuple[float, float]:
+    """bloch_fma_peaks: measured FP64 and FP32 FMA throughput (GFLOP/s) of
+    the current device."""
+    g64 = ctypes.c_double(0.0)
+    g32 = ctypes.c_double(0.0)
+    _check(lib().bloch_fma_peaks(ctypes.byref(g64), ctypes.byref(g32)))
+    return g64.value, g32.value
 
 
 def set_preconditioner(plan: Plan, lp: "LearnedPrecond | None"):

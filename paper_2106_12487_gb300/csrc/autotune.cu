@@ -180,3 +180,67 @@ extern "C" bloch_status bloch_plan_autotune(bloch_plan* pl, int32_t precision, i
     if (precision == BLOCH_FP64) return tune<double>(pl, systems, report);
     return set_error(BLOCH_EINVAL, "precision must be BLOCH_FP32 or BLOCH_FP64");
 }
+
+namespace {
+
+// Independent FMA chains: 8 accumulators per thread, 16 x 8 FMAs per loop trip.
+template <typename T>
+__global__ void k_fma_chain(T* out, int trips) {
+    T a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = T(threadIdx.x) * T(1e-6) + T(i);
+    const T m = T(1.0000001), c = T(1e-12);
+    for (int it = 0; it < trips; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = fma(a[i], m, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+bloch_status fma_rate(int blocks, int trips, double* gflops) {
+    const int threads = 256;
+    T* d = nullptr;
+    if (cudaMalloc(&d, sizeof(T) * (size_t)blocks * threads) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(BLOCH_ENOMEM, "FMA probe: device allocation failed");
+    }
+    Timer t;
+    bloch_status st = BLOCH_OK;
+    if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) st = BLOCH_ECUDA;
+    if (st == BLOCH_OK) {
+        for (int w = 0; w < 3; ++w) k_fma_chain<T><<<blocks, threads>>>(d, trips);
+        cudaEventRecord(t.a);
+        k_fma_chain<T><<<blocks, threads>>>(d, trips);
+        cudaEventRecord(t.b);
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess || ms <= 0.f)
+            st = BLOCH_ECUDA;
+        else
+            *gflops = 2.0 * blocks * threads * (double)trips * 16 * 8 / ms / 1e6;
+    }
+    cudaFree(d);
+    return st == BLOCH_OK ? st : set_error(st, "FMA probe: CUDA error");
+}
+
+}  // namespace
+
+extern "C" bloch_status bloch_fma_peaks(double* fp64_gflops, double* fp32_gflops) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return set_error(BLOCH_ECUDA, "FMA probe: no device");
+    double g64 = 0.0, g32 = 0.0;
+    bloch_status st = fma_rate<double>(sms * 8, 2000, &g64);
+    if (st == BLOCH_OK) st = fma_rate<float>(sms * 8, 16000, &g32);
+    if (st != BLOCH_OK) return st;
+    if (fp64_gflops) *fp64_gflops = g64;
+    if (fp32_gflops) *fp32_gflops = g32;
+    return BLOCH_OK;
+}

@@ -123,12 +123,10 @@ static void z_strain(bloch_plan* pl, int nb, const float2* u, float2* E, const f
 
 template <int RA, int RB>
 static void x_stress(bloch_plan* pl, int nb, float2* E) {
-    constexpr int N = RA * RB;
-    constexpr int LD = N + N / 16;
     constexpr int P = 128 / RA;
     const long long rows = (long long)pl->Ny * pl->Nz;
     dim3 gr((unsigned)((rows + P - 1) / P), nb);
-    k_fpass_x_stress<float, RA, RB><<<gr, 128, (size_t)(N + 3 * P * LD) * sizeof(float2), pl->stream>>>(
+    k_fpass_x_stress<float, RA, RB><<<gr, 128, fpass_x_smem<float, RA, RB>(), pl->stream>>>(
         E, pl->d_ids, pl->d_Cpf, pl->d_twf[0], pl->geo_f);
 }
 

@@ -351,10 +351,8 @@ static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale, const c
 template <typename T, int RA, int RB>
 static void fast_x3(bloch_plan* pl, int nb) {
     const Geo& g = geo_of<T>(pl);
-    constexpr int N = RA * RB;
-    constexpr int LD = N + N / 16;
     constexpr int P = 128 / RA;
-    const size_t smem = (size_t)(N + 3 * P * LD) * sizeof(cplx_t<T>);
+    const size_t smem = fpass_x_smem<T, RA, RB>();
     const long long rows = (long long)pl->Ny * pl->Nz;
     dim3 gr((unsigned)((rows + P - 1) / P), nb);
     ++pl->launches;

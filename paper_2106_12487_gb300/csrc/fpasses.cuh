@@ -353,9 +353,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 
 template <typename T, int RA, int RB>
-__global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
-                                                           const T* __restrict__ Cpk,
-                                                           const cplx_t<T>* __restrict__ twx, Geo g) {
+__device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __restrict__ ids,
+                                                const T* __restrict__ Cpk, const cplx_t<T>* __restrict__ twx,
+                                                const Geo& g) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int LD = N + N / 16;
@@ -476,6 +476,194 @@ __global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const i
             }
         }
     }
+}
+
+
+// sigma = C_g gamma at one owned element (packed symmetric 6x6, 21 per grain)
+template <typename T, typename C>
+__device__ __forceinline__ void stress_at(C (&s)[6], const T* __restrict__ Cg) {
+    C gam[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gam[c] = s[c];
+    T cij[6][6];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int jj = i; jj < 6; ++jj) {
+            cij[i][jj] = __ldg(Cg + k++);
+            cij[jj][i] = cij[i][jj];
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T sr = 0, si = 0;
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) {
+            sr = fma(cij[i][jj], gam[jj].x, sr);
+            si = fma(cij[i][jj], gam[jj].y, si);
+        }
+        s[i] = mk(sr, si);
+    }
+}
+
+// Balanced form for P * RB == 64 (N = 128 as 16 x 8, N = 32 as 8 x 4), where a
+// component's radix-RA stage has tasks for only half of the 128 threads: the
+// components are taken in pairs, threads 0-63 running the radix-RA stage of
+// the pair's first component and threads 64-127 that of the second, so every
+// warp works in every stage and one barrier serves two components.  The
+// pairs' pencils stream in by cp.async, two pairs in flight (four staging
+// buffers); the grain ids of the CTA's rows follow as a fifth group, so the
+// stress step reads them from shared memory.  10 barriers per CTA.
+template <int N>
+constexpr int x_ids_ld() { return N + 16; }
+
+template <typename T, int RA, int RB>
+__device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __restrict__ ids,
+                                                const T* __restrict__ Cpk, const cplx_t<T>* __restrict__ twx,
+                                                const Geo& g) {
+    using C = cplx_t<T>;
+    constexpr int N = RA * RB;
+    constexpr int LD = N + N / 16;
+    constexpr int P = 128 / RA;
+    constexpr int LI = x_ids_ld<N>();
+    static_assert(P * RB == 64, "paired x pass needs P * RB == 64");
+    static_assert(P * LI * sizeof(int32_t) <= P * LD * sizeof(C), "grain-id tile must fit a staging buffer");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* stg = tw + N;          // 4 x P*LD: pair buffers (set 0: 0, 1; set 1: 2, 3)
+    C* xb = stg + 4 * P * LD; // 2 x P*LD exchange of the inverse transform
+    int32_t* sid = reinterpret_cast<int32_t*>(stg + 2 * P * LD);   // set 1, buffer 0, once free
+    const int tid = threadIdx.x;
+    const int b = blockIdx.y;
+    const unsigned rows = (unsigned)g.Ny * (unsigned)g.Nz;
+    const unsigned r0 = blockIdx.x * P;
+    const int nr = (int)min((unsigned)P, rows - r0);
+    C* Eb = E + (size_t)b * 6 * g.V;
+    auto prefetch = [&](int c, C* dstb) {
+        const C* src = Eb + (size_t)c * g.V + (size_t)r0 * N;
+#pragma unroll
+        for (int e = tid; e < P * N; e += 128) {
+            const int p = e / N, n = e % N;
+            const bool ok = p < nr;
+            cp_async_cplx(dstb + p * LD + n, src + (ok ? e : 0), ok);
+        }
+    };
+    prefetch(0, stg);
+    prefetch(1, stg + P * LD);
+    cp_async_commit();
+    prefetch(2, stg + 2 * P * LD);
+    prefetch(3, stg + 3 * P * LD);
+    cp_async_commit();
+    for (int i = tid; i < N; i += 128) tw[i] = twx[i];
+    const int half = tid >> 6;              // radix-RA stage: component 2m + half
+    const int j1 = (tid & 63) % RB, p1 = (tid & 63) / RB;
+    const int j2 = tid % RA, p2 = tid / RA; // radix-RB stage and the stress: one task per thread
+    const bool own = p2 < nr;
+    C s[6][RB];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        if (m < 2) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();   // pair m landed; every thread is past the exchange reads of pair m - 1
+        {
+            const C* sb = stg + ((m & 1) * 2 + half) * P * LD + p1 * LD;
+            C v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = sb[j1 + r * RB];
+            RegDFT<RA, +1, C>::run(v);
+            C* xh = xb + half * P * LD + p1 * LD;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) xh[xpad(j1 * RA + r)] = v[r];
+        }
+        __syncthreads();   // exchange written; the staging buffers of pair m are free
+        if (m == 0) {      // pair 2 into set 0
+            prefetch(4, stg);
+            prefetch(5, stg + P * LD);
+            cp_async_commit();
+        } else if (m == 1) {   // the grain ids of the CTA's rows into set 1
+            for (int e = tid; e < P * (N / 4); e += 128) {
+                const int p = e / (N / 4), n4 = e % (N / 4);
+                const bool ok = p < nr;
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(sid + p * LI + 4 * n4);
+                const int32_t* src = ids + (ok ? (size_t)(r0 + p) * N + 4 * n4 : 0);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src),
+                             "r"(ok ? 16 : 0));
+            }
+            cp_async_commit();
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            C v[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) v[r] = xb[h * P * LD + p2 * LD + xpad(j2 + r * RA)];
+#pragma unroll
+            for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], +1);
+            RegDFT<RB, +1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) s[2 * m + h][r] = v[r];
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();   // grain ids visible; all staging buffers free for the forward exchange
+    if (own) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            C sv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sv[c] = s[c][r];
+            stress_at<T>(sv, Cpk + (size_t)sid[p2 * LI + j2 + r * RA] * 21);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s[c][r] = sv[c];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        C* bufs = stg + (m & 1) * 2 * P * LD;
+        // forward stage 1 (radix RB) of both components by every thread
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            C v[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) v[r] = s[2 * m + h][r];
+            RegDFT<RB, -1, C>::run(v);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) bufs[h * P * LD + p2 * LD + xpad(j2 * RB + r)] = v[r];
+        }
+        __syncthreads();   // a thread writing this buffer set again (pair m + 2) has passed the next barrier
+        // forward stage 2 (radix RA): component 2m + half
+        {
+            C v[RA];
+            const C* bh = bufs + half * P * LD + p1 * LD;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = bh[xpad(j1 + r * RB)];
+#pragma unroll
+            for (int r = 1; r < RA; ++r) v[r] = twmul(v[r], tw[r * j1], -1);
+            RegDFT<RA, -1, C>::run(v);
+            if (p1 < nr) {
+                C* dst = Eb + (size_t)(2 * m + half) * g.V + (size_t)(r0 + p1) * N + j1;
+#pragma unroll
+                for (int r = 0; r < RA; ++r) dst[r * RB] = v[r];
+            }
+        }
+    }
+}
+
+// Shared memory of k_fpass_x_stress<T, RA, RB> (bytes).
+template <typename T, int RA, int RB>
+constexpr size_t fpass_x_smem() {
+    constexpr int N = RA * RB, LD = N + N / 16, P = 128 / RA;
+    return (size_t)(N + (P * RB == 64 ? 6 : 3) * P * LD) * sizeof(cplx_t<T>);
+}
+
+template <typename T, int RA, int RB>
+__global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
+                                                           const T* __restrict__ Cpk,
+                                                           const cplx_t<T>* __restrict__ twx, Geo g) {
+    if (sys_idle(g, blockIdx.y)) return;
+    if constexpr ((128 / RA) * RB == 64)
+        x_stress_paired<T, RA, RB>(E, ids, Cpk, twx, g);
+    else
+        x_stress_single<T, RA, RB>(E, ids, Cpk, twx, g);
 }
 
 }  // namespace bloch

@@ -122,3 +122,15 @@ def test_trace_phases_are_consistent(B, prec, method):
     plan.solve_bands(ks, 4)
     off = plan.trace(False)
     assert all(v["count"] == 0 for v in off.values())
+
+
+def test_fma_peaks():
+    """bloch_fma_peaks: positive rates, FP32 above FP64 (GB300's FP64 units
+    run at a small fraction of its FP32 rate), and both below the FMA issue
+    limit of the device (2 flops x 128 lanes x SMs x 2.1 GHz for FP32)."""
+    import torch
+    from paper_2106_12487_gb300 import bloch as B
+    g64, g32 = B.fma_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0 < g64 < g32
+    assert g32 < 2 * 128 * sms * 2.2e9 / 1e9
