@@ -106,6 +106,12 @@ __device__ __forceinline__ void cp_async_cplx(C* smem, const C* gmem, bool src_v
     else
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
 }
+// Asynchronous 16-byte global -> shared copy that bypasses L1 (both
+// addresses 16-byte aligned); src_valid = false fills zeros without reading.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool src_valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_valid ? 16 : 0));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }

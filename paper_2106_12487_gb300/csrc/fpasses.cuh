@@ -352,6 +352,32 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
 // to spread the strided Stockham writes over the banks.
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 
+// Index of C_ij (any order) in the packed upper triangle of a symmetric 6x6.
+__host__ __device__ constexpr int sym6(int i, int j) {
+    return i <= j ? i * 6 - i * (i - 1) / 2 + (j - i) : j * 6 - j * (j - 1) / 2 + (i - j);
+}
+
+// sigma = C_g gamma at the element r of every component (packed symmetric
+// table, 21 per grain), one row of C_g at a time so that few coefficients
+// are live next to the six components held per element.
+template <typename T, typename C, int R>
+__device__ __forceinline__ void stress_at(C (&s)[6][R], int r, const T* __restrict__ Cg) {
+    C sig[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T sr = 0, si = 0;
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) {
+            const T cij = __ldg(Cg + sym6(i, jj));
+            sr = fma(cij, s[jj][r].x, sr);
+            si = fma(cij, s[jj][r].y, si);
+        }
+        sig[i] = mk(sr, si);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i][r] = sig[i];
+}
+
 template <typename T, int RA, int RB>
 __device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __restrict__ ids,
                                                 const T* __restrict__ Cpk, const cplx_t<T>* __restrict__ twx,
@@ -366,18 +392,26 @@ __device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __r
     C* xb = stg + 2 * P * LD; // P*LD exchange of the inverse transform
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
-    if (sys_idle(g, b)) return;
     const unsigned rows = (unsigned)g.Ny * (unsigned)g.Nz;
     const unsigned r0 = blockIdx.x * P;
     const int nr = (int)min((unsigned)P, rows - r0);
     C* Eb = E + (size_t)b * 6 * g.V;
     auto prefetch = [&](int c, C* dstb) {
         const C* src = Eb + (size_t)c * g.V + (size_t)r0 * N;
+        if constexpr (LD % 2 == 0 && sizeof(C) == 8) {   // 16-byte rows: two values per copy, past L1
 #pragma unroll
-        for (int e = tid; e < P * N; e += 128) {
-            const int p = e / N, n = e % N;
-            const bool ok = p < nr;
-            cp_async_cplx(dstb + p * LD + n, src + (ok ? e : 0), ok);
+            for (int e = tid; e < P * N / 2; e += 128) {
+                const int p = e / (N / 2), n = 2 * (e % (N / 2));
+                const bool ok = p < nr;
+                cp_async16(dstb + p * LD + n, src + (ok ? p * N + n : 0), ok);
+            }
+        } else {
+#pragma unroll
+            for (int e = tid; e < P * N; e += 128) {
+                const int p = e / N, n = e % N;
+                const bool ok = p < nr;
+                cp_async_cplx(dstb + p * LD + n, src + (ok ? e : 0), ok);
+            }
         }
         cp_async_commit();
     };
@@ -420,32 +454,8 @@ __device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __r
     // stress sigma = C_g gamma at the RB owned elements (packed symmetric table, 21 per grain)
     if (own) {
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-            const int n = j2 + r * RA;
-            const T* Cg = Cpk + (size_t)ids[(size_t)(r0 + p2) * N + n] * 21;
-            C gam[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) gam[c] = s[c][r];
-            int k = 0;
-            T cij[6][6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-#pragma unroll
-                for (int jj = i; jj < 6; ++jj) {
-                    cij[i][jj] = __ldg(Cg + k++);
-                    cij[jj][i] = cij[i][jj];
-                }
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                T sr = 0, si = 0;
-#pragma unroll
-                for (int jj = 0; jj < 6; ++jj) {
-                    sr = fma(cij[i][jj], gam[jj].x, sr);
-                    si = fma(cij[i][jj], gam[jj].y, si);
-                }
-                s[i][r] = mk(sr, si);
-            }
-        }
+        for (int r = 0; r < RB; ++r)
+            stress_at<T>(s, r, Cpk + (size_t)ids[(size_t)(r0 + p2) * N + j2 + r * RA] * 21);
     }
     __syncthreads();   // the staging buffers become the forward exchange buffers
 #pragma unroll
@@ -478,33 +488,6 @@ __device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __r
     }
 }
 
-
-// sigma = C_g gamma at one owned element (packed symmetric 6x6, 21 per grain)
-template <typename T, typename C>
-__device__ __forceinline__ void stress_at(C (&s)[6], const T* __restrict__ Cg) {
-    C gam[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) gam[c] = s[c];
-    T cij[6][6];
-    int k = 0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int jj = i; jj < 6; ++jj) {
-            cij[i][jj] = __ldg(Cg + k++);
-            cij[jj][i] = cij[i][jj];
-        }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        T sr = 0, si = 0;
-#pragma unroll
-        for (int jj = 0; jj < 6; ++jj) {
-            sr = fma(cij[i][jj], gam[jj].x, sr);
-            si = fma(cij[i][jj], gam[jj].y, si);
-        }
-        s[i] = mk(sr, si);
-    }
-}
 
 // Balanced form for P * RB == 64 (N = 128 as 16 x 8, N = 32 as 8 x 4), where a
 // component's radix-RA stage has tasks for only half of the 128 threads: the
@@ -539,13 +522,15 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
     const unsigned r0 = blockIdx.x * P;
     const int nr = (int)min((unsigned)P, rows - r0);
     C* Eb = E + (size_t)b * 6 * g.V;
+    // two complex values per 16-byte copy, past L1 (which then keeps the stiffness table)
+    static_assert(sizeof(C) == 8 && LD % 2 == 0, "paired x pass stages FP32 complex values in 16-byte rows");
     auto prefetch = [&](int c, C* dstb) {
         const C* src = Eb + (size_t)c * g.V + (size_t)r0 * N;
 #pragma unroll
-        for (int e = tid; e < P * N; e += 128) {
-            const int p = e / N, n = e % N;
+        for (int e = tid; e < P * N / 2; e += 128) {
+            const int p = e / (N / 2), n = 2 * (e % (N / 2));
             const bool ok = p < nr;
-            cp_async_cplx(dstb + p * LD + n, src + (ok ? e : 0), ok);
+            cp_async16(dstb + p * LD + n, src + (ok ? p * N + n : 0), ok);
         }
     };
     prefetch(0, stg);
@@ -584,10 +569,7 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
             for (int e = tid; e < P * (N / 4); e += 128) {
                 const int p = e / (N / 4), n4 = e % (N / 4);
                 const bool ok = p < nr;
-                const unsigned sa = (unsigned)__cvta_generic_to_shared(sid + p * LI + 4 * n4);
-                const int32_t* src = ids + (ok ? (size_t)(r0 + p) * N + 4 * n4 : 0);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src),
-                             "r"(ok ? 16 : 0));
+                cp_async16(sid + p * LI + 4 * n4, ids + (ok ? (size_t)(r0 + p) * N + 4 * n4 : 0), ok);
             }
             cp_async_commit();
         }
@@ -607,14 +589,7 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
     __syncthreads();   // grain ids visible; all staging buffers free for the forward exchange
     if (own) {
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-            C sv[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) sv[c] = s[c][r];
-            stress_at<T>(sv, Cpk + (size_t)sid[p2 * LI + j2 + r * RA] * 21);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) s[c][r] = sv[c];
-        }
+        for (int r = 0; r < RB; ++r) stress_at<T>(s, r, Cpk + (size_t)sid[p2 * LI + j2 + r * RA] * 21);
     }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
