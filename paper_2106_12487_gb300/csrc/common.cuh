@@ -59,6 +59,10 @@ struct dfloat2 {
 
 #ifdef __CUDACC__
 // read-only cached load of a real table entry of any of the field types
+// Store of a streamed FP32 complex value that takes no L1 line.
+__device__ __forceinline__ void st_stream(float2* p, float2 v) {
+    asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y));
+}
 __device__ __forceinline__ float ldg_t(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double ldg_t(const double* p) { return __ldg(p); }
 __device__ __forceinline__ dfloat ldg_t(const dfloat* p) {

@@ -617,7 +617,7 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
             if (p1 < nr) {
                 C* dst = Eb + (size_t)(2 * m + half) * g.V + (size_t)(r0 + p1) * N + j1;
 #pragma unroll
-                for (int r = 0; r < RA; ++r) dst[r * RB] = v[r];
+                for (int r = 0; r < RA; ++r) st_stream(dst + r * RB, v[r]);
             }
         }
     }
