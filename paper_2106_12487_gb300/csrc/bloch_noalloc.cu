@@ -112,12 +112,11 @@ static void y_pass(bloch_plan* pl, int DIR, int nb, float2* E) {
 // neighbouring pencils, the launch shape of bloch_apply_K
 template <int RA, int RB>
 static void z_strain(bloch_plan* pl, int nb, const float2* u, float2* E, const float* qtab) {
-    constexpr int N = RA * RB;
     constexpr int NT = kFastZThreads;
     constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
-    k_fpass_z_strain<float, RA, RB, NT><<<gr, NT, (size_t)(N + 4 * N * P) * sizeof(float2), pl->stream>>>(
+    k_fpass_z_strain<float, RA, RB, NT><<<gr, NT, fpass_z1_smem<float, RA, RB, NT>(), pl->stream>>>(
         u, E, qtab, pl->d_twf[2], pl->geo_f);
 }
 
@@ -132,12 +131,11 @@ static void x_stress(bloch_plan* pl, int nb, float2* E) {
 
 template <int RA, int RB>
 static void z_div(bloch_plan* pl, int nb, const float2* E, float2* out, const float* qtab) {
-    constexpr int N = RA * RB;
     constexpr int NT = kFastZThreads;
     constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
-    k_fpass_z_div<float, RA, RB, NT><<<gr, NT, (size_t)(N + 3 * N * P) * sizeof(float2), pl->stream>>>(
+    k_fpass_z_div<float, RA, RB, NT><<<gr, NT, fpass_z5_smem<float, RA, RB, NT>(), pl->stream>>>(
         E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale, nullptr, nullptr);
 }
 

@@ -323,11 +323,10 @@ static void fast_y(bloch_plan* pl, int DIR, int nb, cplx_t<T>* E) {
 template <typename T, int RA, int RB>
 static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
     const Geo& g = geo_of<T>(pl);
-    constexpr int N = RA * RB;
     constexpr int NT = kFastZThreads;
     constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
-    const size_t smem = (size_t)(N + 4 * N * P) * sizeof(cplx_t<T>);
+    const size_t smem = fpass_z1_smem<T, RA, RB, NT>();
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
     k_fpass_z_strain<T, RA, RB, NT><<<gr, NT, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
@@ -337,11 +336,10 @@ static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
 template <typename T, int RA, int RB>
 static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale, const cplx_t<T>* dotp, double2* dpart) {
     const Geo& g = geo_of<T>(pl);
-    constexpr int N = RA * RB;
     constexpr int NT = kFastZThreads;
     constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
-    const size_t smem = (size_t)(N + 3 * N * P) * sizeof(cplx_t<T>);
+    const size_t smem = fpass_z5_smem<T, RA, RB, NT>();
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
     k_fpass_z_div<T, RA, RB, NT><<<gr, NT, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,

@@ -129,13 +129,25 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
     const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T* qyt = qxt + g.Nx;
     const T* qzt = qyt + g.Ny;
+    // FP32: two neighbouring pencils per 16-byte copy, past L1 (P, pi0 and the
+    // plane are even, so a pair is wholly inside or outside the ragged tail)
+    constexpr bool k16 = sizeof(C) == 8 && P % 2 == 0;
     auto prefetch = [&](int k, C* dstb) {
         const C* src = Ub + (size_t)k * g.V;
+        if constexpr (k16) {
 #pragma unroll
-        for (int e = tid; e < NP; e += NT) {
-            const int n = e / P, p = e % P;
-            const bool ok = p < np;
-            cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+            for (int e = 2 * tid; e < NP; e += 2 * NT) {
+                const int n = e / P, p = e % P;
+                const bool ok = p < np;
+                cp_async16(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+            }
+        } else {
+#pragma unroll
+            for (int e = tid; e < NP; e += NT) {
+                const int n = e / P, p = e % P;
+                const bool ok = p < np;
+                cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+            }
         }
         cp_async_commit();
     };
@@ -145,11 +157,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
     const int p2 = tid % P, j2 = tid / P;
     const unsigned pi = pi0 + (p2 < np ? p2 : 0);
     const T qx = qxt[pi % (unsigned)g.Nx], qy = qyt[pi / (unsigned)g.Nx];
-    const int p1 = tid % P, j1 = tid / P;
-    const bool st1 = tid < P * RB;
+    // stage 1 has P * RB tasks per transform and two transforms per component
+    // (plain and q_z-scaled): with P * RB == NT / 2 the first half of the CTA
+    // runs the plain one and the second half the scaled one
+    constexpr bool split = 2 * P * RB == NT;
+    const int t1 = split ? tid % (P * RB) : tid;
+    const int p1 = t1 % P, j1 = t1 / P;
+    const bool st1 = split || tid < P * RB;
+    const bool scaled = split && tid >= P * RB;
     C az[RB], ax[RB];
     auto store = [&](int c, int r, C v) {
-        if (p2 < np) Eb[(size_t)c * g.V + (size_t)(j2 + r * RA) * plane + pi0 + p2] = v;
+        if (p2 < np) {
+            C* d = Eb + (size_t)c * g.V + (size_t)(j2 + r * RA) * plane + pi0 + p2;
+            if constexpr (sizeof(C) == 8) st_stream(d, v);
+            else *d = v;
+        }
     };
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
@@ -157,7 +179,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
         if (kk < 2) cp_async_wait<1>();
         else cp_async_wait<0>();
         __syncthreads();
-        if (st1) {
+        if constexpr (split) {
+            const C* sb = stg + (kk & 1) * NP;
+            C v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                v[r] = sb[(j1 + r * RB) * P + p1];
+                if (scaled) v[r] = cscale(v[r], qzt[j1 + r * RB]);
+            }
+            RegDFT<RA, +1, C>::run(v);
+            C* dst = scaled ? bufB : bufA;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) dst[(j1 * RA + r) * P + p1] = v[r];
+        } else if (st1) {
             const C* sb = stg + (kk & 1) * NP;
             C u[RA], v[RA];
 #pragma unroll
@@ -231,10 +265,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
     constexpr int N = RA * RB;
     constexpr int P = NT / RA;
     constexpr int NP = N * P;
+    // With 2 P RB == NT a component's radix-RA stage has tasks for half of the
+    // CTA: the components then go in pairs (first half of the CTA on the
+    // pair's first component, second half on its second), two pairs in
+    // flight in four staging buffers and one exchange buffer per component.
+    constexpr bool pair = 2 * P * RB == NT;
+    constexpr int NSTG = pair ? 4 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* stg = tw + N;          // 2 x NP staging
-    C* xb = stg + 2 * NP;     // NP exchange
+    C* stg = tw + N;             // NSTG x NP staging
+    C* xb = stg + NSTG * NP;     // (pair ? 2 : 1) x NP exchange
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
     if (sys_idle(g, b)) return;
@@ -246,49 +286,46 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
     const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T* qyt = qxt + g.Nx;
     const T* qzt = qyt + g.Ny;
+    constexpr bool k16 = sizeof(C) == 8 && P % 2 == 0;   // as in the z-strain pass
     auto prefetch = [&](int c, C* dstb) {
         const C* src = Eb + (size_t)c * g.V;
+        if constexpr (k16) {
 #pragma unroll
-        for (int e = tid; e < NP; e += NT) {
-            const int n = e / P, p = e % P;
-            const bool ok = p < np;
-            cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+            for (int e = 2 * tid; e < NP; e += 2 * NT) {
+                const int n = e / P, p = e % P;
+                const bool ok = p < np;
+                cp_async16(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+            }
+        } else {
+#pragma unroll
+            for (int e = tid; e < NP; e += NT) {
+                const int n = e / P, p = e % P;
+                const bool ok = p < np;
+                cp_async_cplx(dstb + e, src + (ok ? (size_t)n * plane + pi0 + p : 0), ok);
+            }
         }
         cp_async_commit();
     };
-    prefetch(0, stg);
-    prefetch(1, stg + NP);
+#pragma unroll
+    for (int c = 0; c < NSTG; ++c) prefetch(c, stg + c * NP);
     for (int i = tid; i < N; i += NT) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
     const unsigned pi = pi0 + (p2 < np ? p2 : 0);
     const T qv[2] = {qxt[pi % (unsigned)g.Nx], qyt[pi / (unsigned)g.Nx]};
-    const int p1 = tid % P, j1 = tid / P;
-    const bool st1 = tid < P * RB;
+    const int t1 = pair ? tid % (P * RB) : tid;
+    const int p1 = t1 % P, j1 = t1 / P;
+    const int half = pair ? tid / (P * RB) : 0;
+    const bool st1 = pair || tid < P * RB;
     C acc[3][RB];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        if (c < 5) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        __syncthreads();
-        if (st1) {
-            const C* sb = stg + (c & 1) * NP;
-            C v[RA];
-#pragma unroll
-            for (int r = 0; r < RA; ++r) v[r] = sb[(j1 + r * RB) * P + p1];
-            RegDFT<RA, -1, C>::run(v);
-#pragma unroll
-            for (int r = 0; r < RA; ++r) xb[(j1 * RA + r) * P + p1] = v[r];
-        }
-        __syncthreads();
-        if (c + 2 < 6) prefetch(c + 2, stg + (c & 1) * NP);
-        else cp_async_commit();
+    // stage 2 of component c from exchange buffer xc, accumulated into out_a, out_b:
+    // sigma_c contributes q_b sigma to out_a and q_a sigma to out_b
+    auto stage2 = [&](const int c, const C* xc) {
         C v[RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) v[r] = xb[(j2 + r * RA) * P + p2];
+        for (int r = 0; r < RB; ++r) v[r] = xc[(j2 + r * RA) * P + p2];
 #pragma unroll
         for (int r = 1; r < RB; ++r) v[r] = twmul(v[r], tw[r * j2], -1);
         RegDFT<RB, -1, C>::run(v);
-        // sigma_c contributes q_b sigma to out_a and q_a sigma to out_b
         const int ca = c < 3 ? c : (c == 3 ? 1 : 0);
         const int cb = c < 3 ? c : (c == 5 ? 1 : 2);
 #pragma unroll
@@ -303,6 +340,51 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
                 acc[cb][r] = cadd(acc[cb][r], cscale(v[r], qa));
             }
         }
+    };
+    if constexpr (pair) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            if (m < 2) cp_async_wait<2>();
+            else cp_async_wait<0>();
+            __syncthreads();   // pair m landed; every thread is past the exchange reads of pair m - 1
+            {
+                const C* sb = stg + ((m & 1) * 2 + half) * NP;
+                C v[RA];
+#pragma unroll
+                for (int r = 0; r < RA; ++r) v[r] = sb[(j1 + r * RB) * P + p1];
+                RegDFT<RA, -1, C>::run(v);
+                C* xh = xb + half * NP;
+#pragma unroll
+                for (int r = 0; r < RA; ++r) xh[(j1 * RA + r) * P + p1] = v[r];
+            }
+            __syncthreads();   // exchange written; the staging buffers of pair m are free
+            if (m == 0) {
+                prefetch(4, stg);
+                prefetch(5, stg + NP);
+            }
+            stage2(2 * m, xb);
+            stage2(2 * m + 1, xb + NP);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (c < 5) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncthreads();
+            if (st1) {
+                const C* sb = stg + (c & 1) * NP;
+                C v[RA];
+#pragma unroll
+                for (int r = 0; r < RA; ++r) v[r] = sb[(j1 + r * RB) * P + p1];
+                RegDFT<RA, -1, C>::run(v);
+#pragma unroll
+                for (int r = 0; r < RA; ++r) xb[(j1 * RA + r) * P + p1] = v[r];
+            }
+            __syncthreads();
+            if (c + 2 < 6) prefetch(c + 2, stg + (c & 1) * NP);
+            else cp_async_commit();
+            stage2(c, xb);
+        }
     }
     T dre = T(0), dim = T(0);
     const C* pb = dotp ? dotp + (size_t)b * 3 * g.V : nullptr;
@@ -313,7 +395,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const C o = cscale(acc[i][r], out_scale);
-                ob[(size_t)i * g.V + a] = o;
+                if constexpr (sizeof(C) == 8) st_stream(ob + (size_t)i * g.V + a, o);
+                else ob[(size_t)i * g.V + a] = o;
                 if (pb) {
                     const C pv = pb[(size_t)i * g.V + a];
                     dre += pv.x * o.x + pv.y * o.y;
@@ -621,6 +704,17 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
             }
         }
     }
+}
+
+// Shared memory of k_fpass_z_strain<T, RA, RB, NT> and k_fpass_z_div<T, RA, RB, NT> (bytes).
+template <typename T, int RA, int RB, int NT>
+constexpr size_t fpass_z1_smem() {
+    return (size_t)(RA * RB + 4 * RA * RB * (NT / RA)) * sizeof(cplx_t<T>);
+}
+template <typename T, int RA, int RB, int NT>
+constexpr size_t fpass_z5_smem() {
+    constexpr int P = NT / RA, NP = RA * RB * P;
+    return (size_t)(RA * RB + (2 * P * RB == NT ? 6 : 3) * NP) * sizeof(cplx_t<T>);
 }
 
 // Shared memory of k_fpass_x_stress<T, RA, RB> (bytes).
