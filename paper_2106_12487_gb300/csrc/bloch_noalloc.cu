@@ -126,7 +126,7 @@ static void x_stress(bloch_plan* pl, int nb, float2* E) {
     const long long rows = (long long)pl->Ny * pl->Nz;
     dim3 gr((unsigned)((rows + P - 1) / P), nb);
     k_fpass_x_stress<float, RA, RB><<<gr, 128, fpass_x_smem<float, RA, RB>(), pl->stream>>>(
-        E, pl->d_ids, pl->d_Cpf, pl->d_twf[0], pl->geo_f);
+        E, pl->d_ids, pl->d_Cpf, pl->d_twf[0], pl->geo_f, nullptr);
 }
 
 template <int RA, int RB>

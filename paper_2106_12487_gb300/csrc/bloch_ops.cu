@@ -204,9 +204,10 @@ bloch_status ensure_cg(bloch_plan* pl, int nb) {
     BLOCH_CUDA_CHECK_RET(dmalloc(&w.part2, (size_t)nb * pl->nblk_max, &pl->device_bytes));
     BLOCH_CUDA_CHECK_RET(dmalloc(&w.dots, (size_t)nb, &pl->device_bytes));
     BLOCH_CUDA_CHECK_RET(dmalloc(&w.sys, (size_t)nb, &pl->device_bytes));
-    // the fused (p, Ap) partials need one slot per CTA of the z pass, for any fast variant later chosen
-    w.zblk = std::is_same<T, float>::value && fast_x(pl->Nz)
-                 ? (int)(((long long)pl->Nx * pl->Ny + 1) / 2)   // >= CTAs per system for every P >= 2
+    // the fused (p, Ap) partials need one slot per CTA of the fast x or z pass that forms them,
+    // for any fast variant later chosen (>= CTAs per system for every P >= 2)
+    w.zblk = std::is_same<T, float>::value && (fast_x(pl->Nz) || fast_x(pl->Nx))
+                 ? (int)((std::max((long long)pl->Nx * pl->Ny, (long long)pl->Ny * pl->Nz) + 1) / 2)
                  : 0;
     if (w.zblk) BLOCH_CUDA_CHECK_RET(dmalloc(&w.partz, (size_t)nb * w.zblk, &pl->device_bytes));
     w.cg_cap = nb;
@@ -346,8 +347,9 @@ static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale, const c
                                                                 tw_of<T>(pl, 2), g, out_scale, dotp, dpart);
 }
 
+// returns the CTAs per system (the number of (p, A p) partials written when dpart != nullptr)
 template <typename T, int RA, int RB>
-static void fast_x3(bloch_plan* pl, int nb) {
+static int fast_x3(bloch_plan* pl, int nb, double2* dpart) {
     const Geo& g = geo_of<T>(pl);
     constexpr int P = 128 / RA;
     const size_t smem = fpass_x_smem<T, RA, RB>();
@@ -355,7 +357,8 @@ static void fast_x3(bloch_plan* pl, int nb) {
     dim3 gr((unsigned)((rows + P - 1) / P), nb);
     ++pl->launches;
     k_fpass_x_stress<T, RA, RB><<<gr, 128, smem, pl->stream>>>(ws_of<T>(pl).E, pl->d_ids, cpk_of<T>(pl),
-                                                                 tw_of<T>(pl, 0), g);
+                                                                 tw_of<T>(pl, 0), g, dpart);
+    return (int)gr.x;
 }
 
 #define BLOCH_FAST_SWITCH(N, FN, ...)              \
@@ -413,15 +416,21 @@ int launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_s
             ++pl->launches;
             k_pass_axis<T, +1, 1><<<g2, 256, t.smem_y2, pl->stream>>>(w.E, w.E, tw_of<T>(pl, 1), g, t.Py2, T(1));
         }
+        // (p, A p) partials: from the strain energy in the fast x pass where it runs,
+        // else from the fast z-divergence pass (which then reads p once more)
         bool done3 = false;
+        const bool xdot = fx && dpart && dotp;
         if constexpr (std::is_same<T, float>::value) {
             if (fx) {
+                double2* xd = xdot ? dpart : nullptr;
+                int xb = 0;
                 switch (pl->Nx) {
-                    case 16: fast_x3<T, 4, 4>(pl, nb); break;
-                    case 32: fast_x3<T, 8, 4>(pl, nb); break;
-                    case 64: fast_x3<T, 8, 8>(pl, nb); break;
-                    default: fast_x3<T, 16, 8>(pl, nb); break;
+                    case 16: xb = fast_x3<T, 4, 4>(pl, nb, xd); break;
+                    case 32: xb = fast_x3<T, 8, 4>(pl, nb, xd); break;
+                    case 64: xb = fast_x3<T, 8, 8>(pl, nb, xd); break;
+                    default: xb = fast_x3<T, 16, 8>(pl, nb, xd); break;
                 }
+                if (xdot) fused = xb;
                 done3 = true;
             }
         }
@@ -439,9 +448,11 @@ int launch_K(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out, T out_s
         bool done5 = false;
         if constexpr (std::is_same<T, float>::value) {
             if (fz) {
-                BLOCH_FAST_SWITCH_Z(pl->Nz, fast_z5, pl, nb, out, out_scale, dpart ? dotp : nullptr, dpart);
+                const bool zdot = !xdot && dpart && dotp;
+                BLOCH_FAST_SWITCH_Z(pl->Nz, fast_z5, pl, nb, out, out_scale, zdot ? dotp : nullptr,
+                                    zdot ? dpart : nullptr);
                 done5 = true;
-                if (dpart && dotp) fused = fast_z_blocks(pl);
+                if (zdot) fused = fast_z_blocks(pl);
             }
         }
         if (!done5) {

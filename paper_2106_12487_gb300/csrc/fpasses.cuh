@@ -444,7 +444,7 @@ __host__ __device__ constexpr int sym6(int i, int j) {
 // table, 21 per grain), one row of C_g at a time so that few coefficients
 // are live next to the six components held per element.
 template <typename T, typename C, int R>
-__device__ __forceinline__ void stress_at(C (&s)[6][R], int r, const T* __restrict__ Cg) {
+__device__ __forceinline__ void stress_at(C (&s)[6][R], int r, const T* __restrict__ Cg, T& energy) {
     C sig[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -456,15 +456,32 @@ __device__ __forceinline__ void stress_at(C (&s)[6][R], int r, const T* __restri
             si = fma(cij, s[jj][r].y, si);
         }
         sig[i] = mk(sr, si);
+        energy = fma(s[i][r].x, sr, fma(s[i][r].y, si, energy));
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i][r] = sig[i];
 }
 
+// CTA sum in two steps around a barrier the caller already has: warp sums
+// into red[] before it, thread 0 adds them (FP64) after it.
+template <typename T>
+__device__ __forceinline__ void warp_sum_to(T v, T* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+}
+template <int NW, typename T>
+__device__ __forceinline__ void red_to(const T* red, double2* dst) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t += (double)red[w];
+    *dst = make_double2(t, 0.0);
+}
+
 template <typename T, int RA, int RB>
 __device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __restrict__ ids,
                                                 const T* __restrict__ Cpk, const cplx_t<T>* __restrict__ twx,
-                                                const Geo& g) {
+                                                const Geo& g, double2* __restrict__ dpart) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int LD = N + N / 16;
@@ -535,12 +552,21 @@ __device__ __forceinline__ void x_stress_single(cplx_t<T>* E, const int32_t* __r
         for (int r = 0; r < RB; ++r) s[c][r] = v[r];
     }
     // stress sigma = C_g gamma at the RB owned elements (packed symmetric table, 21 per grain)
-    if (own) {
+    __shared__ T red[4];
+    {
+        T energy = T(0);
+        if (own) {
 #pragma unroll
-        for (int r = 0; r < RB; ++r)
-            stress_at<T>(s, r, Cpk + (size_t)ids[(size_t)(r0 + p2) * N + j2 + r * RA] * 21);
+            for (int r = 0; r < RB; ++r) {
+                T e = T(0);
+                stress_at<T>(s, r, Cpk + (size_t)ids[(size_t)(r0 + p2) * N + j2 + r * RA] * 21, e);
+                energy += e;
+            }
+        }
+        if (dpart) warp_sum_to(energy, red);
     }
-    __syncthreads();   // the staging buffers become the forward exchange buffers
+    __syncthreads();   // the staging buffers become the forward exchange buffers; red[] complete
+    if (dpart && tid == 0) red_to<4>(red, dpart + (size_t)b * gridDim.x + blockIdx.x);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         C* buf = stg + (c & 1) * P * LD;
@@ -586,7 +612,7 @@ constexpr int x_ids_ld() { return N + 16; }
 template <typename T, int RA, int RB>
 __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __restrict__ ids,
                                                 const T* __restrict__ Cpk, const cplx_t<T>* __restrict__ twx,
-                                                const Geo& g) {
+                                                const Geo& g, double2* __restrict__ dpart) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int LD = N + N / 16;
@@ -670,9 +696,18 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
     }
     cp_async_wait<0>();
     __syncthreads();   // grain ids visible; all staging buffers free for the forward exchange
-    if (own) {
+    __shared__ T red[4];
+    {
+        T energy = T(0);
+        if (own) {
 #pragma unroll
-        for (int r = 0; r < RB; ++r) stress_at<T>(s, r, Cpk + (size_t)sid[p2 * LI + j2 + r * RA] * 21);
+            for (int r = 0; r < RB; ++r) {
+                T e = T(0);
+                stress_at<T>(s, r, Cpk + (size_t)sid[p2 * LI + j2 + r * RA] * 21, e);
+                energy += e;
+            }
+        }
+        if (dpart) warp_sum_to(energy, red);
     }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -688,6 +723,7 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
             for (int r = 0; r < RB; ++r) bufs[h * P * LD + p2 * LD + xpad(j2 * RB + r)] = v[r];
         }
         __syncthreads();   // a thread writing this buffer set again (pair m + 2) has passed the next barrier
+        if (m == 0 && dpart && tid == 0) red_to<4>(red, dpart + (size_t)blockIdx.y * gridDim.x + blockIdx.x);
         // forward stage 2 (radix RA): component 2m + half
         {
             C v[RA];
@@ -724,15 +760,22 @@ constexpr size_t fpass_x_smem() {
     return (size_t)(N + (P * RB == 64 ? 6 : 3) * P * LD) * sizeof(cplx_t<T>);
 }
 
+// With dpart != nullptr the CTA also forms the strain energy sum over its
+// points of conj(gamma) . sigma, which by Parseval equals its share of
+// (u, A_k u) for the apply's input u (the passes' transforms are unnormalised
+// and the divergence is the transpose of the strain map), and writes it to
+// dpart[b * gridDim.x + blockIdx.x]: the (p, A p) product of the PCG
+// iteration (Algorithm 2) without a second read of p.
 template <typename T, int RA, int RB>
 __global__ void __launch_bounds__(128, 4) k_fpass_x_stress(cplx_t<T>* E, const int32_t* __restrict__ ids,
                                                            const T* __restrict__ Cpk,
-                                                           const cplx_t<T>* __restrict__ twx, Geo g) {
+                                                           const cplx_t<T>* __restrict__ twx, Geo g,
+                                                           double2* __restrict__ dpart) {
     if (sys_idle(g, blockIdx.y)) return;
     if constexpr ((128 / RA) * RB == 64)
-        x_stress_paired<T, RA, RB>(E, ids, Cpk, twx, g);
+        x_stress_paired<T, RA, RB>(E, ids, Cpk, twx, g, dpart);
     else
-        x_stress_single<T, RA, RB>(E, ids, Cpk, twx, g);
+        x_stress_single<T, RA, RB>(E, ids, Cpk, twx, g, dpart);
 }
 
 }  // namespace bloch

@@ -33,7 +33,7 @@ struct Workspace {
     double2* part2 = nullptr; // cg_cap x nblk_max
     double2* dots = nullptr;  // cg_cap
     CGSys* sys = nullptr;     // cg_cap
-    double2* partz = nullptr; // cg_cap x zblk: (p, Ap) partials of the fused z-divergence pass
+    double2* partz = nullptr; // cg_cap x zblk: (p, Ap) partials of the fused x-stress or z-divergence pass
     int zblk = 0;
 };
 

@@ -172,6 +172,31 @@ def test_pcg_fp32_reaches_fp32_tolerance(B):
     assert relres[0] <= 1e-5 and true_rel < 3e-5
 
 
+@pytest.mark.parametrize("grid", [(16, 12, 10), (32, 10, 12), (64, 8, 6), (128, 6, 4), (12, 10, 32),
+                                  (10, 6, 128)])
+def test_pcg_fp32_fused_products(B, grid):
+    """FP32 PCG with (p, A p) formed inside the operator: by the strain energy
+    of the fast x pass (x axes 16-128: both x-pass forms) or by the fast
+    z-divergence pass (z axes 32, 128 with a generic x axis).  Iteration
+    counts follow the FP64 oracle's PCG and the true residual meets the
+    tolerance: a mis-scaled or mis-summed product would change the step
+    lengths and with them the iteration count."""
+    p = synth.small_polycrystal(grid, 5, 17)
+    med = O.Medium.from_problem(p)
+    plan = B.Plan.from_problem(p, precision=1)
+    ks = np.array([[0.3, 0.2, 0.1], [0.9, -0.4, 0.2]]) * math.pi / 1e-3
+    b = synth.random_field(grid, 8, batch=2) * 1e18
+    x = to_dev(np.zeros_like(b), 1)
+    iters, relres, _ = plan.pcg(ks, to_dev(b, 1), x, 1e-5, 2000)
+    got = x.cpu().numpy().astype(np.complex128)
+    for i in range(2):
+        A = lambda v, kk=ks[i]: O.apply_K(med, kk, v)
+        ref = O.pcg(A, lambda v, kk=ks[i]: O.apply_precond(med, kk, v), b[i], 1e-5, 2000)
+        assert abs(int(iters[i]) - ref.iters) <= 1
+        assert relres[i] <= 1e-5
+        assert O.norm(b[i] - A(got[i])) / O.norm(b[i]) < 3e-5
+
+
 def test_apply_K_large_grid_sampled(B):
     """Full-size 128^3 cell of the measured workload (200 grains, <001> fibre):
     FP32 apply against the oracle on the whole field, two wave vectors."""
