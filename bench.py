@@ -33,8 +33,8 @@ KAPPLY_BYTES_PER_VOXEL = {1: 436.0, 0: 868.0, 2: 868.0}   # algorithmic bytes pe
 # 1550.9 MB written); it scales with the systems per launch.  Valid only while the pass sources hash
 # to `sources_sha256` (fpasses.cuh, fft.cuh, common.cuh in that order); otherwise traffic is null.
 KAPPLY_TRAFFIC = {"grid": (128, 128, 128), "precision": 1, "fft_variant": 0,
-                  "bytes_per_system": 3383.66e6 / 4,
-                  "sources_sha256": "a089297b59baf58ba1706c191aa3f8bf8fd2ff722aab9d402da608ca207dae57"}
+                  "bytes_per_system": 3354.93e6 / 4,
+                  "sources_sha256": "41a688c96bd63cc65e705a03c72c5b75fc1145e236f979e9f7d593ea9c5d27eb"}
 
 
 def parse():
@@ -408,7 +408,8 @@ def alu_peaks_leg(p, opt, nb):
     return out
 
 
-PCG_BYTES_PER_VOXEL = 676.0   # FP32: K-apply 54c + 4, (p, Ap) partials 3c, CG vector kernels 27c (c = 8 B)
+# FP32, c = 8 B: K-apply 54c + 4 (its x pass also forms (p, Ap)), k_cg_update 9c, k_cg_pupdate 15c
+PCG_BYTES_PER_VOXEL = 628.0
 
 
 def pcg_roofline(plan, p, nb, iters):
