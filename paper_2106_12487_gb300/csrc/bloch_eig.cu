@@ -1292,6 +1292,25 @@ struct Lanczos {
         k_fill_int<<<1, 64, 0, pl->stream>>>(d_nv, nact, nv);
         const C* Wm = uniform ? Xc : MXc;
         const double sc = uniform ? rho_s : 1.0;
+        if (uniform && nv <= kGsMax) {
+            // the same two passes, reading the basis three times (dots; update + dots; update + norm)
+            pl->launches += 9;
+            const dim3 gg(nblk, nact);
+            launch_gs3<T>(0, gg, pl->stream, Vb, stride(), Xc, n3, nullptr, d_nv, n3, nv, d_part);
+            k_vdots_final<<<dim3(nv, nact), 256, 0, pl->stream>>>(d_part, nblk, nv, sc, d_h);
+            k_h_accum<<<nact, 64, 0, pl->stream>>>(d_H, d_h, nv, nv, j, m);
+            launch_gs3<T>(1, gg, pl->stream, Vb, stride(), Xc, n3, d_h, d_nv, n3, nv, d_part);
+            k_vdots_final<<<dim3(nv, nact), 256, 0, pl->stream>>>(d_part, nblk, nv, sc, d_h);
+            k_h_accum<<<nact, 64, 0, pl->stream>>>(d_H, d_h, nv, nv, j, m);
+            launch_gs3<T>(2, gg, pl->stream, Vb, stride(), Xc, n3, d_h, d_nv, n3, nv, d_part);
+            k_dot_final<<<nact, 256, 0, pl->stream>>>(d_part, nblk, w.dots);
+            k_lz_norm<<<(nact + 63) / 64, 64, 0, pl->stream>>>(w.dots, sc, d_H, j, m, nact, d_s);
+            ++pl->launches;
+            k_put_col<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(Xc, Vb, stride(), j + 1, n3, d_s);
+            trace_end(pl, tr_orth);
+            BLOCH_CUDA_CHECK_RET(cudaGetLastError());
+            return BLOCH_OK;
+        }
         for (int pass = 0; pass < 2; ++pass) {
             pl->launches += 4;
             k_vdots<T><<<dim3(nblk, nv, nact), 256, 0, pl->stream>>>(Vb, stride(), Wm, n3, d_nv, n3, nv, d_part);
@@ -1370,11 +1389,12 @@ struct Lanczos {
         pl->launches += 3;
         k_lz_ritz<<<nact, kThreadsRitz, lz_ritz_smem(m, kThreadsRitz), pl->stream>>>(
             m, d_H, d_neff, tol_eig, kc, kr, d_Q, d_theta, d_est, d_conv, d_jac);
-        launch_basis<T>(pl->stream, nact, Vb, Tmp, d_Q, m, n3, stride());
+        // only the kc kept or returned Ritz vectors are formed
+        launch_basis_first<T>(pl->stream, nact, Vb, Tmp, d_Q, m, kc, n3, stride());
         k_lz_restart_copy<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(Vb, Tmp, m, kr, n3);
         if (!uniform) {
             pl->launches += 2;
-            launch_basis<T>(pl->stream, nact, MVb, TmpM, d_Q, m, n3, stride());
+            launch_basis_first<T>(pl->stream, nact, MVb, TmpM, d_Q, m, kc, n3, stride());
             k_lz_restart_copy<T><<<dim3(gx(), nact), 256, 0, pl->stream>>>(MVb, TmpM, m, kr, n3);
         }
         BLOCH_CUDA_CHECK_RET(cudaGetLastError());

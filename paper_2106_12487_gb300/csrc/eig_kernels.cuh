@@ -318,6 +318,21 @@ void launch_basis(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* Ou
     launch_rotate<T>(st, nslot, In, Out, Q, rv, n_per);
 }
 
+// First qo columns of the square rotation: Out[slot][j] = sum_i In[slot][i] Q[slot][i][j], j < qo
+// (Q q x q row-major; outputs at the square layout's stride q * n_per).
+template <typename T>
+void launch_basis_first(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* Out, const double2* Q, int q,
+                        int qo, long long n_per, long long in_stride) {
+    RotView rv;
+    rv.in_slot = in_stride;
+    rv.segstride = 0;
+    rv.out_slot = (long long)q * n_per;
+    rv.qstride = (long long)q * q;
+    rv.qi = rv.seg = rv.ldq = q;
+    rv.qo = qo;
+    launch_rotate<T>(st, nslot, In, Out, Q, rv, n_per);
+}
+
 // Per vector v (blockIdx.y): partial sums of Re(u^H Ku), u^H (M u), |Ku|^2.
 // M u = MU[v] if MU is given, else rho_s * u.
 template <typename TK>
@@ -590,6 +605,157 @@ __global__ void k_vaxpy(const cplx_t<T>* __restrict__ V, long long vstride, cplx
         }
         w[e] = acc;
     }
+}
+
+// ---- two-pass classical Gram-Schmidt reading the basis three times (nv <= kGsMax)
+// The first pass forms all nv inner products from one read of W; the second
+// updates W and forms the inner products of the updated W in the same read
+// of the basis; the last update also forms |W|^2.  Partials per (slot,
+// block) as in k_vdots.  NV (8, 16, 24, 32) bounds nv at compile time so
+// the accumulators stay in registers.
+constexpr int kGsMax = 32;
+
+__device__ __forceinline__ float2 ldca_c(const float2* p) { return __ldca(p); }
+__device__ __forceinline__ double2 ldca_c(const double2* p) { return __ldca(p); }
+
+template <int NV, typename T>
+__device__ __forceinline__ void gs_write_partials(T (&acc)[2 * NV], int m, int maxnv, double2* __restrict__ partial) {
+    block_sum<T, 2 * NV>(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < m)
+                partial[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * maxnv + i] =
+                    make_double2(acc[2 * i], acc[2 * i + 1]);
+    }
+}
+
+// partial[(slot*gridDim.x + blk)*maxnv + i] = sum_e conj(V[slot][i][e]) W[slot][e], i < nv[slot]
+template <typename T, int NV>
+__global__ void __launch_bounds__(256, 2) k_vdots_all(const cplx_t<T>* __restrict__ V, long long vstride,
+                                                   const cplx_t<T>* __restrict__ W, long long wstride,
+                                                   const int* __restrict__ nv, long long n, int maxnv,
+                                                   double2* __restrict__ partial) {
+    using C = cplx_t<T>;
+    const int slot = blockIdx.y;
+    const int m = nv[slot];
+    const C* vb = V + (size_t)slot * vstride;
+    const C* w = W + (size_t)slot * wstride;
+    T acc[2 * NV];
+#pragma unroll
+    for (int i = 0; i < 2 * NV; ++i) acc[i] = T(0);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const C b = w[e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < m) {
+                const C a = vb[(size_t)i * n + e];
+                acc[2 * i] += a.x * b.x + a.y * b.y;
+                acc[2 * i + 1] += a.x * b.y - a.y * b.x;
+            }
+    }
+    gs_write_partials<NV>(acc, m, maxnv, partial);
+}
+
+// W[slot] -= sum_i V[slot][i] h[slot][i], then the inner products of the updated W
+// with every V[slot][i] into partial (layout as k_vdots_all); the basis
+// elements of the update are kept in registers for the products
+template <typename T, int NV>
+__global__ void __launch_bounds__(256, 2) k_vaxpy_dots(const cplx_t<T>* __restrict__ V, long long vstride,
+                                                    cplx_t<T>* __restrict__ W, long long wstride,
+                                                    const double2* __restrict__ h, const int* __restrict__ nv,
+                                                    long long n, int maxnv, double2* __restrict__ partial) {
+    using C = cplx_t<T>;
+    __shared__ C sh[NV];
+    const int slot = blockIdx.y;
+    const int m = nv[slot];
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+        const double2 v = i < m ? h[(size_t)slot * maxnv + i] : make_double2(0.0, 0.0);
+        sh[i] = mk(T(v.x), T(v.y));
+    }
+    __syncthreads();
+    const C* vb = V + (size_t)slot * vstride;
+    C* w = W + (size_t)slot * wstride;
+    T acc[2 * NV];
+#pragma unroll
+    for (int i = 0; i < 2 * NV; ++i) acc[i] = T(0);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        C b = w[e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < m) {
+                const C a = vb[(size_t)i * n + e], c = sh[i];
+                b.x -= a.x * c.x - a.y * c.y;
+                b.y -= a.x * c.y + a.y * c.x;
+            }
+        w[e] = b;
+        // the basis elements again, from L1 (just fetched by this thread)
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < m) {
+                const C a = ldca_c(vb + (size_t)i * n + e);
+                acc[2 * i] += a.x * b.x + a.y * b.y;
+                acc[2 * i + 1] += a.x * b.y - a.y * b.x;
+            }
+    }
+    gs_write_partials<NV>(acc, m, maxnv, partial);
+}
+
+// W[slot] -= sum_i V[slot][i] h[slot][i], and part[slot*gridDim.x + blk] = (sum |W|^2, 0)
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_vaxpy_norm(const cplx_t<T>* __restrict__ V, long long vstride,
+                                                    cplx_t<T>* __restrict__ W, long long wstride,
+                                                    const double2* __restrict__ h, const int* __restrict__ nv,
+                                                    long long n, int maxnv, double2* __restrict__ part) {
+    using C = cplx_t<T>;
+    __shared__ C sh[NV];
+    const int slot = blockIdx.y;
+    const int m = nv[slot];
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+        const double2 v = i < m ? h[(size_t)slot * maxnv + i] : make_double2(0.0, 0.0);
+        sh[i] = mk(T(v.x), T(v.y));
+    }
+    __syncthreads();
+    const C* vb = V + (size_t)slot * vstride;
+    C* w = W + (size_t)slot * wstride;
+    T acc[2] = {T(0), T(0)};
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        C b = w[e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < m) {
+                const C a = vb[(size_t)i * n + e], c = sh[i];
+                b.x -= a.x * c.x - a.y * c.y;
+                b.y -= a.x * c.y + a.y * c.x;
+            }
+        w[e] = b;
+        acc[0] += b.x * b.x + b.y * b.y;
+    }
+    block_sum<T, 2>(acc);
+    if (threadIdx.x == 0) part[(size_t)slot * gridDim.x + blockIdx.x] = make_double2(acc[0], 0.0);
+}
+
+// The three kernels above for the smallest NV >= nv.
+template <typename T>
+void launch_gs3(int which, dim3 grid, cudaStream_t st, const cplx_t<T>* V, long long vstride, cplx_t<T>* W,
+                long long wstride, const double2* h, const int* d_nv, long long n, int nv, double2* out) {
+#define BLOCH_GS3(NVC)                                                                                        \
+    do {                                                                                                       \
+        if (which == 0)                                                                                        \
+            k_vdots_all<T, NVC><<<grid, 256, 0, st>>>(V, vstride, W, wstride, d_nv, n, nv, out);             \
+        else if (which == 1)                                                                                   \
+            k_vaxpy_dots<T, NVC><<<grid, 256, 0, st>>>(V, vstride, W, wstride, h, d_nv, n, nv, out);         \
+        else                                                                                                   \
+            k_vaxpy_norm<T, NVC><<<grid, 256, 0, st>>>(V, vstride, W, wstride, h, d_nv, n, nv, out);         \
+    } while (0)
+    if (nv <= 8) BLOCH_GS3(8);
+    else if (nv <= 16) BLOCH_GS3(16);
+    else if (nv <= 24) BLOCH_GS3(24);
+    else BLOCH_GS3(32);
+#undef BLOCH_GS3
 }
 
 // dst[slot] (at per-slot element offsets) = src[slot] * s[slot]
