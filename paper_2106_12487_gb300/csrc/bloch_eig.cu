@@ -1292,7 +1292,7 @@ struct Lanczos {
         k_fill_int<<<1, 64, 0, pl->stream>>>(d_nv, nact, nv);
         const C* Wm = uniform ? Xc : MXc;
         const double sc = uniform ? rho_s : 1.0;
-        if (uniform && nv <= kGsMax) {
+        if (uniform && nv <= kGsMax && std::is_same<T, float>::value) {
             // the same two passes, reading the basis three times (dots; update + dots; update + norm)
             pl->launches += 9;
             const dim3 gg(nblk, nact);

@@ -612,7 +612,10 @@ __global__ void k_vaxpy(const cplx_t<T>* __restrict__ V, long long vstride, cplx
 // updates W and forms the inner products of the updated W in the same read
 // of the basis; the last update also forms |W|^2.  Partials per (slot,
 // block) as in k_vdots.  NV (8, 16, 24, 32) bounds nv at compile time so
-// the accumulators stay in registers.
+// the accumulators stay in registers; every thread issues all NV loads of an
+// element before using them (indices past nv repeat the last vector, an L1
+// hit, with a zero coefficient or an unused product), so they are in flight
+// together.
 constexpr int kGsMax = 32;
 
 __device__ __forceinline__ float2 ldca_c(const float2* p) { return __ldca(p); }
@@ -639,6 +642,7 @@ __global__ void __launch_bounds__(256, 2) k_vdots_all(const cplx_t<T>* __restric
     using C = cplx_t<T>;
     const int slot = blockIdx.y;
     const int m = nv[slot];
+    if (m <= 0) return;   // uniform over the block
     const C* vb = V + (size_t)slot * vstride;
     const C* w = W + (size_t)slot * wstride;
     T acc[2 * NV];
@@ -647,13 +651,14 @@ __global__ void __launch_bounds__(256, 2) k_vdots_all(const cplx_t<T>* __restric
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         const C b = w[e];
+        C a[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < m) {
-                const C a = vb[(size_t)i * n + e];
-                acc[2 * i] += a.x * b.x + a.y * b.y;
-                acc[2 * i + 1] += a.x * b.y - a.y * b.x;
-            }
+        for (int i = 0; i < NV; ++i) a[i] = vb[(size_t)min(i, m - 1) * n + e];   // all loads in flight
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            acc[2 * i] += a[i].x * b.x + a[i].y * b.y;
+            acc[2 * i + 1] += a[i].x * b.y - a[i].y * b.x;
+        }
     }
     gs_write_partials<NV>(acc, m, maxnv, partial);
 }
@@ -675,6 +680,7 @@ __global__ void __launch_bounds__(256, 2) k_vaxpy_dots(const cplx_t<T>* __restri
         sh[i] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
+    if (m <= 0) return;   // uniform over the block
     const C* vb = V + (size_t)slot * vstride;
     C* w = W + (size_t)slot * wstride;
     T acc[2 * NV];
@@ -683,29 +689,36 @@ __global__ void __launch_bounds__(256, 2) k_vaxpy_dots(const cplx_t<T>* __restri
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         C b = w[e];
+        {
+            C a[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < m) {
-                const C a = vb[(size_t)i * n + e], c = sh[i];
-                b.x -= a.x * c.x - a.y * c.y;
-                b.y -= a.x * c.y + a.y * c.x;
+            for (int i = 0; i < NV; ++i) a[i] = vb[(size_t)min(i, m - 1) * n + e];   // all loads in flight
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {   // sh[i] = 0 for i >= m
+                const C c = sh[i];
+                b.x -= a[i].x * c.x - a[i].y * c.y;
+                b.y -= a[i].x * c.y + a[i].y * c.x;
             }
+        }
         w[e] = b;
         // the basis elements again, from L1 (just fetched by this thread)
+        {
+            C a[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < m) {
-                const C a = ldca_c(vb + (size_t)i * n + e);
-                acc[2 * i] += a.x * b.x + a.y * b.y;
-                acc[2 * i + 1] += a.x * b.y - a.y * b.x;
+            for (int i = 0; i < NV; ++i) a[i] = ldca_c(vb + (size_t)min(i, m - 1) * n + e);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                acc[2 * i] += a[i].x * b.x + a[i].y * b.y;
+                acc[2 * i + 1] += a[i].x * b.y - a[i].y * b.x;
             }
+        }
     }
     gs_write_partials<NV>(acc, m, maxnv, partial);
 }
 
 // W[slot] -= sum_i V[slot][i] h[slot][i], and part[slot*gridDim.x + blk] = (sum |W|^2, 0)
 template <typename T, int NV>
-__global__ void __launch_bounds__(256) k_vaxpy_norm(const cplx_t<T>* __restrict__ V, long long vstride,
+__global__ void __launch_bounds__(256, 2) k_vaxpy_norm(const cplx_t<T>* __restrict__ V, long long vstride,
                                                     cplx_t<T>* __restrict__ W, long long wstride,
                                                     const double2* __restrict__ h, const int* __restrict__ nv,
                                                     long long n, int maxnv, double2* __restrict__ part) {
@@ -718,19 +731,22 @@ __global__ void __launch_bounds__(256) k_vaxpy_norm(const cplx_t<T>* __restrict_
         sh[i] = mk(T(v.x), T(v.y));
     }
     __syncthreads();
+    if (m <= 0) return;   // uniform over the block
     const C* vb = V + (size_t)slot * vstride;
     C* w = W + (size_t)slot * wstride;
     T acc[2] = {T(0), T(0)};
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         C b = w[e];
+        C a[NV];
 #pragma unroll
-        for (int i = 0; i < NV; ++i)
-            if (i < m) {
-                const C a = vb[(size_t)i * n + e], c = sh[i];
-                b.x -= a.x * c.x - a.y * c.y;
-                b.y -= a.x * c.y + a.y * c.x;
-            }
+        for (int i = 0; i < NV; ++i) a[i] = vb[(size_t)min(i, m - 1) * n + e];   // all loads in flight
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {   // sh[i] = 0 for i >= m
+            const C c = sh[i];
+            b.x -= a[i].x * c.x - a[i].y * c.y;
+            b.y -= a[i].x * c.y + a[i].y * c.x;
+        }
         w[e] = b;
         acc[0] += b.x * b.x + b.y * b.y;
     }
