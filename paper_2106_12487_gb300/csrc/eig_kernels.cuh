@@ -611,12 +611,13 @@ __global__ void k_vaxpy(const cplx_t<T>* __restrict__ V, long long vstride, cplx
 // The first pass forms all nv inner products from one read of W; the second
 // updates W and forms the inner products of the updated W in the same read
 // of the basis; the last update also forms |W|^2.  Partials per (slot,
-// block) as in k_vdots.  NV (8, 16, 24, 32) bounds nv at compile time so
+// block) as in k_vdots.  NV (8, 12, 16, 20, 24, 32) bounds nv at compile time so
 // the accumulators stay in registers; every thread issues all NV loads of an
 // element before using them (indices past nv repeat the last vector, an L1
 // hit, with a zero coefficient or an unused product), so they are in flight
 // together.
 constexpr int kGsMax = 32;
+constexpr int kGsKeep = 20;   // up to this NV the update keeps the basis elements in registers
 
 __device__ __forceinline__ float2 ldca_c(const float2* p) { return __ldca(p); }
 __device__ __forceinline__ double2 ldca_c(const double2* p) { return __ldca(p); }
@@ -689,28 +690,24 @@ __global__ void __launch_bounds__(256, 2) k_vaxpy_dots(const cplx_t<T>* __restri
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         C b = w[e];
-        {
-            C a[NV];
+        C a[NV];
 #pragma unroll
-            for (int i = 0; i < NV; ++i) a[i] = vb[(size_t)min(i, m - 1) * n + e];   // all loads in flight
+        for (int i = 0; i < NV; ++i) a[i] = vb[(size_t)min(i, m - 1) * n + e];   // all loads in flight
 #pragma unroll
-            for (int i = 0; i < NV; ++i) {   // sh[i] = 0 for i >= m
-                const C c = sh[i];
-                b.x -= a[i].x * c.x - a[i].y * c.y;
-                b.y -= a[i].x * c.y + a[i].y * c.x;
-            }
+        for (int i = 0; i < NV; ++i) {   // sh[i] = 0 for i >= m
+            const C c = sh[i];
+            b.x -= a[i].x * c.x - a[i].y * c.y;
+            b.y -= a[i].x * c.y + a[i].y * c.x;
         }
         w[e] = b;
-        // the basis elements again, from L1 (just fetched by this thread)
-        {
-            C a[NV];
+        if constexpr (NV > kGsKeep) {   // the basis elements again, from L1 (just fetched by this thread)
 #pragma unroll
             for (int i = 0; i < NV; ++i) a[i] = ldca_c(vb + (size_t)min(i, m - 1) * n + e);
+        }
 #pragma unroll
-            for (int i = 0; i < NV; ++i) {
-                acc[2 * i] += a[i].x * b.x + a[i].y * b.y;
-                acc[2 * i + 1] += a[i].x * b.y - a[i].y * b.x;
-            }
+        for (int i = 0; i < NV; ++i) {
+            acc[2 * i] += a[i].x * b.x + a[i].y * b.y;
+            acc[2 * i + 1] += a[i].x * b.y - a[i].y * b.x;
         }
     }
     gs_write_partials<NV>(acc, m, maxnv, partial);
@@ -768,7 +765,9 @@ void launch_gs3(int which, dim3 grid, cudaStream_t st, const cplx_t<T>* V, long 
             k_vaxpy_norm<T, NVC><<<grid, 256, 0, st>>>(V, vstride, W, wstride, h, d_nv, n, nv, out);         \
     } while (0)
     if (nv <= 8) BLOCH_GS3(8);
+    else if (nv <= 12) BLOCH_GS3(12);
     else if (nv <= 16) BLOCH_GS3(16);
+    else if (nv <= 20) BLOCH_GS3(20);
     else if (nv <= 24) BLOCH_GS3(24);
     else BLOCH_GS3(32);
 #undef BLOCH_GS3
