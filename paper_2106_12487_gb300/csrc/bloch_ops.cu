@@ -295,7 +295,8 @@ static void set_fast_attrs_n() {
     }
 }
 
-// the z and x fast passes exist in FP32 only (their register budget)
+// the z and x fast passes exist in FP32 only (their register budget); the
+// y passes serve FP32, FP64 and float-float
 template <typename T>
 static void set_fast_attrs() {
     constexpr bool Z = std::is_same<T, float>::value;
@@ -488,11 +489,30 @@ void launch_K_generic(bloch_plan* pl, int nb, const cplx_t<T>* u, cplx_t<T>* out
     k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5, out_scale);
 }
 
-// Float-float operator: the shared-memory passes in every configuration
+// Float-float operator: the shared-memory z and x passes; the two-stage
+// register y passes where the y axis has one (fft_variant 0)
 template <>
 int launch_K<dfloat>(bloch_plan* pl, int nb, const dfloat2* u, dfloat2* out, dfloat out_scale, const dfloat2*,
                      double2*) {
-    launch_K_generic<dfloat>(pl, nb, u, out, out_scale);
+    using T = dfloat;
+    if (!pl->fast || !fast_axis(pl->Ny)) {
+        launch_K_generic<T>(pl, nb, u, out, out_scale);
+        return 0;
+    }
+    Workspace<T>& w = ws_of<T>(pl);
+    const Geo& g = geo_of<T>(pl);
+    const TileCfg& t = tile_of<T>(pl);
+    const long long pxy = (long long)pl->Nx * pl->Ny, pyz = (long long)pl->Ny * pl->Nz;
+    dim3 g1((unsigned)((pxy + t.Pz5 - 1) / t.Pz5), nb);
+    dim3 g3((unsigned)((pyz + t.Px7 - 1) / t.Px7), nb);
+    ++pl->launches;
+    k_pass_z_strain<T><<<g1, 256, t.smem_z5, pl->stream>>>(u, w.E, w.qtab, tw_of<T>(pl, 2), g, t.Pz5);
+    BLOCH_FAST_SWITCH(pl->Ny, fast_y, pl, +1, nb, w.E);
+    ++pl->launches;
+    k_pass_x_stress<T><<<g3, 256, t.smem_x7, pl->stream>>>(w.E, pl->d_ids, ctab_of<T>(pl), tw_of<T>(pl, 0), g, t.Px7);
+    BLOCH_FAST_SWITCH(pl->Ny, fast_y, pl, -1, nb, w.E);
+    ++pl->launches;
+    k_pass_z_div<T><<<g1, 256, t.smem_z5, pl->stream>>>(w.E, out, w.qtab, tw_of<T>(pl, 2), g, t.Pz5, out_scale);
     return 0;
 }
 
@@ -1166,6 +1186,7 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
     CK(set_smem_attrs<dfloat>());
     set_fast_attrs<float>();
     set_fast_attrs<double>();
+    set_fast_attrs<dfloat>();
     pl->fast = pl->opt.fft_variant == 0;
     pl->variant = pl->opt.fft_variant;
 #undef CK
