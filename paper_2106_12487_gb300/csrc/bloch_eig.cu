@@ -59,10 +59,9 @@ bloch_status plan_solver_buf(bloch_plan* pl, int pool, int idx, size_t bytes, vo
     return BLOCH_OK;
 }
 
-size_t plan_solver_bytes(const bloch_plan* pl) {
-    size_t t = pl->handoff_bytes;
-    for (const auto& v : pl->solver_bufs)
-        for (const auto& b : v) t += b.bytes;
+size_t plan_solver_bytes(const bloch_plan* pl, int pool) {
+    size_t t = 0;
+    for (const auto& b : pl->solver_bufs[pool]) t += b.bytes;
     return t;
 }
 
@@ -1086,7 +1085,7 @@ static bloch_status run_subspace(bloch_plan* pl, const std::vector<std::array<do
     // slots: from the options or from free memory
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
-    freeb += plan_solver_bytes(pl);   // held by the plan from earlier solves, reused
+    freeb += plan_solver_bytes(pl, 0);   // this solver's pool, held from earlier solves and reused
     const size_t blk = (size_t)S.q * S.n3 * sizeof(cplx_t<T>);
     const size_t per_slot = blk * (S.lob ? (S.uniform ? 15 : 20) : (S.uniform ? 9 : 11)) + 64 * 1024;
     long long Bmax = std::max<long long>(1, (long long)(0.6 * (double)freeb / (double)per_slot));
@@ -1508,7 +1507,7 @@ static bloch_status run_lanczos(bloch_plan* pl, const std::vector<std::array<dou
     if (S.order.empty()) return BLOCH_OK;
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
-    freeb += plan_solver_bytes(pl);   // held by the plan from earlier solves, reused
+    freeb += plan_solver_bytes(pl, 1);   // this solver's pool, held from earlier solves and reused
     // basis, rotated basis, step vectors and CG workspace (twice the basis part
     // with a non-uniform density: the M-images are kept too)
     const size_t per_slot = (size_t)((2 * S.m + 1) * (S.uniform ? 1 : 2) + 2 + 6) * S.n3 * sizeof(cplx_t<T>);

@@ -260,7 +260,7 @@ void lp_deactivate(bloch_plan* pl);
 namespace bloch {
 // eigensolver buffers kept by the plan (bloch_eig.cu): buffer idx of pool, at least bytes
 bloch_status plan_solver_buf(bloch_plan* pl, int pool, int idx, size_t bytes, void** out);
-size_t plan_solver_bytes(const bloch_plan* pl);
+size_t plan_solver_bytes(const bloch_plan* pl, int pool);
 void plan_solver_release(bloch_plan* pl);
 // (M~ t_0)_0 for the Gamma-point deflation (non-uniform density), built once per precision
 template <typename T> bloch_status gamma_rhohat(bloch_plan* pl, const cplx_t<T>** out);
