@@ -116,8 +116,10 @@ static void z_strain(bloch_plan* pl, int nb, const float2* u, float2* E, const f
     constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
+    CUtensorMap map;   // encoded on the host: no device memory
+    const int tma = encode_zmap(&map, u, pl, 3LL * nb, P) ? 1 : 0;
     k_fpass_z_strain<float, RA, RB, NT><<<gr, NT, fpass_z1_smem<float, RA, RB, NT>(), pl->stream>>>(
-        u, E, qtab, pl->d_twf[2], pl->geo_f);
+        u, E, qtab, pl->d_twf[2], pl->geo_f, map, tma);
 }
 
 template <int RA, int RB>
@@ -135,8 +137,10 @@ static void z_div(bloch_plan* pl, int nb, const float2* E, float2* out, const fl
     constexpr int P = NT / RA;
     const long long npen = (long long)pl->Nx * pl->Ny;
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
+    CUtensorMap map;
+    const int tma = encode_zmap(&map, E, pl, 6LL * nb, P) ? 1 : 0;
     k_fpass_z_div<float, RA, RB, NT><<<gr, NT, fpass_z5_smem<float, RA, RB, NT>(), pl->stream>>>(
-        E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale, nullptr, nullptr);
+        E, out, qtab, pl->d_twf[2], pl->geo_f, (float)pl->Kscale, nullptr, nullptr, map, tma);
 }
 
 #define NOALLOC_SWITCH(N, FN, ...)                \

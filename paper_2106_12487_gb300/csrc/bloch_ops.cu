@@ -1,6 +1,7 @@
 // Plan creation, operator launchers, batched PCG and the C ABI entry points
 // for the operators (Section 3.2 Eqs. hatA/hatM, Section 3.3 Algorithm 2).
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -322,6 +323,56 @@ static void fast_y(bloch_plan* pl, int DIR, int nb, cplx_t<T>* E) {
         k_fpass_y<T, -1, RA, RB, PT><<<gr, 256, smem, pl->stream>>>(E, E, tw_of<T>(pl, 1), g);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_zmap(CUtensorMap* map, const void* base, const bloch_plan* pl, long long nsc, int P) {
+    std::memset(map, 0, sizeof(*map));
+    const unsigned long long plane = (unsigned long long)pl->Nx * pl->Ny;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+    if (!enc || base == nullptr || ((uintptr_t)base & 15) || (plane * 8) % 16 || plane < (unsigned long long)P ||
+        pl->Nz > 256 || nsc < 1)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)plane, (cuuint64_t)pl->Nz, (cuuint64_t)nsc};
+    const cuuint64_t strides[2] = {(cuuint64_t)(plane * 8), (cuuint64_t)(plane * 8 * (unsigned long long)pl->Nz)};
+    const cuuint32_t box[3] = {(cuuint32_t)P, (cuuint32_t)pl->Nz, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        std::memset(map, 0, sizeof(*map));
+        return false;
+    }
+    return true;
+}
+
+bloch_status check_pass_err(bloch_plan* pl) {
+    int e = 0;
+    BLOCH_CUDA_CHECK_RET(cudaMemcpyAsync(&e, pl->d_perr, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+    BLOCH_CUDA_CHECK_RET(cudaStreamSynchronize(pl->stream));
+    if (e) {
+        cudaMemsetAsync(pl->d_perr, 0, sizeof(int), pl->stream);
+        return set_error(BLOCH_ECUDA, "a pass's staging copy did not complete within its wait bound");
+    }
+    return BLOCH_OK;
+}
+
 template <typename T, int RA, int RB>
 static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
     const Geo& g = geo_of<T>(pl);
@@ -331,8 +382,10 @@ static void fast_z1(bloch_plan* pl, int nb, const cplx_t<T>* u) {
     const size_t smem = fpass_z1_smem<T, RA, RB, NT>();
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
+    CUtensorMap map;
+    const int tma = encode_zmap(&map, u, pl, 3LL * nb, P) ? 1 : 0;
     k_fpass_z_strain<T, RA, RB, NT><<<gr, NT, smem, pl->stream>>>(u, ws_of<T>(pl).E, ws_of<T>(pl).qtab,
-                                                                   tw_of<T>(pl, 2), g);
+                                                                   tw_of<T>(pl, 2), g, map, tma);
 }
 
 template <typename T, int RA, int RB>
@@ -344,8 +397,11 @@ static void fast_z5(bloch_plan* pl, int nb, cplx_t<T>* out, T out_scale, const c
     const size_t smem = fpass_z5_smem<T, RA, RB, NT>();
     dim3 gr((unsigned)((npen + P - 1) / P), nb);
     ++pl->launches;
+    CUtensorMap map;
+    const int tma = encode_zmap(&map, ws_of<T>(pl).E, pl, 6LL * nb, P) ? 1 : 0;
     k_fpass_z_div<T, RA, RB, NT><<<gr, NT, smem, pl->stream>>>(ws_of<T>(pl).E, out, ws_of<T>(pl).qtab,
-                                                                tw_of<T>(pl, 2), g, out_scale, dotp, dpart);
+                                                                tw_of<T>(pl, 2), g, out_scale, dotp, dpart, map,
+                                                                tma);
 }
 
 // returns the CTAs per system (the number of (p, A p) partials written when dpart != nullptr)
@@ -957,6 +1013,7 @@ void bloch_plan_destroy(bloch_plan* pl) {
     cudaFree(pl->d_Cx);
     cudaFree(pl->d_rx);
     cudaFree(pl->d_nactive);
+    cudaFree(pl->d_perr);
     cudaFreeHost(pl->h_nactive);
     cudaFree(pl->d_ztab);
     cudaFree(pl->d_handoff);
@@ -1178,6 +1235,8 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         CK(cudaMemcpy(pl->d_twx[a], tx.data(), sizeof(dfloat2) * N, cudaMemcpyHostToDevice));
     }
     CK(dmalloc(&pl->d_nactive, 1, acc));
+    CK(dmalloc(&pl->d_perr, 1, acc));
+    CK(cudaMemset(pl->d_perr, 0, sizeof(int)));
     CK(dmalloc(&pl->d_iter, 1, acc));
     CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
     CK(cudaMallocHost((void**)&pl->h_nactive, sizeof(int)));
@@ -1197,6 +1256,7 @@ bloch_status bloch_plan_create(bloch_plan** out, const int32_t grid[3], const do
         gp->V = V;
         gp->dx = make_fastdiv((unsigned)pl->Nx);
         gp->dy = make_fastdiv((unsigned)pl->Ny);
+        gp->err = pl->d_perr;
     }
     for (int a = 0; a < 3; ++a) {
         pl->geo_f.ax[a] = make_axis(grid[a], 4);   // radices up to 16 in FP32
@@ -1339,6 +1399,10 @@ bloch_status bloch_pcg(bloch_plan* pl, int32_t nb, const double* k, int32_t prec
                              iters, rel_res, nullptr);
     }
     lp_deactivate(pl);
+    if (st == BLOCH_OK || st == BLOCH_ENOTCONV_CG) {
+        const bloch_status e = check_pass_err(pl);
+        if (e != BLOCH_OK) return e;
+    }
     return st;
 }
 
@@ -1347,7 +1411,12 @@ bloch_status bloch_solve_bands(bloch_plan* pl, int32_t n_k, const double* k_list
     if (!pl) return set_error(BLOCH_EINVAL, "plan is NULL");
     if (n_k < 1 || !k_list || !omega_out) return set_error(BLOCH_EINVAL, "n_k >= 1, k_list and omega_out required");
     if (n_bands < 1 || (long long)n_bands >= 3 * pl->V) return set_error(BLOCH_EINVAL, "n_bands must be in [1, 3V)");
-    return bloch_solve_bands_impl(pl, n_k, k_list, n_bands, omega_out, vecs_out, stats);
+    const bloch_status st = bloch_solve_bands_impl(pl, n_k, k_list, n_bands, omega_out, vecs_out, stats);
+    if (st == BLOCH_OK || st == BLOCH_ENOTCONV_EIG) {
+        const bloch_status e = check_pass_err(pl);
+        if (e != BLOCH_OK) return e;
+    }
+    return st;
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "passes.cuh"
+#include "tma.cuh"
 
 namespace bloch {
 
@@ -105,22 +106,36 @@ __global__ void __launch_bounds__(256) k_fpass_y(const cplx_t<T>* in, cplx_t<T>*
 // transformed.
 // NT = 256 gives 16-32 neighbouring pencils per CTA, so each z row of the
 // tile is 128-256 contiguous bytes in HBM.
+// With use_tma the pencils are staged by the tensor memory accelerator: one
+// tiled copy of P pencils x N points per component (tensor map over the field
+// as [system * component][z][y * Nx + x] of 8-byte values), completed on an
+// mbarrier; otherwise by cp.async.  A wait that runs out sets *g.err.
 template <typename T, int RA, int RB, int NT = 128>
 __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>* __restrict__ U, cplx_t<T>* __restrict__ E,
                                                            const T* __restrict__ qtab,
-                                                           const cplx_t<T>* __restrict__ twz, Geo g) {
+                                                           const cplx_t<T>* __restrict__ twz, Geo g,
+                                                           const __grid_constant__ CUtensorMap tmap, int use_tma) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int P = NT / RA;
     constexpr int NP = N * P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tw = reinterpret_cast<C*>(smem_raw);
+    __shared__ __align__(8) uint64_t zbar[2];
+    C* tw = reinterpret_cast<C*>(smem_raw + smem_pad128(smem_raw));   // 128-byte aligned (TMA destinations)
     C* stg = tw + N;          // 2 x NP staging
     C* bufA = stg + 2 * NP;   // NP
     C* bufB = bufA + NP;      // NP
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
     if (sys_idle(g, b)) return;
+    if (use_tma) {
+        if (tid == 0) {
+            mbar_init(smem_u32(&zbar[0]), 1);
+            mbar_init(smem_u32(&zbar[1]), 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
     const unsigned plane = (unsigned)g.Nx * (unsigned)g.Ny;
     const unsigned pi0 = blockIdx.x * P;
     const int np = (int)min((unsigned)P, plane - pi0);
@@ -151,8 +166,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
         }
         cp_async_commit();
     };
-    prefetch(2, stg);
-    prefetch(0, stg + NP);
+    // component k into staging buffer bi
+    auto stage_in = [&](int k, int bi) {
+        if (use_tma) {
+            if (tid == 0) {
+                fence_async_smem();
+                mbar_expect_tx(smem_u32(&zbar[bi]), (uint32_t)(NP * sizeof(C)));
+                tma_load_3d(smem_u32(stg + bi * NP), &tmap, (int)pi0, 0, b * 3 + k, smem_u32(&zbar[bi]));
+            }
+        } else {
+            prefetch(k, stg + bi * NP);
+        }
+    };
+    stage_in(2, 0);
+    stage_in(0, 1);
     for (int i = tid; i < N; i += NT) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
     const unsigned pi = pi0 + (p2 < np ? p2 : 0);
@@ -176,8 +203,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
         const int k = kk == 0 ? 2 : kk - 1;   // z, x, y
-        if (kk < 2) cp_async_wait<1>();
-        else cp_async_wait<0>();
+        if (use_tma) {
+            if (!mbar_wait(smem_u32(&zbar[kk & 1]), (uint32_t)((kk >> 1) & 1)) && g.err) atomicExch(g.err, 1);
+        } else if (kk < 2) {
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
         if constexpr (split) {
             const C* sb = stg + (kk & 1) * NP;
@@ -209,7 +241,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
             for (int r = 0; r < RA; ++r) bufB[(j1 * RA + r) * P + p1] = u[r];
         }
         __syncthreads();
-        if (kk == 0) prefetch(1, stg);   // y into the buffer z has left
+        if (kk == 0) stage_in(1, 0);   // y into the buffer z has left
         C a[RB], bb[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
@@ -260,7 +292,8 @@ template <typename T, int RA, int RB, int NT = 128>
 __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* __restrict__ E, cplx_t<T>* __restrict__ out,
                                                         const T* __restrict__ qtab, const cplx_t<T>* __restrict__ twz,
                                                         Geo g, T out_scale, const cplx_t<T>* __restrict__ dotp,
-                                                        double2* __restrict__ dpart) {
+                                                        double2* __restrict__ dpart,
+                                                        const __grid_constant__ CUtensorMap tmap, int use_tma) {
     using C = cplx_t<T>;
     constexpr int N = RA * RB;
     constexpr int P = NT / RA;
@@ -272,12 +305,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
     constexpr bool pair = 2 * P * RB == NT;
     constexpr int NSTG = pair ? 4 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* tw = reinterpret_cast<C*>(smem_raw);
+    __shared__ __align__(8) uint64_t zbar[4];
+    C* tw = reinterpret_cast<C*>(smem_raw + smem_pad128(smem_raw));   // 128-byte aligned (TMA destinations)
     C* stg = tw + N;             // NSTG x NP staging
     C* xb = stg + NSTG * NP;     // (pair ? 2 : 1) x NP exchange
     const int tid = threadIdx.x;
     const int b = blockIdx.y;
     if (sys_idle(g, b)) return;
+    if (use_tma) {
+        if (tid == 0) {
+#pragma unroll
+            for (int i = 0; i < NSTG; ++i) mbar_init(smem_u32(&zbar[i]), 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
     const unsigned plane = (unsigned)g.Nx * (unsigned)g.Ny;
     const unsigned pi0 = blockIdx.x * P;
     const int np = (int)min((unsigned)P, plane - pi0);
@@ -306,8 +348,23 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
         }
         cp_async_commit();
     };
+    // component c into staging buffer bi (TMA: one tiled copy, as in the z-strain pass)
+    auto stage_in = [&](int c, int bi) {
+        if (use_tma) {
+            if (tid == 0) {
+                fence_async_smem();
+                mbar_expect_tx(smem_u32(&zbar[bi]), (uint32_t)(NP * sizeof(C)));
+                tma_load_3d(smem_u32(stg + bi * NP), &tmap, (int)pi0, 0, b * 6 + c, smem_u32(&zbar[bi]));
+            }
+        } else {
+            prefetch(c, stg + bi * NP);
+        }
+    };
+    auto stage_wait = [&](int bi, int parity) {
+        if (!mbar_wait(smem_u32(&zbar[bi]), (uint32_t)parity) && g.err) atomicExch(g.err, 1);
+    };
 #pragma unroll
-    for (int c = 0; c < NSTG; ++c) prefetch(c, stg + c * NP);
+    for (int c = 0; c < NSTG; ++c) stage_in(c, c);
     for (int i = tid; i < N; i += NT) tw[i] = twz[i];
     const int p2 = tid % P, j2 = tid / P;
     const unsigned pi = pi0 + (p2 < np ? p2 : 0);
@@ -344,8 +401,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
     if constexpr (pair) {
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            if (m < 2) cp_async_wait<2>();
-            else cp_async_wait<0>();
+            if (use_tma) {
+                stage_wait((m & 1) * 2, m >> 1);
+                stage_wait((m & 1) * 2 + 1, m >> 1);
+            } else if (m < 2) {
+                cp_async_wait<2>();
+            } else {
+                cp_async_wait<0>();
+            }
             __syncthreads();   // pair m landed; every thread is past the exchange reads of pair m - 1
             {
                 const C* sb = stg + ((m & 1) * 2 + half) * NP;
@@ -359,8 +422,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
             }
             __syncthreads();   // exchange written; the staging buffers of pair m are free
             if (m == 0) {
-                prefetch(4, stg);
-                prefetch(5, stg + NP);
+                stage_in(4, 0);
+                stage_in(5, 1);
             }
             stage2(2 * m, xb);
             stage2(2 * m + 1, xb + NP);
@@ -368,7 +431,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
     } else {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            if (c < 5) cp_async_wait<1>();
+            if (use_tma) stage_wait(c & 1, (c >> 1) & 1);
+            else if (c < 5) cp_async_wait<1>();
             else cp_async_wait<0>();
             __syncthreads();
             if (st1) {
@@ -381,8 +445,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
                 for (int r = 0; r < RA; ++r) xb[(j1 * RA + r) * P + p1] = v[r];
             }
             __syncthreads();
-            if (c + 2 < 6) prefetch(c + 2, stg + (c & 1) * NP);
-            else cp_async_commit();
+            if (c + 2 < 6) stage_in(c + 2, c & 1);
+            else if (!use_tma) cp_async_commit();
             stage2(c, xb);
         }
     }
@@ -745,12 +809,12 @@ __device__ __forceinline__ void x_stress_paired(cplx_t<T>* E, const int32_t* __r
 // Shared memory of k_fpass_z_strain<T, RA, RB, NT> and k_fpass_z_div<T, RA, RB, NT> (bytes).
 template <typename T, int RA, int RB, int NT>
 constexpr size_t fpass_z1_smem() {
-    return (size_t)(RA * RB + 4 * RA * RB * (NT / RA)) * sizeof(cplx_t<T>);
+    return (size_t)(RA * RB + 4 * RA * RB * (NT / RA)) * sizeof(cplx_t<T>) + kSmemAlignSlack;
 }
 template <typename T, int RA, int RB, int NT>
 constexpr size_t fpass_z5_smem() {
     constexpr int P = NT / RA, NP = RA * RB * P;
-    return (size_t)(RA * RB + (2 * P * RB == NT ? 6 : 3) * NP) * sizeof(cplx_t<T>);
+    return (size_t)(RA * RB + (2 * P * RB == NT ? 6 : 3) * NP) * sizeof(cplx_t<T>) + kSmemAlignSlack;
 }
 
 // Shared memory of k_fpass_x_stress<T, RA, RB> (bytes).

@@ -39,6 +39,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace bloch {
 
@@ -48,7 +49,6 @@ constexpr int kTCElems = 32;                 // complex elements of a chunk
 constexpr int kTCK = 2 * kTCElems;           // floats of a chunk (K extent of a stage)
 constexpr int kTCSBO = (kTCK / 4) * 128;     // bytes between 8-row groups of a tile
 constexpr int kTCLBO = 128;                  // bytes between core matrices adjacent in K
-constexpr long long kTCSpin = 1ll << 24;     // bound on mbarrier polls
 
 __host__ __device__ constexpr int tc_npad(int q) { return ((4 * q + 15) / 16) * 16; }
 __host__ __device__ constexpr int tc_agroups(int q) { return (4 * q + 7) / 8; }
@@ -63,30 +63,6 @@ inline size_t tc_smem_bytes(int q) {
     return std::max(std::max(2 * stage, need_read), dcopy);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < kTCSpin; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 

@@ -109,6 +109,7 @@ struct bloch_plan {
     dfloat* d_Cx = nullptr;
     dfloat* d_rx = nullptr;
     int* d_nactive = nullptr;
+    int* d_perr = nullptr;    // pass error word (a staging wait ran out), Geo::err
     int* h_nactive = nullptr;     // pinned
 
     bloch::Geo geo_f, geo_d;
@@ -261,6 +262,13 @@ namespace bloch {
 // eigensolver buffers kept by the plan (bloch_eig.cu): buffer idx of pool, at least bytes
 bloch_status plan_solver_buf(bloch_plan* pl, int pool, int idx, size_t bytes, void** out);
 size_t plan_solver_bytes(const bloch_plan* pl, int pool);
+// Tensor map for the TMA staging of the fast z passes: a complex FP32 field of
+// nsc [Nz][Ny * Nx] blocks at base, box P pencils x Nz; false where TMA cannot
+// serve (no driver entry point, base or strides not 16-byte multiples, fewer
+// than P pencils in a plane), *map then zeroed.
+bool encode_zmap(CUtensorMap* map, const void* base, const bloch_plan* pl, long long nsc, int P);
+// reads and clears the plan's pass error word (synchronises the plan's stream)
+bloch_status check_pass_err(bloch_plan* pl);
 void plan_solver_release(bloch_plan* pl);
 // (M~ t_0)_0 for the Gamma-point deflation (non-uniform density), built once per precision
 template <typename T> bloch_status gamma_rhohat(bloch_plan* pl, const cplx_t<T>** out);

@@ -49,6 +49,8 @@ struct Geo {
     const int* skip = nullptr;
     int skip_stride = 1;
     int skip_ncomp = 1;
+    // plan error word: a pass whose staging wait runs out sets it (nullptr: none)
+    int* err = nullptr;
 };
 
 __device__ __forceinline__ bool sys_idle(const Geo& g, int b) {

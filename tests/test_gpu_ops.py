@@ -173,14 +173,16 @@ def test_pcg_fp32_reaches_fp32_tolerance(B):
 
 
 @pytest.mark.parametrize("grid", [(16, 12, 10), (32, 10, 12), (64, 8, 6), (128, 6, 4), (12, 10, 32),
-                                  (10, 6, 128)])
+                                  (10, 6, 128), (5, 3, 32), (4, 2, 64)])
 def test_pcg_fp32_fused_products(B, grid):
     """FP32 PCG with (p, A p) formed inside the operator: by the strain energy
     of the fast x pass (x axes 16-128: both x-pass forms) or by the fast
     z-divergence pass (z axes 32, 128 with a generic x axis).  Iteration
     counts follow the FP64 oracle's PCG and the true residual meets the
     tolerance: a mis-scaled or mis-summed product would change the step
-    lengths and with them the iteration count."""
+    lengths and with them the iteration count.  The fast z passes stage their
+    pencils by TMA tiles where a plane has an even number of at least P
+    pencils, by cp.async otherwise (5 x 3 and 4 x 2 planes)."""
     p = synth.small_polycrystal(grid, 5, 17)
     med = O.Medium.from_problem(p)
     plan = B.Plan.from_problem(p, precision=1)
