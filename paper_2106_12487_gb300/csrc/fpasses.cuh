@@ -144,12 +144,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_strain(const cplx_t<T>
     const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T* qyt = qxt + g.Nx;
     const T* qzt = qyt + g.Ny;
-    // FP32: two neighbouring pencils per 16-byte copy, past L1 (P, pi0 and the
-    // plane are even, so a pair is wholly inside or outside the ragged tail)
-    constexpr bool k16 = sizeof(C) == 8 && P % 2 == 0;
+    // FP32 with an even plane: two neighbouring pencils per 16-byte copy, past
+    // L1 (P, pi0 and the plane even: 16-byte aligned pairs, each wholly inside
+    // or outside the ragged tail); 8-byte copies otherwise
+    const bool k16 = sizeof(C) == 8 && P % 2 == 0 && (plane & 1u) == 0;
     auto prefetch = [&](int k, C* dstb) {
         const C* src = Ub + (size_t)k * g.V;
-        if constexpr (k16) {
+        if (k16) {
 #pragma unroll
             for (int e = 2 * tid; e < NP; e += 2 * NT) {
                 const int n = e / P, p = e % P;
@@ -328,10 +329,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_fpass_z_div(const cplx_t<T>* _
     const T* qxt = qtab + (size_t)b * (g.Nx + g.Ny + g.Nz);
     const T* qyt = qxt + g.Nx;
     const T* qzt = qyt + g.Ny;
-    constexpr bool k16 = sizeof(C) == 8 && P % 2 == 0;   // as in the z-strain pass
+    const bool k16 = sizeof(C) == 8 && P % 2 == 0 && (plane & 1u) == 0;   // as in the z-strain pass
     auto prefetch = [&](int c, C* dstb) {
         const C* src = Eb + (size_t)c * g.V;
-        if constexpr (k16) {
+        if (k16) {
 #pragma unroll
             for (int e = 2 * tid; e < NP; e += 2 * NT) {
                 const int n = e / P, p = e % P;
