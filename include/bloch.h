@@ -192,7 +192,10 @@ void bloch_plan_destroy(bloch_plan* plan);
  *   u          device, nb x 3 x V complex, Fourier basis; not modified
  *   Ku         device, nb x 3 x V complex; may not alias u
  * Enqueued on the plan's stream (asynchronous).  Scratch: 6 x V complex per
- * vector, held by the plan and grown on demand.
+ * vector, held by the plan and grown on demand.  The FP32 fast z passes stage
+ * their pencils with TMA tiles when u is 16-byte aligned and Nx * Ny is even
+ * (cp.async otherwise); a staging wait that runs out sets the plan's pass
+ * error word, reported by the next bloch_pcg or bloch_solve_bands.
  */
 bloch_status bloch_apply_K(bloch_plan* plan, int32_t nb, const double* k, int32_t precision,
                            const void* u, void* Ku);
@@ -241,7 +244,9 @@ bloch_status bloch_apply_precond(bloch_plan* plan, int32_t nb, const double* k, 
  *   max_iter   iteration cap
  *   iters      host, nb (may be NULL): iterations taken per system
  *   rel_res    host, nb (may be NULL): final recursive relative residual per system
- * Synchronises the stream.  Returns BLOCH_ENOTCONV_CG if any system missed tol.
+ * Synchronises the stream.  Returns BLOCH_ENOTCONV_CG if any system missed tol,
+ * and BLOCH_ECUDA if a pass kernel since the previous synchronising call gave
+ * up waiting for its staging copies (the plan's pass error word; then cleared).
  */
 bloch_status bloch_pcg(bloch_plan* plan, int32_t nb, const double* k, int32_t precision,
                        const void* b, void* x, double tol, int32_t max_iter, int32_t use_x0,
@@ -261,7 +266,8 @@ bloch_status bloch_pcg(bloch_plan* plan, int32_t nb, const double* k, int32_t pr
  * Stop test (options.method = BLOCH_SUBSPACE, Algorithm 1): err1 <= tol_eig
  * and err2 <= 10 tol_eig (relative eigenvalue change, max relative residual).
  * With BLOCH_FP32 the FP32 iteration stops at the FP32 noise floor and the
- * block is refined by an FP64 Rayleigh-Ritz projection.  Synchronises.
+ * block is refined by an FP64 Rayleigh-Ritz projection.  Synchronises; returns
+ * BLOCH_ECUDA when the plan's pass error word is set (as bloch_pcg).
  */
 bloch_status bloch_solve_bands(bloch_plan* plan, int32_t n_k, const double* k_list, int32_t n_bands,
                                double* omega_out, void* vecs_out, bloch_stats* stats);
