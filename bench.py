@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--tensor-gram", type=int, default=0, choices=[0, 1],
                     help="1: Algorithm 1 projections of FP32 blocks on the tensor cores (tcgen05)")
     ap.add_argument("--ncv", type=int, default=0, help="Lanczos basis size of the chosen form (0: max(2n+1, 20))")
+    ap.add_argument("--k-batch", type=int, default=0,
+                    help="wave vectors advanced together by the chosen form (0: the library's choice, 8)")
     ap.add_argument("--hybrid-tol", type=float, default=0.0,
                     help="Lanczos-stage hand-over tolerance of the chosen form (0: max(1e-5, 10 tol_eig))")
     ap.add_argument("--refine-arith", type=int, default=1, choices=[0, 1],
@@ -555,7 +557,7 @@ def run_ours(args, ws, rank, local):
         opt = dict(precision=prec, method=bloch.LANCZOS, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
                    max_outer=args.max_outer, fft_variant=args.fft_variant, cuda_graph=args.cuda_graph,
                    tensor_gram=args.tensor_gram, ncv=args.ncv, hybrid_tol=args.hybrid_tol,
-                   refine_arith=args.refine_arith)
+                   refine_arith=args.refine_arith, k_batch=args.k_batch)
     elif args.form == "lobpcg":
         # FP32 LOBPCG with the Green preconditioner (no inner PCG), FP64 residual check
         opt = dict(precision=prec, method=bloch.LOBPCG, tol_lin=1e-2, tol_eig=1e-5, max_cg=500, block=p.n_bands + 2,
@@ -751,7 +753,7 @@ def run_ours(args, ws, rank, local):
                            "form": args.form, "tol_eig": opt["tol_eig"], "tol_lin": opt["tol_lin"],
                            "fft_variant": opt["fft_variant"], "cuda_graph": opt["cuda_graph"],
                            "tensor_gram": opt.get("tensor_gram", 0), "block": opt.get("block", 0),
-                           "ncv": opt.get("ncv", 0), "hybrid_tol": opt.get("hybrid_tol", 0.0),
+                           "ncv": opt.get("ncv", 0), "k_batch": opt.get("k_batch", 0), "hybrid_tol": opt.get("hybrid_tol", 0.0),
                            "refine_arith": opt.get("refine_arith", 0),
                            "method": {0: "lanczos", 1: "subspace", 2: "lobpcg"}[opt["method"]],
                            "l2": "inputs larger than L2 (one 3-component FP32 vector is %.0f MB)"
