@@ -206,43 +206,47 @@ __device__ __forceinline__ size_t rot_in(const RotView& r, int slot, int i, long
     return (size_t)slot * r.in_slot + (size_t)(i / r.seg) * r.segstride + (size_t)(i % r.seg) * n_per;
 }
 
-// k_basis_reg (qi, qo <= 32): each thread loads the qi inputs of its element
-// into registers at once (qi loads in flight) and forms the outputs one by one
-// from Q in shared memory (broadcast reads).
+// k_basis_reg (qi <= QI <= 32, qo <= 32): each thread loads the qi inputs of
+// its element into registers at once and forms the outputs one by one from Q
+// in shared memory (broadcast reads).  The per-input offsets are computed once
+// per CTA into shared memory, and every thread issues all QI loads before
+// using them (indices past qi repeat the last input, an L1 hit, with zero
+// rows of Q), so they are in flight together.
 // k_basis_cols (any qi, qo): output columns in chunks of 32 (blockIdx.y =
 // slot * nchunk + chunk), the qi x 32 slice of Q in dynamic shared memory, 32
 // accumulators per thread.
 constexpr int kBasisQMax = 64;
 
-template <typename T>
+template <typename T, int QI>
 __global__ void __launch_bounds__(128) k_basis_reg(const cplx_t<T>* __restrict__ In, cplx_t<T>* __restrict__ Out,
                                                    const double2* __restrict__ Q, RotView rv, long long n_per) {
     using C = cplx_t<T>;
-    __shared__ C sQ[kQMax * kQMax];
+    __shared__ C sQ[QI * kQMax];
+    __shared__ long long soff[QI];
     const int slot = blockIdx.y;
     const int qi = rv.qi, qo = rv.qo;
-    for (int t = threadIdx.x; t < qi * qo; t += blockDim.x) {
+    if (qi < 1) return;   // uniform over the grid
+    for (int t = threadIdx.x; t < QI * qo; t += blockDim.x) {
         const int i = t / qo, j = t - i * qo;
-        const double2 v = Q[(size_t)slot * rv.qstride + (size_t)i * rv.ldq + j];
+        const double2 v = i < qi ? Q[(size_t)slot * rv.qstride + (size_t)i * rv.ldq + j] : make_double2(0.0, 0.0);
         sQ[t] = mk(T(v.x), T(v.y));
     }
+    for (int i = threadIdx.x; i < QI; i += blockDim.x) soff[i] = (long long)rot_in(rv, slot, min(i, qi - 1), n_per);
     __syncthreads();
     C* ob = Out + (size_t)slot * rv.out_slot;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
          e += (long long)gridDim.x * blockDim.x) {
-        C v[kQMax];
+        C v[QI];
 #pragma unroll
-        for (int i = 0; i < kQMax; ++i)
-            if (i < qi) v[i] = In[rot_in(rv, slot, i, n_per) + e];
+        for (int i = 0; i < QI; ++i) v[i] = In[soff[i] + e];
         for (int j = 0; j < qo; ++j) {
             T re = 0, im = 0;
 #pragma unroll
-            for (int i = 0; i < kQMax; ++i)
-                if (i < qi) {
-                    const C w = sQ[i * qo + j];
-                    re = fma(v[i].x, w.x, fma(-v[i].y, w.y, re));
-                    im = fma(v[i].x, w.y, fma(v[i].y, w.x, im));
-                }
+            for (int i = 0; i < QI; ++i) {
+                const C w = sQ[i * qo + j];
+                re = fma(v[i].x, w.x, fma(-v[i].y, w.y, re));
+                im = fma(v[i].x, w.y, fma(v[i].y, w.x, im));
+            }
             ob[(size_t)j * n_per + e] = mk(re, im);
         }
     }
@@ -296,7 +300,10 @@ void launch_rotate(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* O
                    const RotView& rv, long long n_per) {
     const unsigned gx = (unsigned)std::min<long long>((n_per + 127) / 128, 8192);
     if (rv.qi <= kQMax && rv.qo <= kQMax) {
-        k_basis_reg<T><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
+        if (rv.qi <= 8) k_basis_reg<T, 8><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
+        else if (rv.qi <= 16) k_basis_reg<T, 16><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
+        else if (rv.qi <= 24) k_basis_reg<T, 24><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
+        else k_basis_reg<T, kQMax><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
     } else {
         const int nch = (rv.qo + kBasisJC - 1) / kBasisJC;
         k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)rv.qi * kBasisJC * sizeof(cplx_t<T>), st>>>(
