@@ -213,8 +213,8 @@ __device__ __forceinline__ size_t rot_in(const RotView& r, int slot, int i, long
 // using them (indices past qi repeat the last input, an L1 hit, with zero
 // rows of Q), so they are in flight together.
 // k_basis_cols (any qi, qo): output columns in chunks of 32 (blockIdx.y =
-// slot * nchunk + chunk), the qi x 32 slice of Q in dynamic shared memory, 32
-// accumulators per thread.
+// slot * nchunk + chunk), the qi x 32 slice of Q and the input offsets in
+// dynamic shared memory, 32 accumulators per thread, inputs loaded 8 at a time.
 constexpr int kBasisQMax = 64;
 
 template <typename T, int QI>
@@ -260,18 +260,23 @@ __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict_
     using C = cplx_t<T>;
     constexpr int JC = kBasisJC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sQ = reinterpret_cast<C*>(smem_raw);   // sQ[i * JC + jj] = Q[i][j0 + jj]
+    constexpr int IB = 8;   // inputs loaded together
+    C* sQ = reinterpret_cast<C*>(smem_raw);   // sQ[i * JC + jj] = Q[i][j0 + jj], qi rounded up to IB rows
     const int qi = rv.qi, qo = rv.qo;
+    if (qi < 1) return;   // uniform over the grid
+    const int qr = (qi + IB - 1) / IB * IB;
+    long long* soff = reinterpret_cast<long long*>(sQ + (size_t)qr * JC);   // input offsets
     const int nch = (qo + JC - 1) / JC;
     const int slot = blockIdx.y / nch;
     const int j0 = (blockIdx.y - slot * nch) * JC;
     const int ncol = min(JC, qo - j0);
-    for (int t = threadIdx.x; t < qi * JC; t += blockDim.x) {
+    for (int t = threadIdx.x; t < qr * JC; t += blockDim.x) {
         const int i = t / JC, jj = t - i * JC;
-        const double2 v = jj < ncol ? Q[(size_t)slot * rv.qstride + (size_t)i * rv.ldq + j0 + jj]
-                                    : make_double2(0.0, 0.0);
+        const double2 v = (jj < ncol && i < qi) ? Q[(size_t)slot * rv.qstride + (size_t)i * rv.ldq + j0 + jj]
+                                                : make_double2(0.0, 0.0);
         sQ[t] = mk(T(v.x), T(v.y));
     }
+    for (int i = threadIdx.x; i < qr; i += blockDim.x) soff[i] = (long long)rot_in(rv, slot, min(i, qi - 1), n_per);
     __syncthreads();
     C* ob = Out + (size_t)slot * rv.out_slot;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_per;
@@ -279,15 +284,18 @@ __global__ void __launch_bounds__(128) k_basis_cols(const cplx_t<T>* __restrict_
         T re[JC], im[JC];
 #pragma unroll
         for (int jj = 0; jj < JC; ++jj) re[jj] = im[jj] = T(0);
-#pragma unroll 2
-        for (int i = 0; i < qi; ++i) {
-            const C v = In[rot_in(rv, slot, i, n_per) + e];
+        for (int i0 = 0; i0 < qr; i0 += IB) {   // rows past qi repeat the last input with zero Q rows
+            C v[IB];
 #pragma unroll
-            for (int jj = 0; jj < JC; ++jj) {
-                const C w = sQ[i * JC + jj];
-                re[jj] = fma(v.x, w.x, fma(-v.y, w.y, re[jj]));
-                im[jj] = fma(v.x, w.y, fma(v.y, w.x, im[jj]));
-            }
+            for (int u = 0; u < IB; ++u) v[u] = In[soff[i0 + u] + e];
+#pragma unroll
+            for (int u = 0; u < IB; ++u)
+#pragma unroll
+                for (int jj = 0; jj < JC; ++jj) {
+                    const C w = sQ[(i0 + u) * JC + jj];
+                    re[jj] = fma(v[u].x, w.x, fma(-v[u].y, w.y, re[jj]));
+                    im[jj] = fma(v[u].x, w.y, fma(v[u].y, w.x, im[jj]));
+                }
         }
 #pragma unroll
         for (int jj = 0; jj < JC; ++jj)
@@ -306,8 +314,9 @@ void launch_rotate(cudaStream_t st, int nslot, const cplx_t<T>* In, cplx_t<T>* O
         else k_basis_reg<T, kQMax><<<dim3(gx, nslot), 128, 0, st>>>(In, Out, Q, rv, n_per);
     } else {
         const int nch = (rv.qo + kBasisJC - 1) / kBasisJC;
-        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, (size_t)rv.qi * kBasisJC * sizeof(cplx_t<T>), st>>>(
-            In, Out, Q, rv, n_per);
+        const size_t qr = (size_t)(rv.qi + 7) / 8 * 8;
+        k_basis_cols<T><<<dim3(gx, nslot * nch), 128, qr * kBasisJC * sizeof(cplx_t<T>) + qr * sizeof(long long),
+                          st>>>(In, Out, Q, rv, n_per);
     }
 }
 
