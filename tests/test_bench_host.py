@@ -43,3 +43,19 @@ def test_captured_traffic_is_below_the_algorithmic_bytes():
     V = t["grid"][0] * t["grid"][1] * t["grid"][2]
     alg = bench.KAPPLY_BYTES_PER_VOXEL[t["precision"]] * V
     assert 0.8 * alg < t["bytes_per_system"] < 1.05 * alg
+
+
+def test_algorithmic_counts_and_metric_names():
+    """The per-voxel counts the roofline lines divide by: the K-apply moves
+    54 complex values + a 4-byte grain id per voxel (436 B in FP32), a PCG
+    iteration adds the two CG vector kernels' 9c + 15c (628 B), and one apply
+    executes 36 length-N transforms at 5 log2 N flops per point plus the
+    pointwise strain, stress and divergence (1458 flops at 128^3)."""
+    c = 8
+    assert bench.KAPPLY_BYTES_PER_VOXEL[1] == 54 * c + 4
+    assert bench.PCG_BYTES_PER_VOXEL == 54 * c + 4 + (9 + 15) * c
+    assert bench.kapply_flops_per_voxel((128, 128, 128)) == 36 * 5 * 7 + 24 + 144 + 30
+    assert bench.kapply_flops_per_voxel((64, 32, 16)) == 5 * 12 * (6 + 5 + 4) + 24 + 144 + 30
+    assert bench.metric_of((128, 128, 128)) == bench.METRIC
+    assert "256^3" in bench.metric_of((256, 256, 256))
+    assert "128x128x1" in bench.metric_of((128, 128, 1))
