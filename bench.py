@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--alu-peaks", action="store_true",
                     help="measure FP64/FP32 FMA throughput and time the FP64, float-float and FP32 operator chains "
                          "on --kapply-nb systems against it")
+    ap.add_argument("--props", action="store_true",
+                    help="time the band-property calls (group velocity, real-space fields with strain) on "
+                         "--kapply-nb vectors (default 10) against one K-apply of the same vectors")
     ap.add_argument("--pcg-only", type=int, default=0, metavar="ITERS",
                     help="time only ITERS FP32 PCG iterations on --kapply-nb systems (default 4)")
     ap.add_argument("--kapply-prec", default="form", choices=["form", "fp32", "fp64", "ff"],
@@ -398,6 +401,40 @@ def kapply_flops_per_voxel(grid):
     return 5.0 * (12 * math.log2(nz) + 12 * math.log2(ny) + 12 * math.log2(nx)) + 24 + 144 + 30
 
 
+def props_leg(plan, p, nb):
+    """Group velocity (Eq. c_group) and real-space eigenvector fields with
+    strain (Eq. rotate_eigenvector) of nb vectors, CUDA events after one
+    warm-up call each, next to one K-apply of the same vectors."""
+    import torch
+    from paper_2106_12487_gb300 import bloch
+    prec = plan.precision
+    dt = torch.complex64 if prec == bloch.FP32 else torch.complex128
+    g = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.randn(nb * 3 * plan.V, dtype=dt, device="cuda", generator=g)
+    ur = torch.empty_like(u)
+    eps = torch.empty(nb * 6 * plan.V, dtype=dt, device="cuda")
+    kq = np.repeat(p.k_list[5:6], nb, axis=0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    t_k = timed(lambda: plan.apply_K(kq, u, ur))
+    t_gv = timed(lambda: plan.group_velocity(kq, u))
+    t_ev = timed(lambda: plan.eigvec_real(u, ur, eps))
+    return {"vectors": nb, "grid": list(p.grid), "ms_apply_K": t_k, "ms_group_velocity": t_gv,
+            "ms_eigvec_real_with_strain": t_ev, "group_velocity_over_apply_K": t_gv / t_k,
+            "eigvec_real_over_apply_K": t_ev / t_k}
+
+
 def alu_peaks_leg(p, opt, nb):
     """FMA peaks of the device and the operator chains timed against them."""
     from paper_2106_12487_gb300 import bloch
@@ -582,6 +619,12 @@ def run_ours(args, ws, rank, local):
         leg = alu_peaks_leg(p, opt, args.kapply_nb or 4)
         if rank == 0:
             print(json.dumps({"alu": leg}), flush=True)
+        return
+    if args.props:
+        leg = props_leg(plan, p, args.kapply_nb or 10)
+        if rank == 0:
+            print(json.dumps({"props": leg}), flush=True)
+        plan.close()
         return
     if args.pcg_only:
         roof = pcg_roofline(plan, p, args.kapply_nb or 4, args.pcg_only)
