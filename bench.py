@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--alu-peaks", action="store_true",
                     help="measure FP64/FP32 FMA throughput and time the FP64, float-float and FP32 operator chains "
                          "on --kapply-nb systems against it")
+    ap.add_argument("--wave-speeds", action="store_true",
+                    help="low-frequency wave speeds (Section 5.2, Eq. wave_speed2) of the workload along x, y "
+                         "and z: Hellmann-Feynman slopes of the three acoustic branches at k = K d, FP64 form")
     ap.add_argument("--props", action="store_true",
                     help="time the band-property calls (group velocity, real-space fields with strain) on "
                          "--kapply-nb vectors (default 10) against one K-apply of the same vectors")
@@ -435,6 +438,45 @@ def props_leg(plan, p, nb):
             "eigvec_real_over_apply_K": t_ev / t_k}
 
 
+def voigt_christoffel_speeds(p, d):
+    """Plane-wave speeds along d of the volume-average (Voigt) stiffness and
+    density of the cell: sqrt of the eigenvalues (ascending) of the Christoffel
+    matrix C0_ijkl d_j d_l / rho_bar."""
+    ids = np.asarray(p.grain_ids).ravel()
+    counts = np.bincount(ids, minlength=len(p.rho)) / ids.size
+    C0 = np.einsum("g,gij->ij", counts, np.asarray(p.C_per_grain, float))
+    rho = float(np.dot(counts, p.rho))
+    vi = ((0, 5, 4), (5, 1, 3), (4, 3, 2))   # Voigt index of the tensor pair (i, j)
+    C4 = np.array([[[[C0[vi[i][j], vi[k][l]] for l in range(3)] for k in range(3)] for j in range(3)]
+                   for i in range(3)])
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    return np.sqrt(np.linalg.eigvalsh(np.einsum("ijkl,j,l->ik", C4, d, d) / rho))
+
+
+def wave_speeds_leg(p, K_frac=0.01):
+    """Wave speeds along x, y, z (Eq. wave_speed2): the three lowest bands at
+    k = K d (K = K_frac pi / L) from bloch_solve_bands (FP64 plain form's
+    precision and tolerances, our passes), their group velocities from
+    bloch_group_velocity, projected on d.  Next to them, the Christoffel speeds
+    of the volume-average stiffness C0 (Eq. wave_speed with the Voigt average in
+    place of the paper's FFT-homogenised C, an upper bound)."""
+    import torch
+    from paper_2106_12487_gb300 import bloch
+    plan = bloch.Plan.from_problem(p, precision=bloch.FP64, method=bloch.LANCZOS, tol_lin=1e-10,
+                                   tol_eig=1e-10, max_cg=2000)
+    out = {}
+    for name, d in (("x", (1.0, 0.0, 0.0)), ("y", (0.0, 1.0, 0.0)), ("z", (0.0, 0.0, 1.0))):
+        d = np.array(d)
+        K = K_frac * math.pi / p.L[int(np.argmax(d))]
+        vecs = torch.zeros(3 * 3 * plan.V, dtype=torch.complex128, device="cuda")
+        omega, _, st = plan.solve_bands((K * d)[None], 3, vecs_out=vecs)
+        _, c = plan.group_velocity(np.repeat((K * d)[None], 3, 0), vecs)
+        out[name] = {"speeds": (c @ d).tolist(), "secant": (omega[0] / K).tolist(), "status": int(st),
+                     "voigt_christoffel": voigt_christoffel_speeds(p, d).tolist()}
+    plan.close()
+    return {"workload": p.name if hasattr(p, "name") else None, "K_frac_pi_over_L": K_frac, "directions": out}
+
+
 def alu_peaks_leg(p, opt, nb):
     """FMA peaks of the device and the operator chains timed against them."""
     from paper_2106_12487_gb300 import bloch
@@ -619,6 +661,12 @@ def run_ours(args, ws, rank, local):
         leg = alu_peaks_leg(p, opt, args.kapply_nb or 4)
         if rank == 0:
             print(json.dumps({"alu": leg}), flush=True)
+        return
+    if args.wave_speeds:
+        plan.close()
+        leg = wave_speeds_leg(p)
+        if rank == 0:
+            print(json.dumps({"wave_speeds": leg}), flush=True)
         return
     if args.props:
         leg = props_leg(plan, p, args.kapply_nb or 10)

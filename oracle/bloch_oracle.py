@@ -505,6 +505,29 @@ def group_velocity_hf(med: Medium, k, U: np.ndarray):
     return om, c
 
 
+def wave_speeds(med: Medium, direction, K: float | None = None) -> np.ndarray:
+    """Low-frequency wave speeds along a propagation direction (Section 5.2,
+    Eq. wave_speed2): the slopes d omega^b / dK of the three acoustic branches
+    b = 1, 2, 3 (ascending omega: the two transverse branches, then the
+    longitudinal one) at k = K d, d the unit direction and K small against the
+    Brillouin zone (default 1e-3 pi / max L).  Each slope is d . grad_k omega of
+    the dense eigenvector by the Hellmann-Feynman identity (group_velocity_hf);
+    for a degenerate transverse pair every vector of the pair gives the same
+    slope along d when d is a symmetry axis.  Dense eigensolve: tiny grids only.
+    Returns the three speeds (m/s)."""
+    import scipy.linalg
+
+    d = np.asarray(direction, float)
+    d = d / np.linalg.norm(d)
+    if K is None:
+        K = 1e-3 * math.pi / max(med.L)
+    k = K * d
+    _, W = scipy.linalg.eigh(dense_K(med, k), dense_M(med), subset_by_index=(0, 2))
+    U = W.T.reshape((3,) + med.shape)
+    _, c = group_velocity_hf(med, k, U)
+    return c @ d
+
+
 def group_velocity_fd(med: Medium, k, n: int, h: float, solver=None):
     """Group velocities of the n lowest bands by central finite differences of
     the band frequencies along each axis, the derivative of Eq. (c_group) taken

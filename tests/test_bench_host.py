@@ -59,3 +59,25 @@ def test_algorithmic_counts_and_metric_names():
     assert bench.metric_of((128, 128, 128)) == bench.METRIC
     assert "256^3" in bench.metric_of((256, 256, 256))
     assert "128x128x1" in bench.metric_of((128, 128, 1))
+
+
+def test_voigt_christoffel_speeds_match_the_oracle_on_a_single_crystal():
+    """For a one-grain cell the volume average is the crystal itself, so the
+    Christoffel speeds of the wave-speed study equal the oracle's branch slopes
+    (Eq. wave_speed2) of that homogeneous cell."""
+    import numpy as np
+    from oracle import bloch_oracle as O
+    from paper_2106_12487_gb300 import synth
+    hx = synth.hexagonal_voigt(162e9, 92e9, 69e9, 181e9, 46.7e9)
+    C6 = synth.rotate_voigt(hx, synth.haar_rotations(1, 5)[0])
+    grid = (3, 4, 4)
+    Nx, Ny, Nz = grid
+
+    class P1:
+        grain_ids = np.zeros((Nz, Ny, Nx), np.int32)
+        C_per_grain = C6[None]
+        rho = np.array([4506.0])
+
+    med = O.Medium(grid, (1e-3,) * 3, P1.grain_ids, P1.C_per_grain, P1.rho)
+    for d in ([1.0, 0.0, 0.0], [0.3, -0.2, 0.9]):
+        assert np.allclose(bench.voigt_christoffel_speeds(P1, d), O.wave_speeds(med, d), rtol=1e-8)

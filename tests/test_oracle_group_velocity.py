@@ -150,3 +150,75 @@ def test_eigvec_real_strain_of_a_plane_wave():
             assert np.max(np.abs(eps[c] - want)) <= 1e-12 * np.max(np.abs(xi)) / (Nx * Ny * Nz)
         for i in range(3):
             assert np.max(np.abs(U[i] - pol[i] * wave)) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Wave speeds (Section 5.2, Eq. wave_speed2)
+# ---------------------------------------------------------------------------
+def christoffel_speeds(C6, rho, d):
+    """sqrt of the eigenvalues of the Christoffel matrix G_ik = C_ijkl d_j d_l / rho
+    of a homogeneous crystal (the closed form of plane waves, Eq. wave_speed for
+    general anisotropy), from the Voigt matrix through the full tensor."""
+    idx = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (1, 2): 3, (2, 1): 3, (0, 2): 4, (2, 0): 4, (0, 1): 5, (1, 0): 5}
+    C = np.zeros((3, 3, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    C[i, j, k, l] = C6[idx[(i, j)], idx[(k, l)]]
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    G = np.einsum("ijkl,j,l->ik", C, d, d) / rho
+    return np.sqrt(np.linalg.eigvalsh(G))
+
+
+def test_wave_speeds_isotropic_and_cubic_closed_forms():
+    rho = 8960.0
+    iso = synth.isotropic_voigt(90e9, 40e9)
+    ws = O.wave_speeds(homog(iso, rho, (4, 4, 3)), [0.3, -0.5, 0.8])
+    cT, cL = math.sqrt(40e9 / rho), math.sqrt(170e9 / rho)
+    assert np.allclose(ws, [cT, cT, cL], rtol=1e-9)
+    C11, C12, C44 = 168.4e9, 121.4e9, 75.4e9
+    cub = synth.cubic_voigt(C11, C12, C44)
+    med = homog(cub, rho, (4, 3, 4))
+    # [100]: two transverse branches at sqrt(C44/rho), longitudinal sqrt(C11/rho)
+    assert np.allclose(O.wave_speeds(med, [1, 0, 0]),
+                       [math.sqrt(C44 / rho), math.sqrt(C44 / rho), math.sqrt(C11 / rho)], rtol=1e-9)
+    # [110]: split transverse pair; a slope taken along x instead of d fails here
+    want = sorted([math.sqrt(C44 / rho), math.sqrt((C11 - C12) / (2 * rho)),
+                   math.sqrt((C11 + C12 + 2 * C44) / (2 * rho))])
+    got = O.wave_speeds(med, [1, 1, 0])
+    assert np.allclose(got, want, rtol=1e-9)
+    assert not np.allclose(got / math.sqrt(2.0), want, rtol=1e-3)
+
+
+def test_wave_speeds_rotated_hexagonal_crystal_christoffel():
+    rho = 4506.0
+    hx = synth.hexagonal_voigt(162e9, 92e9, 69e9, 181e9, 46.7e9)
+    R = synth.haar_rotations(1, 23)[0]
+    C6 = synth.rotate_voigt(hx, R)
+    med = homog(C6, rho, (3, 4, 4))
+    for d in ([0.2, 0.9, -0.4], [1.0, 0.0, 0.0], [0.0, 0.3, 1.0]):
+        assert np.allclose(O.wave_speeds(med, d), christoffel_speeds(C6, rho, d), rtol=1e-8)
+
+
+def test_wave_speeds_polycrystal_equal_branch_slopes():
+    """On a polycrystal the Hellmann-Feynman slopes along d equal central
+    differences of the three lowest frequencies along d at k = K d (the paper
+    differentiates the branch numerically near the origin)."""
+    import scipy.linalg
+    med = small_poly()
+    d = np.array([0.0, 0.0, 1.0])
+    K = 0.02 * math.pi / 1e-3
+    ws = O.wave_speeds(med, d, K)
+    Md = O.dense_M(med)
+
+    def om3(kk):
+        lam = scipy.linalg.eigh(O.dense_K(med, kk), Md, eigvals_only=True, subset_by_index=(0, 2))
+        return np.sqrt(lam)
+
+    h = 0.1 * K
+    fd = (om3((K + h) * d) - om3((K - h) * d)) / (2 * h)
+    assert np.all(np.diff(ws) >= 0) or np.all(np.abs(np.diff(ws)) < 1e-3 * ws[2])
+    assert np.allclose(ws, fd, rtol=1e-5)
+    # the low-frequency limit: the secant omega(K)/K agrees to O(K^2)
+    assert np.allclose(om3(K * d) / K, ws, rtol=1e-3)
